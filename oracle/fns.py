@@ -1,0 +1,131 @@
+"""Oracle: FNS++ perturbation-sensitive natural-spinor truncation (test infrastructure).
+
+Only tests and the CPU-baseline leg of ``bench.py`` may use this module.
+Plain numpy, complex128, following Sec. II.B-C of the paper:
+
+1. MP2 doubles t_ij^ab = <ab||ij>/(e_i + e_j - e_a - e_b)             (Eq. 39)
+2. Hbar_ii = f_ii + 1/2 sum_nef t_in^ef <in||ef>,
+   Hbar_aa = f_aa - 1/2 sum_mnf t_mn^fa <mn||fa>                        (Eq. 49-50)
+3. per dipole direction A: Abar_ij^ab = P(ab) sum_e t_ij^ae A_be
+   - P(ij) sum_m t_im^ab A_mj, Abar_i^a = A_ai + sum_me A_me t_im^ae    (Eq. 48)
+4. t^(1) = Abar / (Dbar - omega), Dbar from Hbar                       (Eq. 46-47)
+5. D^A_ab = 1/2 sum_ijc t_ij^ac conj(t_ij^bc) + sum_i t_i^a conj(t_i^b),
+   averaged over x, y, z                                               (Eq. 45)
+6. eigenvectors of the averaged density = natural spinors (Eq. 41); keep by
+   |n| descending (stable in the eigen-solver's order), by count or by
+   threshold (the density is not positive definite, so |n| is used)
+7. Ftilde = Vt^H F_vv Vt, diagonalise (Eq. 42-43); U = Vt Z (Eq. 44 read as
+   a column-vector transformation)
+8. rotate B^L and mu into the new virtual basis; new virtual energies are the
+   semicanonical eigenvalues.
+
+Readings where the paper is ambiguous (the project's readings): Eq. 40/45 are
+taken with the complex conjugate on the second amplitude (Hermitian density);
+the three directions are averaged at the level of densities; the denominator
+sign follows Eq. 29 (Dbar - omega), with ``plus_omega=True`` giving Eq. 46 as
+printed.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _anti(B, P, Q, R, S):
+    d = np.einsum('lpr,lqs->pqrs', B[:, P, R], B[:, Q, S], optimize=True)
+    x = np.einsum('lps,lqr->pqrs', B[:, P, S], B[:, Q, R], optimize=True)
+    return d - x
+
+
+def mp2_doubles(eps, B, O):
+    N = eps.shape[0]
+    o, v = slice(0, O), slice(O, N)
+    vvoo = _anti(B, v, v, o, o)                      # <ab||ij>
+    eo, ev = eps[:O], eps[O:]
+    D = eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
+    return vvoo.transpose(2, 3, 0, 1) / D           # t[i,j,a,b]
+
+
+def mp2_energy(eps, B, O):
+    N = eps.shape[0]
+    o, v = slice(0, O), slice(O, N)
+    t2 = mp2_doubles(eps, B, O)
+    oovv = _anti(B, o, o, v, v)
+    return 0.25 * np.einsum('ijab,ijab->', oovv, t2)
+
+
+def hbar_diagonals(eps, B, O, t2):
+    N = eps.shape[0]
+    o, v = slice(0, O), slice(O, N)
+    oovv = _anti(B, o, o, v, v)                      # <mn||ef>
+    Hii = eps[:O] + 0.5 * np.einsum('inef,inef->i', t2, oovv).real
+    Haa = eps[O:] - 0.5 * np.einsum('mnfa,mnfa->a', t2, oovv).real
+    return Hii, Haa
+
+
+def first_order_amplitudes(eps, B, mu_c, O, t2, Hii, Haa, omega=0.0, plus_omega=False):
+    """Abar over (Dbar -/+ omega) for one perturbation A = mu_c (Eq. 46-48)."""
+    N = eps.shape[0]
+    A = np.asarray(mu_c)
+    Aoo, Aov, Avo, Avv = A[:O, :O], A[:O, O:], A[O:, :O], A[O:, O:]
+    X = np.einsum('ijae,be->ijab', t2, Avv)
+    Yy = np.einsum('imab,mj->ijab', t2, Aoo)
+    A2 = (X - X.transpose(0, 1, 3, 2)) - (Yy - Yy.transpose(1, 0, 2, 3))
+    A1 = Avo.T + np.einsum('me,imae->ia', Aov, t2)
+    s = 1.0 if plus_omega else -1.0
+    D2 = (Haa[None, None, :, None] + Haa[None, None, None, :]
+          - Hii[:, None, None, None] - Hii[None, :, None, None]) + s * omega
+    D1 = Haa[None, :] - Hii[:, None] + s * omega
+    return A1 / D1, A2 / D2
+
+
+def fnspp_density(eps, B, mu, O, omega=0.0, plus_omega=False):
+    """Averaged perturbation-sensitive virtual density M [V, V] (Eq. 45)."""
+    t2 = mp2_doubles(eps, B, O)
+    Hii, Haa = hbar_diagonals(eps, B, O, t2)
+    V = eps.shape[0] - O
+    M = np.zeros((V, V), dtype=np.complex128)
+    for c in range(3):
+        t1p, t2p = first_order_amplitudes(eps, B, mu[c], O, t2, Hii, Haa, omega, plus_omega)
+        M += 0.5 * np.einsum('ijac,ijbc->ab', t2p, t2p.conj()) + np.einsum('ia,ib->ab', t1p, t1p.conj())
+    return M / 3.0
+
+
+def select(n: np.ndarray, by_count: bool, value: float) -> np.ndarray:
+    """Indices of kept natural spinors: sort by |n| descending, ties in the
+    eigen-solver's order; keep the first ``value`` (count) or all with
+    |n| >= value (threshold)."""
+    order = np.argsort(-np.abs(n), kind='stable')
+    if by_count:
+        k = int(value)
+        if k < 1 or k > n.shape[0]:
+            raise ValueError("count out of range")
+        return order[:k]
+    keep = order[np.abs(n[order]) >= value]
+    if keep.size == 0:
+        raise ValueError("threshold removes every virtual")
+    return keep
+
+
+def truncate(system, by_count=True, value=None, omega=0.0, plus_omega=False):
+    """FNS++ truncation.  Returns (new_system, occupations sorted by |n| desc)."""
+    eps = np.asarray(system["eps"], dtype=np.float64)
+    B = np.asarray(system["B"])
+    mu = np.asarray(system["mu"])
+    O = system["O"]
+    M = fnspp_density(eps, B, mu, O, omega, plus_omega)
+    n, Vn = np.linalg.eigh(M)
+    keep = select(n, by_count, value)
+    Vt = Vn[:, keep]
+    Ft = Vt.conj().T @ np.diag(eps[O:]) @ Vt
+    et, Z = np.linalg.eigh(Ft)
+    U = Vt @ Z
+    N, Vk = eps.shape[0], U.shape[1]
+    Uf = np.zeros((N, O + Vk), dtype=np.complex128)
+    Uf[:O, :O] = np.eye(O)
+    Uf[O:, O:] = U
+    Bn = np.einsum('pr,lpq,qs->lrs', Uf.conj(), B, Uf, optimize=True)
+    mun = np.einsum('pr,cpq,qs->crs', Uf.conj(), mu, Uf, optimize=True)
+    new = dict(system)
+    new.update(V=Vk, N=O + Vk, eps=np.concatenate([eps[:O], et]), B=Bn, mu=mun)
+    occ = np.abs(n[np.argsort(-np.abs(n), kind='stable')])
+    return new, occ, dict(M=M, n=n, U=U)

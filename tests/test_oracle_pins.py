@@ -1,0 +1,281 @@
+"""Pins of the CPU oracle against what the theory fixes (no GPU needed).
+
+Each check compares the oracle with something other than itself:
+brute-force second quantisation, FCI and sum-over-states, closed forms,
+polynomial exactness of finite differences, invariances.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import ccsd, fci, fns
+
+
+def _herm(rng, n, s):
+    g = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return s * (g + g.conj().T)
+
+
+def _random_x(lay, seed, scale):
+    a = synth.random_amplitudes(lay.O, lay.V, 1, seed=seed, scale=scale)
+    return lay.join(torch.as_tensor(a["t1"][0]), torch.as_tensor(a["t2u"][0]))
+
+
+# --- P5: residual and energy against the determinant-space projection -------
+
+@pytest.mark.parametrize("O,V,L,seed", [(2, 4, 6, 1), (3, 5, 12, 7), (4, 5, 9, 3)])
+def test_residual_matches_bruteforce_projection(O, V, L, seed):
+    """R_mu = <mu|e^-T H e^T|0> (Eq. 9-10) for random T and a non-canonical
+    Hermitian Fock matrix, against the explicit determinant-space series."""
+    s = synth.make_system(O, V, L, seed=seed)
+    rng = np.random.default_rng(seed + 100)
+    f = ccsd.fock_of(s) + _herm(rng, O + V, 0.05)
+    model = ccsd.CCModel(ccsd.Hamiltonian(f, O, s["B"]))
+    x = _random_x(model.lay, seed + 5, 0.2)
+    t1, t2 = model.lay.full(x)
+    R1, R2 = ccsd.residual_full(t1, t2, model.H)
+    E = complex(ccsd.energy_full(t1, t2, model.H))
+    Eb, R1b, R2b, _ = fci.cc_projections(f, s["B"], O, t1.numpy(), t2.numpy())
+    scale = max(np.abs(R1b).max(), np.abs(R2b).max())
+    assert np.abs(R1.numpy() - R1b).max() < 1e-13 * scale
+    assert np.abs(R2.numpy() - R2b).max() < 1e-13 * scale
+    assert abs(E - Eb) < 1e-13 * max(1.0, abs(Eb))
+
+
+def test_one_body_residual_is_xi():
+    """xi = <nu|e^-T A e^T|0> (Eq. 31): the residual with f -> A and no
+    two-body part equals the brute-force projection of the one-body operator."""
+    O, V = 3, 4
+    s = synth.make_system(O, V, 5, seed=2)
+    A = s["mu"][1]
+    m = ccsd.dipole_model(s, 1)
+    x = _random_x(m.lay, 8, 0.3)
+    t1, t2 = m.lay.full(x)
+    R1, R2 = ccsd.residual_full(t1, t2, m.H)
+    zeroB = np.zeros_like(s["B"])
+    _, R1b, R2b, _ = fci.cc_projections(A, zeroB, O, t1.numpy(), t2.numpy())
+    assert np.abs(R1.numpy() - R1b).max() < 1e-13
+    assert np.abs(R2.numpy() - R2b).max() < 1e-13
+
+
+@pytest.mark.parametrize("mutation", ["real_driver", "transpose_ovvv", "flip_vvvo", "drop_pab"])
+def test_bruteforce_detects_planted_mistakes(mutation, monkeypatch):
+    """A plausible mistake planted in the oracle (the real-spinor driver
+    <ij||ab>, a transposed operand, a sign, a dropped antisymmetriser) makes
+    the brute-force pin fail, so the pin is sensitive to such errors."""
+    O, V = 3, 4
+    s = synth.make_system(O, V, 6, seed=4)
+    rng = np.random.default_rng(9)
+    f = ccsd.fock_of(s) + _herm(rng, O + V, 0.05)
+    H = ccsd.Hamiltonian(f, O, s["B"])
+    if mutation == "real_driver":
+        H.vvoo = H.oovv.permute(2, 3, 0, 1)
+    elif mutation == "transpose_ovvv":
+        H.ovvv = H.ovvv.transpose(2, 3).contiguous()
+    elif mutation == "flip_vvvo":
+        H.vvvo = -H.vvvo
+    elif mutation == "drop_pab":
+        monkeypatch.setattr(ccsd, "_Pab", lambda x: x)
+    model = ccsd.CCModel(H)
+    x = _random_x(model.lay, 3, 0.2)
+    t1, t2 = model.lay.full(x)
+    R1, R2 = ccsd.residual_full(t1, t2, model.H)
+    _, R1b, R2b, _ = fci.cc_projections(f, s["B"], O, t1.numpy(), t2.numpy())
+    err = max(np.abs(R1.numpy() - R1b).max(), np.abs(R2.numpy() - R2b).max())
+    assert err > 1e-6
+
+
+# --- P1: two electrons, CCSD is exact ---------------------------------------
+
+def test_two_electron_ccsd_equals_fci_and_sos():
+    cfg = synth.CONFIGS["c1b"]
+    s = synth.make_system(cfg["O"], cfg["V"], cfg["L"], cfg["seed"])
+    model = ccsd.build(s)
+    t, E, _ = ccsd.solve_ccsd(model)
+    lam, _ = ccsd.solve_lambda(model, t)
+    Efci, _, _, _, eref = fci.fci_states(ccsd.fock_of(s), s["B"], s["O"])
+    assert abs(complex(E) - (Efci[0] - eref)) < 1e-10
+    oms = list(cfg["omegas"])
+    a_lr = ccsd.polarizability(s, (0, 1, 2), oms, ground=(t, E, lam))
+    a_sos, _, wmin = fci.sos_polarizability(ccsd.fock_of(s), s["B"], s["mu"], s["O"], (0, 1, 2), oms)
+    assert max(oms) < wmin
+    assert np.abs(a_lr - a_sos).max() < 1e-9 * np.abs(a_sos).max()
+
+
+def test_noninteracting_response_closed_form():
+    """Without two-electron terms T = 0 and alpha is the independent-particle
+    sum over (i, a): A_ia B_ai/(d - w) + B_ia A_ai/(d + w), d = e_a - e_i.
+    Checks both the determinant-space SOS and the LR-CC expression of Eq. 35."""
+    O, V = 2, 5
+    s = synth.make_system(O, V, 4, seed=6)
+    s0 = dict(s)
+    s0["B"] = np.zeros_like(s["B"])
+    oms = [0.0, 0.1]
+    comps = (0, 2)
+    eps, mu = s["eps"], s["mu"]
+    d = eps[O:][None, :] - eps[:O][:, None]
+    ref = np.zeros((2, 2, 2), dtype=np.complex128)
+    for wi, w in enumerate(oms):
+        for a, A in enumerate(comps):
+            for b, Bc in enumerate(comps):
+                Aia, Aai = mu[A][:O, O:], mu[A][O:, :O].T
+                Bia, Bai = mu[Bc][:O, O:], mu[Bc][O:, :O].T
+                ref[wi, a, b] = np.sum(Aia * Bai / (d - w) + Bia * Aai / (d + w))
+    sos, E0, _ = fci.sos_polarizability(ccsd.fock_of(s), s0["B"], mu, O, comps, oms)
+    assert abs(E0 - eps[:O].sum()) < 1e-12
+    assert np.abs(sos - ref).max() < 1e-12 * np.abs(ref).max()
+    lr = ccsd.polarizability(s0, comps, oms)
+    assert np.abs(lr - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+# --- P2: MP2 is the first Jacobi step ---------------------------------------
+
+def test_first_iteration_is_mp2():
+    O, V, L = 4, 9, 20
+    s = synth.make_system(O, V, L, seed=3)
+    model = ccsd.build(s)
+    x1, E1 = ccsd.mp2(model)
+    B, eps = s["B"], s["eps"]
+    # closed form with the integrals built element by element
+    e = 0.0
+    for i in range(O):
+        for j in range(O):
+            for a in range(O, O + V):
+                for b in range(O, O + V):
+                    v = np.sum(B[:, a, i] * B[:, b, j]) - np.sum(B[:, a, j] * B[:, b, i])
+                    e -= abs(v) ** 2 / (eps[a] + eps[b] - eps[i] - eps[j])
+    e *= 0.25
+    assert abs(complex(E1).imag) < 1e-15
+    assert e < 0
+    assert abs(complex(E1).real - e) < 1e-13 * abs(e)
+    t1, _ = model.lay.split(x1)
+    assert float(t1.abs().max()) == 0.0           # canonical reference: f_ai = 0
+    assert abs(fns.mp2_energy(eps, B, O) - e) < 1e-13 * abs(e)
+
+
+# --- derivatives: exact polynomial stencils, bilinear identity ---------------
+
+def test_torch_complex_conventions():
+    c = torch.tensor(0.3 - 0.7j, dtype=torch.complex128)
+    z = torch.tensor([1.0 + 2.0j], dtype=torch.complex128)
+    v = torch.tensor([0.5 + 0.25j], dtype=torch.complex128)
+    f = lambda y: c * y * y
+    _, j = torch.func.jvp(f, (z,), (v,))
+    assert torch.allclose(j, 2 * c * z * v)
+    _, g = torch.func.vjp(f, z)
+    assert torch.allclose(g(v.conj())[0].conj(), 2 * c * z * v)
+
+
+def _stencil(fun, x, d, h):
+    return (-fun(x + 2 * h * d) + 8 * fun(x + h * d) - 8 * fun(x - h * d) + fun(x - 2 * h * d)) / (12 * h)
+
+
+def test_jacobian_products_are_exact_derivatives():
+    """R is a polynomial of degree <= 4 in t, so the 5-point stencil is exact
+    for any step; A X (Eq. 30) must match it.  The bilinear identity
+    u.(A^T l) = l.(A u) pins the transpose (left) product, and F X (Eq. 34)
+    is the exact stencil of the Lagrangian gradient (degree <= 3)."""
+    s = synth.make_system(3, 6, 10, seed=5)
+    model = ccsd.build(s)
+    t, _, _ = ccsd.solve_ccsd(model)
+    u = _random_x(model.lay, 1, 0.3)
+    lam = _random_x(model.lay, 2, 0.3)
+    Au = model.jvp(t, u)
+    for h in (0.5, 1.0):
+        st = _stencil(model.R, t, u, h)
+        assert float((Au - st).abs().max()) < 1e-13 * float(Au.abs().max())
+    ATl = model.vjp(t, lam)
+    lhs, rhs = complex(torch.sum(u * ATl)), complex(torch.sum(lam * Au))
+    assert abs(lhs - rhs) < 1e-13 * abs(rhs)
+    FX = model.FX(t, lam, u)
+    st = _stencil(lambda y: model.lagrangian_grad(y, lam), t, u, 0.5)
+    assert float((FX - st).abs().max()) < 1e-12 * float(FX.abs().max())
+
+
+# --- P3: finite field --------------------------------------------------------
+
+def test_static_alpha_equals_finite_field():
+    """g_AA(0) = d^2 E_CCSD/dF^2 with f -> f + F mu_A (orbital-unrelaxed),
+    complex values, 5-point second difference with Richardson extrapolation."""
+    s = synth.make_system(3, 8, 16, seed=11)
+    _, P = ccsd.polarizability(s, (2,), [0.0], tol=1e-12, return_parts=True)
+    X, Y = P["parts"][0.0]["X"][2], P["parts"][0.0]["Y"][2]
+    g = complex(torch.sum(Y * P["xi"][2]) + torch.sum(P["eta"][2] * X))
+
+    def d2(h):
+        E = [complex(ccsd.field_energy(s, 2, k * h)) for k in (-2, -1, 0, 1, 2)]
+        return (-E[0] + 16 * E[1] - 30 * E[2] + 16 * E[3] - E[4]) / (12 * h * h)
+
+    rich = (16 * d2(1e-3) - d2(2e-3)) / 15
+    assert abs(rich - g) < 1e-8 * abs(g)
+
+
+# --- P4: integral symmetries --------------------------------------------------
+
+def test_integral_symmetries():
+    s = synth.make_system(3, 5, 7, seed=8)
+    B, mu = s["B"], s["mu"]
+    assert np.array_equal(B, B.conj().transpose(0, 2, 1))
+    assert np.array_equal(mu, mu.conj().transpose(0, 2, 1))
+    g = fci.full_antisym(B)
+    assert np.abs(g + g.transpose(1, 0, 2, 3)).max() < 1e-15
+    assert np.abs(g + g.transpose(0, 1, 3, 2)).max() < 1e-15
+    assert np.abs(g - g.transpose(2, 3, 0, 1).conj()).max() < 1e-15
+    # no real 8-fold symmetry for complex spinors
+    assert np.abs(g - g.transpose(2, 1, 0, 3)).max() > 1e-3
+
+
+# --- P6: FNS++ ----------------------------------------------------------------
+
+def test_fnspp_untruncated_and_rotation_invariance():
+    O, V = 3, 7
+    s = synth.make_system(O, V, 16, seed=12)
+    oms = [0.0, 0.05]
+    a_full = ccsd.polarizability(s, (0, 1, 2), oms)
+    new, occ, info = fns.truncate(s, True, V)
+    a_tr = ccsd.polarizability(new, (0, 1, 2), oms)
+    assert np.abs(a_full - a_tr).max() < 1e-10 * np.abs(a_full).max()
+    # random (non-semicanonical) unitary virtual rotation: general-f path
+    U = synth.random_unitary(V, 3)
+    Uf = np.eye(O + V, dtype=np.complex128)
+    Uf[O:, O:] = U
+    s3 = dict(s)
+    s3["B"] = np.einsum('pr,lpq,qs->lrs', Uf.conj(), s["B"], Uf)
+    s3["mu"] = np.einsum('pr,cpq,qs->crs', Uf.conj(), s["mu"], Uf)
+    f3 = Uf.conj().T @ ccsd.fock_of(s) @ Uf
+    m3 = ccsd.CCModel(ccsd.Hamiltonian(f3, O, s3["B"]))
+    t3, E3, _ = ccsd.solve_ccsd(m3)
+    _, E0, _ = ccsd.solve_ccsd(ccsd.build(s))
+    assert abs(complex(E3) - complex(E0)) < 1e-11
+
+
+def test_fnspp_density_properties():
+    O, V = 3, 9
+    s = synth.make_system(O, V, 12, seed=13)
+    M = fns.fnspp_density(s["eps"], s["B"], s["mu"], O)
+    assert np.abs(M - M.conj().T).max() < 1e-15 * np.abs(M).max() * 10
+    n, Vn = np.linalg.eigh(M)
+    assert n.min() > -1e-14 * n.max()                     # PSD under the conj reading
+    assert np.abs(M @ Vn - Vn * n).max() < 1e-12 * np.abs(n).max()
+    # Abar equals xi^A at T1 = 0, T2 = MP2 (reading of Eq. 47-48)
+    model = ccsd.build(s)
+    x1, _ = ccsd.mp2(model)
+    t2 = fns.mp2_doubles(s["eps"], s["B"], O)
+    _, t2x = model.lay.full(x1)
+    assert np.abs(t2 - t2x.numpy()).max() < 1e-14
+    Hii, Haa = fns.hbar_diagonals(s["eps"], s["B"], O, t2)
+    zero = np.zeros(V)
+    A1, A2 = fns.first_order_amplitudes(s["eps"], s["B"], s["mu"][0], O, t2,
+                                        np.zeros(O), zero + 1.0, 0.0)
+    xi = ccsd.dipole_model(s, 0).R(x1)
+    xi1, xi2 = model.lay.full(xi)
+    d2 = 2.0  # Haa + Hbb - Hii - Hjj with Haa = 1, Hii = 0
+    assert np.abs(A1 * 1.0 - xi1.numpy()).max() < 1e-14
+    assert np.abs(A2 * d2 - xi2.numpy()).max() < 1e-14
+    # trace of the kept subspace + discarded = trace(M)
+    new, occ, info = fns.truncate(s, True, 4)
+    assert abs(np.sum(occ) - np.trace(M).real) < 1e-14 * abs(np.trace(M))
+    assert new["V"] == 4 and new["B"].shape == (12, O + 4, O + 4)
+    Bn = new["B"]
+    assert np.abs(Bn - Bn.conj().transpose(0, 2, 1)).max() < 1e-15
