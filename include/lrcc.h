@@ -1,0 +1,202 @@
+/*
+ * lrcc.h -- C ABI of a single-GPU (GB300, sm_103a) four-component LR-CCSD
+ * polarizability library in a truncated natural-spinor (FNS++) basis.
+ *
+ * Method: Chakraborty, Manna, Crawford, Dutta, "A low-cost four-component
+ * relativistic coupled cluster linear response theory based on perturbation
+ * sensitive natural spinors", arXiv:2503.23144.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Complex numbers are interleaved (re, im) doubles, layout-compatible with
+ *    C99 `double _Complex` and `std::complex<double>`.  Arrays are row-major.
+ *  - Spinor index p runs over N = O + V spinors, occupied first.
+ *  - The Hamiltonian is given in the molecular-spinor basis: orbital energies
+ *    eps[N] (canonical reference, Fock matrix = diag(eps)), a Hermitian
+ *    three-index factor B[L][N][N] with <pq|rs> = sum_L B^L_pr B^L_qs
+ *    (Sec. II.A, Eq. 7-8 in the no-pair approximation), and Hermitian
+ *    perturbation matrices mu[ncomp][N][N] (dipole components).
+ *  - Amplitude vectors (t, lambda, X, Y, residuals) are passed as a singles
+ *    block [O][V] followed by a FULL antisymmetric doubles block [O][O][V][V]
+ *    (t_ij^ab = -t_ji^ab = -t_ij^ba; Eq. 3-4).  Dot products between such
+ *    vectors run over unique amplitudes (sum_ia + sum_{i<j,a<b}).
+ *  - Host pointers are owned by the caller; the library copies what it needs.
+ *    Device memory is owned by the context.  Every call returns a status and
+ *    never throws; lrcc_last_error() gives a message for the last failure.
+ *  - One context per host thread.  Calls on a context run on its stream in
+ *    order; host-pointer calls synchronise before returning.
+ */
+#ifndef LRCC_H
+#define LRCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lrcc_ctx lrcc_ctx;
+
+typedef enum {
+    LRCC_OK = 0,
+    LRCC_EINVAL = 1,    /* bad argument: shape, Hermiticity, ordering, range   */
+    LRCC_ENOMEM = 2,    /* device allocation failed                            */
+    LRCC_ENOCONV = 3,   /* iteration cap reached or residual not finite        */
+    LRCC_ETIMEOUT = 4,  /* a device wait gave up (kernel-side bounded spin)    */
+    LRCC_ECUDA = 5,     /* CUDA runtime / driver / library error               */
+    LRCC_ESTATE = 6     /* call out of order (e.g. solve before ground state)  */
+} lrcc_status;
+
+typedef enum {
+    LRCC_FP64 = 0,          /* every contraction in FP64                        */
+    LRCC_MIXED_TF32 = 1,    /* ladder/ring on tcgen05 kind::tf32, FP64 refine   */
+    LRCC_MIXED_BF16X3 = 2   /* ladder/ring as 3 bf16 products, FP64 refine      */
+} lrcc_precision;
+
+typedef struct {
+    double r_tol;          /* max |residual| for T, Lambda (default 1e-10)        */
+    double x_tol;          /* max |residual| for X, Y (default 1e-9)              */
+    int max_iter;          /* per solve (default 200)                             */
+    int diis_size;         /* Pulay subspace per right-hand side (default 8)      */
+    int rhs_chunk;         /* right-hand sides per batched solve (default 12)     */
+    lrcc_precision prec;   /* contraction precision of the response solves        */
+    double inner_tol;      /* mixed mode: relative residual drop per inner solve  */
+    int plus_omega;        /* FNS++ denominator Dbar + omega (Eq. 46 as printed)
+                              instead of Dbar - omega (diagonal of Eq. 29)        */
+    int slab_rows;         /* ladder: (a<b) rows per assembled <ab||ef> slab; 0 = auto */
+} lrcc_options;
+
+/* Fill *opt with the defaults above. */
+void lrcc_default_options(lrcc_options* opt);
+
+/*
+ * lrcc_setup -- create a context for one spinor Hamiltonian (Sec. II.A).
+ *   eps  [N]            host, real orbital energies, occupied first; every
+ *                       occupied energy must be below every virtual one.
+ *   B    [L][N][N]      host, complex interleaved, Hermitian per L to
+ *                       1e-12 * max|B| (else LRCC_EINVAL).
+ *   mu   [ncomp][N][N]  host, complex interleaved, Hermitian (ncomp 1..3).
+ *   O, V, L             sizes; N = O + V; O >= 2, V >= 2.
+ *   opt                 may be NULL (defaults).
+ *   out                 receives the context; NULL on failure.
+ * Copies all inputs to the device and builds the integral blocks
+ * <pq||rs> = <pq|rs> - <pq|sr> that the residual needs (never the
+ * <ab||ef> block, which the ladder assembles on the fly from B).
+ */
+lrcc_status lrcc_setup(const double* eps, const double* B, int L, const double* mu, int ncomp,
+                       int O, int V, const lrcc_options* opt, lrcc_ctx** out);
+
+/* Release all device memory of the context.  NULL is allowed. */
+void lrcc_destroy(lrcc_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failing
+ * lrcc_setup when ctx is NULL).  Never NULL. */
+const char* lrcc_last_error(const lrcc_ctx* ctx);
+
+/*
+ * lrcc_ccsd_ground -- solve the CCSD amplitude equations R(T) = 0 (Eq. 9-10)
+ * and the left-CCSD equations lambda A + dE/dT = 0 (Lambda of Eq. 20, 33-35).
+ *   e_corr[2]  out, complex CCSD correlation energy (Re = energy, Im = diagnostic).
+ *   iters_T, iters_L  out, iteration counts (may be NULL).
+ * Returns LRCC_ENOCONV if either solve hits max_iter.
+ */
+lrcc_status lrcc_ccsd_ground(lrcc_ctx* ctx, double e_corr[2], int* iters_T, int* iters_L);
+
+/*
+ * lrcc_fns_truncate -- FNS++ (Sec. II.C, Eq. 39-50 with Eq. 41-44).
+ * Call after lrcc_setup and before lrcc_ccsd_ground.  Builds the MP2 doubles,
+ * the Hbar diagonals (Eq. 49-50), first-order perturbed amplitudes for every
+ * dipole component (Eq. 46-48), the component-averaged perturbation-sensitive
+ * virtual density (Eq. 45), its eigenvectors (natural spinors, Eq. 41), keeps
+ * them by |occupation| descending, semicanonicalises (Eq. 42-44), and
+ * replaces the context's virtual space, B, mu and eps by the rotated ones.
+ *   by_count       1: keep the first round(value) natural spinors;
+ *                  0: keep every one with |n| >= value.
+ *   omega          frequency of the perturbed amplitudes.
+ *   v_kept         out, new V (may be NULL).
+ *   occ_out [V]    out, |n| sorted descending over the ORIGINAL V (may be NULL).
+ */
+lrcc_status lrcc_fns_truncate(lrcc_ctx* ctx, int by_count, double value, double omega,
+                              int* v_kept, double* occ_out);
+
+/*
+ * lrcc_solve -- polarisabilities alpha_AB(omega) = -<<A;B>>_omega (Eq. 35):
+ * for every omega and every component B in comps, X^B from (A - omega) X = -xi
+ * (Eq. 29-31) and Y^B from Y (A + omega) = -(eta + F X) (Eq. 32-34); then
+ * g_AB = Y^B . xi^A + eta^A . X^B and alpha_AB = -(g_AB + conj g_BA)/2.
+ * Right-hand sides (component, omega) are batched rhs_chunk at a time.
+ *   omegas [n_w]                 host, real frequencies (Hartree).
+ *   comps  [n_c]                 host, component indices into mu (0..ncomp-1).
+ *   alpha  [n_w][n_c][n_c] cplx  out, host, Re = polarisability.
+ *   err_est [n_w][n_c]           out (may be NULL): final max |residual| of X
+ *                                and Y combined, per right-hand side.
+ * Requires lrcc_ccsd_ground first (else LRCC_ESTATE).
+ */
+lrcc_status lrcc_solve(lrcc_ctx* ctx, const double* omegas, int n_w, const int* comps, int n_c,
+                       double* alpha, double* err_est);
+
+/* Kinds of lrcc_residual. */
+typedef enum {
+    LRCC_RES_T = 0,        /* out = R(in)  (CCSD residual, Eq. 9-10)          */
+    LRCC_RES_SIGMA = 1,    /* out = A(T) in  (Jacobian product, Eq. 30)       */
+    LRCC_RES_VJP = 2,      /* out = A(T)^T in (holomorphic transpose)         */
+    LRCC_RES_XI = 3,       /* out = xi^comp = <nu|e^-T mu e^T|0> (Eq. 31); in = T */
+    LRCC_RES_ENERGY = 4,   /* out[r][0..1] = E_corr(in_r)                    */
+    LRCC_RES_VJP_FULL = 5  /* out = P J(P t)^T in: adjoint of T -> R(P T) with
+                              every full-array entry independent; P projects
+                              the doubles block onto its antisymmetric part.
+                              This is the map whose conjugate PyTorch's
+                              complex autograd expects.                       */
+} lrcc_residual_kind;
+
+/*
+ * lrcc_residual -- test hook.  Evaluates one residual-type map on R
+ * right-hand sides at once.
+ *   kind     see lrcc_residual_kind.  The doubles blocks of `t` and `in`
+ *            are first projected onto their antisymmetric part (a no-op for
+ *            antisymmetric inputs), so every kind is defined for any array.
+ *   t        host [O*V + O*O*V*V] complex: the amplitudes T at which
+ *            SIGMA / VJP are linearised (ignored for T, ENERGY, XI).
+ *   in       host [R][O*V + O*O*V*V] complex.
+ *   R        number of right-hand sides (>= 1).
+ *   comp     dipole component for XI.
+ *   prec     precision of the contractions (LRCC_FP64 or a mixed mode).
+ *   out      host, same shape as in (ENERGY: [R][2]).
+ */
+lrcc_status lrcc_residual(lrcc_ctx* ctx, int kind, const double* t, const double* in, int R,
+                          int comp, int prec, double* out);
+
+/*
+ * Device-pointer variants for the PyTorch binding: same semantics, but every
+ * array argument is a device pointer on the context's device and the call is
+ * stream-ordered on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * The call does not synchronise; outputs are valid in stream order.
+ */
+lrcc_status lrcc_residual_dev(lrcc_ctx* ctx, int kind, const double* t_dev, const double* in_dev,
+                              int R, int comp, int prec, double* out_dev, void* stream);
+
+/*
+ * lrcc_ladder_dev -- the particle-particle ladder alone (the dominant
+ * contraction of the doubles residual, Eq. 9-10 / 30):
+ *   Z_ij^ab = 1/2 sum_ef <ab||ef> X_ij^ef,   <ab|ef> = sum_L B^L_ae B^L_bf,
+ * for X antisymmetric in (i,j) and in (e,f).
+ *   x_dev  [R][O][O][V][V] complex, device.
+ *   z_dev  [R][O][O][V][V] complex, device, overwritten (antisymmetric).
+ *   transpose  0: the map above; 1: its holomorphic transpose (B -> B^T).
+ *   prec   LRCC_FP64, LRCC_MIXED_TF32 or LRCC_MIXED_BF16X3.
+ */
+lrcc_status lrcc_ladder_dev(lrcc_ctx* ctx, const double* x_dev, double* z_dev, int R,
+                            int transpose, int prec, void* stream);
+
+/* Device timing of the last lrcc_solve / lrcc_ccsd_ground phases (ms):
+ * [0] ground T, [1] Lambda, [2] xi/eta, [3] X, [4] F.X, [5] Y, [6] alpha. */
+lrcc_status lrcc_phase_times(const lrcc_ctx* ctx, double* ms7);
+
+/* Number of kernels this library launched on ctx since creation. */
+int64_t lrcc_kernel_launches(const lrcc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRCC_H */

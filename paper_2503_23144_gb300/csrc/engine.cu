@@ -1,0 +1,357 @@
+// Contraction engine: einsum-style tensor contractions mapped onto one
+// strided batched complex GEMM (transpose copies only where an index group is
+// not flattenable in place), label-driven permuted axpby, and the
+// particle-particle ladder built from the three-index factor.
+#include "lrcc_internal.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace {
+
+struct Spec {
+    std::string a, b, c;
+};
+
+Spec parse(const std::string& s) {
+    Spec sp;
+    size_t comma = s.find(','), arrow = s.find("->");
+    if (comma == std::string::npos || arrow == std::string::npos || comma > arrow)
+        throw LrccError(LRCC_EINVAL, "bad einsum spec: " + s);
+    sp.a = s.substr(0, comma);
+    sp.b = s.substr(comma + 1, arrow - comma - 1);
+    sp.c = s.substr(arrow + 2);
+    return sp;
+}
+
+struct Group {
+    std::vector<char> labels;
+};
+
+// position of label in a string, -1 if absent
+inline int pos(const std::string& s, char c) {
+    size_t p = s.find(c);
+    return p == std::string::npos ? -1 : (int)p;
+}
+
+// order labels by decreasing stride in tensor T (labels string lab)
+std::vector<char> order_by(const std::vector<char>& g, const Tensor& T, const std::string& lab) {
+    std::vector<char> o = g;
+    std::stable_sort(o.begin(), o.end(), [&](char x, char y) {
+        return T.s[pos(lab, x)] > T.s[pos(lab, y)];
+    });
+    return o;
+}
+
+// can labels (in this order) be flattened to one index of T? -> size, stride
+bool flat(const Tensor& T, const std::string& lab, const std::vector<char>& order, int64_t& size, int64_t& stride) {
+    size = 1;
+    stride = 0;
+    int64_t prev_s = -1, prev_d = -1;
+    bool first = true;
+    for (char c : order) {
+        int k = pos(lab, c);
+        int64_t d = T.d[k], s = T.s[k];
+        size *= d;
+        if (d == 1) continue;
+        if (!first && prev_s != s * d) return false;
+        prev_s = s;
+        prev_d = d;
+        stride = s;
+        first = false;
+    }
+    (void)prev_d;
+    return true;
+}
+
+// contiguous copy of T with labels permuted into `want` order
+Tensor copy_as(Dev& D, const Tensor& T, const std::string& lab, const std::string& want, bool conj) {
+    std::vector<int> perm(want.size());
+    std::vector<int64_t> shape(want.size());
+    for (size_t k = 0; k < want.size(); ++k) {
+        perm[k] = pos(lab, want[k]);
+        shape[k] = T.d[perm[k]];
+    }
+    Tensor out = empty(D, shape);
+    axpby(D, mkc(1.0), T.permute(perm), conj, mkc(0.0), out);
+    return out;
+}
+
+std::string cat(const std::vector<char>& a, const std::vector<char>& b, const std::vector<char>& c) {
+    std::string s;
+    for (char x : a) s += x;
+    for (char x : b) s += x;
+    for (char x : c) s += x;
+    return s;
+}
+
+}  // namespace
+
+void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA, const Tensor& B0, bool cB,
+         cplx beta, Tensor& C, int prec) {
+    Spec sp = parse(spec);
+    if ((int)sp.a.size() != A0.nd || (int)sp.b.size() != B0.nd || (int)sp.c.size() != C.nd)
+        throw LrccError(LRCC_EINVAL, "einsum rank mismatch: " + spec);
+    std::vector<char> gb, gm, gn, gk;
+    auto dim_of = [&](char c) -> int64_t {
+        int pa = pos(sp.a, c), pb = pos(sp.b, c), pc = pos(sp.c, c);
+        int64_t d = -1;
+        if (pa >= 0) d = A0.d[pa];
+        if (pb >= 0) { if (d >= 0 && d != B0.d[pb]) throw LrccError(LRCC_EINVAL, "einsum dim mismatch: " + spec); d = B0.d[pb]; }
+        if (pc >= 0) { if (d >= 0 && d != C.d[pc]) throw LrccError(LRCC_EINVAL, "einsum dim mismatch: " + spec); d = C.d[pc]; }
+        return d;
+    };
+    std::string all = sp.a + sp.b + sp.c;
+    std::string seen;
+    for (char c : all) {
+        if (seen.find(c) != std::string::npos) continue;
+        seen += c;
+        bool ia = pos(sp.a, c) >= 0, ib = pos(sp.b, c) >= 0, ic = pos(sp.c, c) >= 0;
+        if (std::count(sp.a.begin(), sp.a.end(), c) > 1 || std::count(sp.b.begin(), sp.b.end(), c) > 1 ||
+            std::count(sp.c.begin(), sp.c.end(), c) > 1)
+            throw LrccError(LRCC_EINVAL, "repeated label in one operand: " + spec);
+        dim_of(c);
+        if (ia && ib && ic) gb.push_back(c);
+        else if (ia && ic) gm.push_back(c);
+        else if (ib && ic) gn.push_back(c);
+        else if (ia && ib) gk.push_back(c);
+        else throw LrccError(LRCC_EINVAL, "label in one operand only: " + spec);
+    }
+    Tensor A = A0, B = B0;
+    std::string la = sp.a, lb = sp.b;
+    bool ca = cA, cb = cB;
+    // group orders: follow C when C can be used in place
+    std::vector<char> ob = order_by(gb, C, sp.c), om = order_by(gm, C, sp.c), on = order_by(gn, C, sp.c);
+    int64_t sz, st;
+    bool c_ok = flat(C, sp.c, ob, sz, st) && flat(C, sp.c, om, sz, st) && flat(C, sp.c, on, sz, st);
+    if (!c_ok) {
+        ob = order_by(gb, A, la);
+        om = order_by(gm, A, la);
+        on = order_by(gn, B, lb);
+    }
+    std::vector<char> ok_ = order_by(gk, A, la);
+    int64_t Mb, sAb, M, sAm, K, sAk;
+    bool a_ok = flat(A, la, ob, Mb, sAb) && flat(A, la, om, M, sAm) && flat(A, la, ok_, K, sAk);
+    if (!a_ok) {
+        std::string want = cat(ob, om, ok_);
+        A = copy_as(D, A, la, want, ca);
+        la = want;
+        ca = false;
+        flat(A, la, ob, Mb, sAb);
+        flat(A, la, om, M, sAm);
+        flat(A, la, ok_, K, sAk);
+    }
+    int64_t Nb, sBb, N, sBn, K2, sBk;
+    bool b_ok = flat(B, lb, ob, Nb, sBb) && flat(B, lb, ok_, K2, sBk) && flat(B, lb, on, N, sBn);
+    if (!b_ok) {
+        std::string want = cat(ob, ok_, on);
+        B = copy_as(D, B, lb, want, cb);
+        lb = want;
+        cb = false;
+        flat(B, lb, ob, Nb, sBb);
+        flat(B, lb, ok_, K2, sBk);
+        flat(B, lb, on, N, sBn);
+    }
+    GemmArgs g;
+    g.M = M; g.N = N; g.K = K; g.batch = Mb;
+    g.A = A.p; g.sAb = sAb; g.sAm = sAm; g.sAk = sAk; g.cA = ca;
+    g.B = B.p; g.sBb = sBb; g.sBk = sBk; g.sBn = sBn; g.cB = cb;
+    Tensor Ct;
+    std::string lc = cat(ob, om, on);
+    if (c_ok) {
+        int64_t b_, m_, n_;
+        flat(C, sp.c, ob, b_, g.sCb);
+        flat(C, sp.c, om, m_, g.sCm);
+        flat(C, sp.c, on, n_, g.sCn);
+        g.C = C.p;
+        g.alpha = alpha;
+        g.beta = beta;
+    } else {
+        std::vector<int64_t> shape;
+        for (char c : lc) shape.push_back(dim_of(c));
+        Ct = empty(D, shape);
+        int64_t b_, m_, n_;
+        flat(Ct, lc, ob, b_, g.sCb);
+        flat(Ct, lc, om, m_, g.sCm);
+        flat(Ct, lc, on, n_, g.sCn);
+        g.C = Ct.p;
+        g.alpha = mkc(1.0);
+        g.beta = mkc(0.0);
+    }
+    if (g.batch == 1) { g.sAb = g.sBb = g.sCb = 0; }
+    double flops = 8.0 * double(g.M) * double(g.N) * double(g.K) * double(g.batch);
+    bool tc = prec != LRCC_FP64 && gemm_tc_available() && flops > 2e9 && g.M >= 64 && g.N >= 32 && g.K >= 32;
+    if (tc) gemm_tc(D, g, prec);
+    else gemm_f64(D, g);
+    if (!c_ok) perm_axpby(D, lc + "->" + sp.c, alpha, Ct, beta, C);
+}
+
+Tensor ein_new(Dev& D, const std::string& spec, cplx alpha, const Tensor& A, bool cA, const Tensor& B, bool cB,
+               int prec) {
+    Spec sp = parse(spec);
+    std::vector<int64_t> shape;
+    for (char c : sp.c) {
+        int pa = pos(sp.a, c), pb = pos(sp.b, c);
+        if (pa >= 0) shape.push_back(A.d[pa]);
+        else if (pb >= 0) shape.push_back(B.d[pb]);
+        else throw LrccError(LRCC_EINVAL, "output label not in inputs: " + spec);
+    }
+    Tensor C = empty(D, shape);
+    ein(D, spec, alpha, A, cA, B, cB, mkc(0.0), C, prec);
+    return C;
+}
+
+void perm_axpby(Dev& D, const std::string& spec, cplx alpha, const Tensor& x, cplx beta, Tensor& y) {
+    size_t arrow = spec.find("->");
+    std::string lx = spec.substr(0, arrow), ly = spec.substr(arrow + 2);
+    if ((int)lx.size() != x.nd || (int)ly.size() != y.nd || lx.size() != ly.size())
+        throw LrccError(LRCC_EINVAL, "perm spec rank mismatch: " + spec);
+    std::vector<int> perm(ly.size());
+    for (size_t k = 0; k < ly.size(); ++k) {
+        perm[k] = pos(lx, ly[k]);
+        if (perm[k] < 0) throw LrccError(LRCC_EINVAL, "perm spec label mismatch: " + spec);
+    }
+    axpby(D, alpha, x.permute(perm), false, beta, y);
+}
+
+// ---------------------------------------------------------------------------
+// ladder
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ inline void pair_decode(int64_t k, int64_t n, int64_t& p, int64_t& q) {
+    double a = double(2 * n - 1);
+    double disc = a * a - 8.0 * double(k);
+    int64_t pp = (int64_t)floor((a - sqrt(fmax(disc, 0.0))) * 0.5);
+    if (pp < 0) pp = 0;
+    while (pp > 0 && pp * (2 * n - pp - 1) / 2 > k) --pp;
+    while (pp < n - 2 && (pp + 1) * (2 * n - pp - 2) / 2 <= k) ++pp;
+    p = pp;
+    q = k - pp * (2 * n - pp - 1) / 2 + pp + 1;
+}
+
+// Xp[ef][r*PO + ij] = 1/2 (X[r][i][j][e][f] - X[r][i][j][f][e]),  i<j, e<f
+__global__ void k_pack_x(const cplx* __restrict__ X, cplx* __restrict__ Xp, int64_t R, int64_t O, int64_t V) {
+    int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
+    int64_t ncol = R * PO, total = PV * ncol;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ef = idx / ncol, col = idx % ncol;
+        int64_t r = col / PO, ij = col % PO;
+        int64_t e, f, i, j;
+        pair_decode(ef, V, e, f);
+        pair_decode(ij, O, i, j);
+        const cplx* x = X + ((r * O + i) * O + j) * V * V;
+        cplx u = x[e * V + f], w = x[f * V + e];
+        Xp[idx] = make_double2(0.5 * (u.x - w.x), 0.5 * (u.y - w.y));
+    }
+}
+
+// W[row][ef] = G[(a-a0)V + e][(b-b0)V + f] - G[(a-a0)V + f][(b-b0)V + e]
+// for the (a<b) pairs of rows a in [a0, a1); row = pair(a,b) - pair(a0,a0+1);
+// b0 = a0 + 1 is the first b column of G.
+__global__ void k_antisym_slab(const cplx* __restrict__ G, int64_t ldg, cplx* __restrict__ W, int64_t a0,
+                               int64_t nrows, int64_t V) {
+    int64_t PV = V * (V - 1) / 2;
+    int64_t row0 = a0 * (2 * V - a0 - 1) / 2;
+    int64_t total = nrows * PV;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row = idx / PV, ef = idx % PV;
+        int64_t a, b, e, f;
+        pair_decode(row + row0, V, a, b);
+        pair_decode(ef, V, e, f);
+        int64_t ra = (a - a0) * V, cb = (b - a0 - 1) * V;
+        cplx g1 = G[(ra + e) * ldg + cb + f];
+        cplx g2 = G[(ra + f) * ldg + cb + e];
+        W[idx] = make_double2(g1.x - g2.x, g1.y - g2.y);
+    }
+}
+
+// Z[r][i][j][a][b] = alpha * sign * Zp[ab][r*PO + ij] + beta * Z
+__global__ void k_unpack_z(const cplx* __restrict__ Zp, cplx* __restrict__ Z, int64_t R, int64_t O, int64_t V,
+                           cplx alpha, cplx beta, int beta0) {
+    int64_t PO = O * (O - 1) / 2;
+    int64_t total = R * O * O * V * V;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = idx % V, t = idx / V;
+        int64_t a = t % V;
+        t /= V;
+        int64_t j = t % O;
+        t /= O;
+        int64_t i = t % O, r = t / O;
+        cplx v = make_double2(0.0, 0.0);
+        if (i != j && a != b) {
+            double sg = 1.0;
+            int64_t ii = i, jj = j, aa = a, bb = b;
+            if (ii > jj) { int64_t q = ii; ii = jj; jj = q; sg = -sg; }
+            if (aa > bb) { int64_t q = aa; aa = bb; bb = q; sg = -sg; }
+            int64_t ab = aa * (2 * V - aa - 1) / 2 + (bb - aa - 1);
+            int64_t ij = ii * (2 * O - ii - 1) / 2 + (jj - ii - 1);
+            cplx z = Zp[ab * (R * PO) + r * PO + ij];
+            v = make_double2(sg * (alpha.x * z.x - alpha.y * z.y), sg * (alpha.x * z.y + alpha.y * z.x));
+        }
+        if (!beta0) {
+            cplx o = Z[idx];
+            v.x += beta.x * o.x - beta.y * o.y;
+            v.y += beta.x * o.y + beta.y * o.x;
+        }
+        Z[idx] = v;
+    }
+}
+
+int grid_n(Dev& D, int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)D.sm_count * 16));
+}
+
+}  // namespace
+
+void ladder(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose, int prec) {
+    REQUIRE(X.nd == 5 && Z.nd == 5 && X.contiguous() && Z.contiguous(), "ladder needs contiguous [R][O][O][V][V]");
+    int64_t R = X.d[0], O = X.d[1], V = X.d[3];
+    int64_t L = LC.Bvv.d[0];
+    REQUIRE(LC.Bvv.d[1] == V && LC.Bvv.d[2] == V, "ladder: Bvv shape");
+    int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
+    bool beta0 = beta.x == 0.0 && beta.y == 0.0;
+    if (PO == 0 || PV == 0) {
+        if (beta0) fill(D, Z, mkc(0.0));
+        else axpby(D, mkc(0.0), Z, false, beta, Z);
+        return;
+    }
+    Tensor Xp = empty(D, {PV, R * PO});
+    k_pack_x<<<grid_n(D, PV * R * PO), 256, 0, D.st>>>(X.p, Xp.p, R, O, V);
+    LAUNCH_CHECK(D);
+    Tensor Zp = empty(D, {PV, R * PO});
+    // slab height: G of na*V x (V-a0-1)*V complex kept under ~4 GiB
+    int64_t budget = LC.slab_rows > 0 ? LC.slab_rows : (int64_t(4) << 30) / 16;
+    int64_t na = std::max<int64_t>(1, budget / std::max<int64_t>(1, V * V * V));
+    for (int64_t a0 = 0; a0 < V - 1; a0 += na) {
+        int64_t a1 = std::min<int64_t>(V - 1, a0 + na);
+        int64_t nb = V - a0 - 1;  // b in [a0+1, V)
+        Tensor G = empty(D, {(a1 - a0) * V, nb * V});
+        GemmArgs g1;
+        g1.M = (a1 - a0) * V; g1.N = nb * V; g1.K = L; g1.batch = 1;
+        g1.A = LC.Bvv.p + a0 * V; g1.sAb = 0; g1.sAm = 1; g1.sAk = V * V; g1.cA = transpose;
+        g1.B = LC.Bvv.p + (a0 + 1) * V; g1.sBb = 0; g1.sBk = V * V; g1.sBn = 1; g1.cB = transpose;
+        g1.C = G.p; g1.sCb = 0; g1.sCm = nb * V; g1.sCn = 1;
+        g1.alpha = mkc(1.0); g1.beta = mkc(0.0);
+        if (prec != LRCC_FP64 && gemm_tc_available()) gemm_tc(D, g1, prec);
+        else gemm_f64(D, g1);
+        int64_t row0 = a0 * (2 * V - a0 - 1) / 2, row1 = a1 * (2 * V - a1 - 1) / 2;
+        int64_t nrows = row1 - row0;
+        Tensor W = empty(D, {nrows, PV});
+        k_antisym_slab<<<grid_n(D, nrows * PV), 256, 0, D.st>>>(G.p, nb * V, W.p, a0, nrows, V);
+        LAUNCH_CHECK(D);
+        GemmArgs g2;
+        g2.M = nrows; g2.N = R * PO; g2.K = PV; g2.batch = 1;
+        g2.A = W.p; g2.sAb = 0; g2.sAm = PV; g2.sAk = 1; g2.cA = false;
+        g2.B = Xp.p; g2.sBb = 0; g2.sBk = R * PO; g2.sBn = 1; g2.cB = false;
+        g2.C = Zp.p + row0 * R * PO; g2.sCb = 0; g2.sCm = R * PO; g2.sCn = 1;
+        g2.alpha = mkc(1.0); g2.beta = mkc(0.0);
+        if (prec != LRCC_FP64 && gemm_tc_available()) gemm_tc(D, g2, prec);
+        else gemm_f64(D, g2);
+    }
+    k_unpack_z<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zp.p, Z.p, R, O, V, alpha, beta, beta0);
+    LAUNCH_CHECK(D);
+}

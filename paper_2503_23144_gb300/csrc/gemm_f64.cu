@@ -1,0 +1,257 @@
+// FP64 complex GEMM on the CUDA cores (the plain-FP64 path and the FP64
+// outer residual of the mixed path).  Operands are arbitrary-stride views, so
+// most contractions of the residual need no transposition copy.
+//
+// Tiling: 64x64 output tile per 256-thread CTA, 4x4 complex accumulators per
+// thread, K step 8 complex, register-prefetched double-buffered shared tiles.
+// Split-K over grid.z with FP64 atomics when the tile grid is too small for
+// the 152 SMs.
+#include "lrcc_internal.h"
+
+#include <algorithm>
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 8, TH = 256;
+
+__device__ __forceinline__ void cfma(cplx& c, cplx a, cplx b) {
+    c.x = fma(a.x, b.x, c.x);
+    c.x = fma(-a.y, b.y, c.x);
+    c.y = fma(a.x, b.y, c.y);
+    c.y = fma(a.y, b.x, c.y);
+}
+
+struct GemmK {
+    int64_t M, N, K;
+    const cplx* A;
+    int64_t sAb, sAm, sAk;
+    int cA;
+    const cplx* B;
+    int64_t sBb, sBk, sBn;
+    int cB;
+    cplx* C;
+    int64_t sCb, sCm, sCn;
+    cplx alpha, beta;
+    int64_t kper;  // K range per split
+    int atomic;    // 1: accumulate alpha*acc with atomics (C pre-scaled by beta)
+    int a_kfast, b_nfast;
+};
+
+__global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
+    __shared__ cplx As[2][BK][BM];
+    __shared__ cplx Bs[2][BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t tiles_n = (g.N + BN - 1) / BN;
+    const int64_t m0 = (blockIdx.x / tiles_n) * BM;
+    const int64_t n0 = (blockIdx.x % tiles_n) * BN;
+    const int64_t b = blockIdx.y;
+    const int64_t kbeg = blockIdx.z * g.kper;
+    const int64_t kend = min(g.K, kbeg + g.kper);
+    const cplx* A = g.A + b * g.sAb;
+    const cplx* B = g.B + b * g.sBb;
+
+    cplx acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+    cplx ra[2], rb[2];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            int e = tid + r * TH;  // 0..511
+            int mm, kk;
+            if (g.a_kfast) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+            int64_t m = m0 + mm, k = k0 + kk;
+            cplx v = make_double2(0.0, 0.0);
+            if (m < g.M && k < kend) v = A[m * g.sAm + k * g.sAk];
+            if (g.cA) v.y = -v.y;
+            ra[r] = v;
+            int nn;
+            if (g.b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+            int64_t n = n0 + nn;
+            k = k0 + kk;
+            cplx w = make_double2(0.0, 0.0);
+            if (n < g.N && k < kend) w = B[k * g.sBk + n * g.sBn];
+            if (g.cB) w.y = -w.y;
+            rb[r] = w;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            int e = tid + r * TH;
+            int mm, kk, nn;
+            if (g.a_kfast) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
+            As[buf][kk][mm] = ra[r];
+            if (g.b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+            Bs[buf][kk][nn] = rb[r];
+        }
+    };
+
+    int buf = 0;
+    if (kbeg < kend) {
+        load(kbeg);
+        store(0);
+    }
+    __syncthreads();
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+        bool more = k0 + BK < kend;
+        if (more) load(k0 + BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            cplx a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], bb[j]);
+        }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+
+    cplx* C = g.C + b * g.sCb;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t m = m0 + ty + 16 * i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t n = n0 + tx + 16 * j;
+            if (n >= g.N) continue;
+            cplx v = acc[i][j];
+            cplx r = make_double2(g.alpha.x * v.x - g.alpha.y * v.y, g.alpha.x * v.y + g.alpha.y * v.x);
+            cplx* c = C + m * g.sCm + n * g.sCn;
+            if (g.atomic) {
+                atomicAdd(&c->x, r.x);
+                atomicAdd(&c->y, r.y);
+            } else {
+                if (g.beta.x != 0.0 || g.beta.y != 0.0) {
+                    cplx o = *c;
+                    r.x += g.beta.x * o.x - g.beta.y * o.y;
+                    r.y += g.beta.x * o.y + g.beta.y * o.x;
+                }
+                *c = r;
+            }
+        }
+    }
+}
+
+// C[b] += alpha * sum_k A[b][k] B[b][k]   (M = N = 1), C pre-scaled by beta
+__global__ void k_dot(int64_t K, const cplx* A, int64_t sAb, int64_t sAk, int cA, const cplx* B,
+                      int64_t sBb, int64_t sBk, int cB, cplx* C, int64_t sCb, cplx alpha) {
+    __shared__ double rx[32], ry[32];
+    int64_t b = blockIdx.y;
+    const cplx* a = A + b * sAb;
+    const cplx* bb = B + b * sBb;
+    double sx = 0, sy = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
+        cplx u = a[k * sAk], v = bb[k * sBk];
+        if (cA) u.y = -u.y;
+        if (cB) v.y = -v.y;
+        sx = fma(u.x, v.x, sx);
+        sx = fma(-u.y, v.y, sx);
+        sy = fma(u.x, v.y, sy);
+        sy = fma(u.y, v.x, sy);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffff, sx, o);
+        sy += __shfl_xor_sync(0xffffffff, sy, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rx[threadIdx.x >> 5] = sx;
+        ry[threadIdx.x >> 5] = sy;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int nw = blockDim.x >> 5;
+        sx = threadIdx.x < nw ? rx[threadIdx.x] : 0.0;
+        sy = threadIdx.x < nw ? ry[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffff, sx, o);
+            sy += __shfl_xor_sync(0xffffffff, sy, o);
+        }
+        if (threadIdx.x == 0) {
+            cplx* c = C + b * sCb;
+            atomicAdd(&c->x, alpha.x * sx - alpha.y * sy);
+            atomicAdd(&c->y, alpha.x * sy + alpha.y * sx);
+        }
+    }
+}
+
+// C[b][m][n] *= beta (strided), beta == 0 -> zero
+__global__ void k_scale(int64_t M, int64_t N, int64_t batch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn,
+                        cplx beta) {
+    int64_t total = M * N * batch;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t n = i % N, r = i / N, m = r % M, b = r / M;
+        cplx* c = C + b * sCb + m * sCm + n * sCn;
+        if (beta.x == 0.0 && beta.y == 0.0) {
+            *c = make_double2(0.0, 0.0);
+        } else {
+            cplx o = *c;
+            *c = make_double2(beta.x * o.x - beta.y * o.y, beta.x * o.y + beta.y * o.x);
+        }
+    }
+}
+
+}  // namespace
+
+static void prescale(Dev& D, const GemmArgs& g) {
+    if (g.beta.x == 1.0 && g.beta.y == 0.0) return;
+    int64_t total = g.M * g.N * g.batch;
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, D.sm_count * 16));
+    k_scale<<<grid, 256, 0, D.st>>>(g.M, g.N, g.batch, g.C, g.sCb, g.sCm, g.sCn, g.beta);
+    LAUNCH_CHECK(D);
+}
+
+void gemm_f64(Dev& D, const GemmArgs& g) {
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+    if (g.K <= 0) {
+        prescale(D, g);
+        return;
+    }
+    if (g.batch > 65535) throw LrccError(LRCC_EINVAL, "gemm batch > 65535");
+    if (g.M == 1 && g.N == 1) {
+        prescale(D, g);
+        int th = 256;
+        int64_t want = (g.K + th * 8 - 1) / (th * 8);
+        int gx = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::max<int64_t>(1, 4 * D.sm_count / g.batch)));
+        dim3 grid(gx, (unsigned)g.batch);
+        k_dot<<<grid, th, 0, D.st>>>(g.K, g.A, g.sAb, g.sAk, g.cA, g.B, g.sBb, g.sBk, g.cB, g.C, g.sCb, g.alpha);
+        LAUNCH_CHECK(D);
+        return;
+    }
+    int64_t tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
+    if (tiles > INT32_MAX) throw LrccError(LRCC_EINVAL, "gemm too large");
+    int64_t ctas = tiles * g.batch;
+    int64_t splits = 1;
+    int64_t target = 2 * (int64_t)D.sm_count;
+    if (ctas < target && g.K >= 4 * BK * 8) {
+        splits = std::min<int64_t>((target + ctas - 1) / ctas, g.K / (BK * 16));
+        splits = std::max<int64_t>(1, std::min<int64_t>(splits, 64));
+    }
+    GemmK k;
+    k.M = g.M; k.N = g.N; k.K = g.K;
+    k.A = g.A; k.sAb = g.sAb; k.sAm = g.sAm; k.sAk = g.sAk; k.cA = g.cA;
+    k.B = g.B; k.sBb = g.sBb; k.sBk = g.sBk; k.sBn = g.sBn; k.cB = g.cB;
+    k.C = g.C; k.sCb = g.sCb; k.sCm = g.sCm; k.sCn = g.sCn;
+    k.alpha = g.alpha; k.beta = g.beta;
+    k.kper = (g.K + splits - 1) / splits;
+    k.kper = (k.kper + BK - 1) / BK * BK;
+    splits = (g.K + k.kper - 1) / k.kper;
+    k.atomic = splits > 1;
+    k.a_kfast = (g.sAk == 1) || (g.sAm != 1 && std::llabs(g.sAk) < std::llabs(g.sAm));
+    k.b_nfast = (g.sBn == 1) || (g.sBk != 1 && std::llabs(g.sBn) < std::llabs(g.sBk));
+    if (k.atomic) prescale(D, g);
+    dim3 grid((unsigned)tiles, (unsigned)g.batch, (unsigned)splits);
+    k_gemm<<<grid, TH, 0, D.st>>>(k);
+    LAUNCH_CHECK(D);
+}

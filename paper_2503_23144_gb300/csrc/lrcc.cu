@@ -1,0 +1,739 @@
+// Context, set-up, ground state, linear response and the extern "C" entry
+// points declared in include/lrcc.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "solver.h"
+
+struct lrcc_ctx {
+    Dev D;
+    lrcc_options opt;
+    int O = 0, V = 0, L = 0, ncomp = 0;
+    std::vector<double> eps;
+    double* eo = nullptr;  // device
+    double* ev = nullptr;
+    Tensor B, mu;          // [L][N][N], [ncomp][N][N]
+    Ham H;
+    std::vector<Ham> Hmu;
+    LadderCtx lad;
+    std::unique_ptr<CCProg> cc;          // two-body program, primal cached at T
+    std::vector<std::unique_ptr<CCProg>> ccmu;  // one-body programs (xi, eta)
+    std::unique_ptr<CCProg> ccfx;        // scratch program for the F.X stencil
+    bool ground = false;
+    Amp T, Lam;                          // R = 1
+    std::string err;
+    double phase_ms[7] = {0};
+    ~lrcc_ctx() {
+        cc.reset();
+        ccmu.clear();
+        ccfx.reset();
+        if (eo) cudaFree(eo);
+        if (ev) cudaFree(ev);
+    }
+};
+
+static std::string g_setup_err = "";
+
+namespace {
+
+struct Timer {
+    cudaEvent_t a, b;
+    Dev& D;
+    explicit Timer(Dev& d) : D(d) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, D.st);
+    }
+    double stop() {
+        cudaEventRecord(b, D.st);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        return ms;
+    }
+    ~Timer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+Tensor dev_copy_c(Dev& D, const double* host, std::vector<int64_t> shape) {
+    Tensor t = empty(D, shape);
+    CK(cudaMemcpyAsync(t.p, host, t.numel() * sizeof(cplx), cudaMemcpyHostToDevice, D.st));
+    return t;
+}
+
+void build_ham(lrcc_ctx* c) {
+    Dev& D = c->D;
+    int O = c->O, V = c->V;
+    int64_t N = O + V;
+    Ham& H = c->H;
+    // Fock = diag(eps) (canonical reference)
+    std::vector<double> f(2 * N * N, 0.0);
+    for (int64_t p = 0; p < N; ++p) f[2 * (p * N + p)] = c->eps[p];
+    Tensor F = dev_copy_c(D, f.data(), {N, N});
+    auto blk = [&](const Tensor& M, int64_t r0, int64_t nr, int64_t c0, int64_t nc) {
+        Tensor out = empty(D, {nr, nc});
+        axpby(D, mkc(1.0), M.slice(0, r0, nr).slice(1, c0, nc), false, mkc(0.0), out);
+        return out;
+    };
+    H.w = true;
+    H.foo = blk(F, 0, O, 0, O);
+    H.fov = blk(F, 0, O, O, V);
+    H.fvo = blk(F, O, V, 0, O);
+    H.fvv = blk(F, O, V, O, V);
+    const Tensor& B = c->B;
+    H.oooo = anti_block(D, B, 0, O, 0, O, 0, O, 0, O);
+    H.ooov = anti_block(D, B, 0, O, 0, O, 0, O, O, V);
+    H.oovo = anti_block(D, B, 0, O, 0, O, O, V, 0, O);
+    H.ovoo = anti_block(D, B, 0, O, O, V, 0, O, 0, O);
+    H.oovv = anti_block(D, B, 0, O, 0, O, O, V, O, V);
+    H.vvoo = anti_block(D, B, O, V, O, V, 0, O, 0, O);
+    H.ovov = anti_block(D, B, 0, O, O, V, 0, O, O, V);
+    H.ovvo = anti_block(D, B, 0, O, O, V, O, V, 0, O);
+    H.ovvv = anti_block(D, B, 0, O, O, V, O, V, O, V);
+    H.vovv = anti_block(D, B, O, V, 0, O, O, V, O, V);
+    H.vvvo = anti_block(D, B, O, V, O, V, O, V, 0, O);
+    c->lad.Bvv = empty(D, {(int64_t)c->L, (int64_t)V, (int64_t)V});
+    axpby(D, mkc(1.0), B.slice(1, O, V).slice(2, O, V), false, mkc(0.0), c->lad.Bvv);
+    c->lad.slab_rows = c->opt.slab_rows;
+    c->Hmu.clear();
+    for (int k = 0; k < c->ncomp; ++k) {
+        Ham h;
+        h.w = false;
+        Tensor M = c->mu.index(k);
+        h.foo = blk(M, 0, O, 0, O);
+        h.fov = blk(M, 0, O, O, V);
+        h.fvo = blk(M, O, V, 0, O);
+        h.fvv = blk(M, O, V, O, V);
+        c->Hmu.push_back(h);
+    }
+    c->cc.reset(new CCProg());
+    build_ccsd(*c->cc, c->H, &c->lad);
+    c->ccfx.reset(new CCProg());
+    build_ccsd(*c->ccfx, c->H, &c->lad);
+    c->ccmu.clear();
+    for (int k = 0; k < c->ncomp; ++k) {
+        c->ccmu.emplace_back(new CCProg());
+        build_ccsd(*c->ccmu.back(), c->Hmu[k], nullptr);
+    }
+    std::vector<double> eo(c->eps.begin(), c->eps.begin() + O), ev(c->eps.begin() + O, c->eps.end());
+    if (c->eo) cudaFree(c->eo);
+    if (c->ev) cudaFree(c->ev);
+    CK(cudaMalloc(&c->eo, sizeof(double) * O));
+    CK(cudaMalloc(&c->ev, sizeof(double) * V));
+    CK(cudaMemcpy(c->eo, eo.data(), sizeof(double) * O, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->ev, ev.data(), sizeof(double) * V, cudaMemcpyHostToDevice));
+    c->ground = false;
+}
+
+// amplitudes of one RHS as program inputs (leading R dropped)
+std::vector<Tensor> inputs_of(const Amp& a, int64_t r) { return {a.t1.index(r), a.t2.index(r)}; }
+
+Amp add_batch(const Tensor& t1, const Tensor& t2) {
+    Amp a;
+    std::vector<int64_t> s1 = t1.shape(), s2 = t2.shape();
+    s1.insert(s1.begin(), 1);
+    s2.insert(s2.begin(), 1);
+    a.t1 = t1.reshape(s1);
+    a.t2 = t2.reshape(s2);
+    return a;
+}
+
+// R(T) for one amplitude set (primal evaluation of the program)
+Amp residual_T(Dev& D, CCProg& cp, const Amp& T, int64_t r, int prec, cplx* energy_out = nullptr) {
+    cp.P.eval(D, inputs_of(T, r), prec);
+    Amp out = add_batch(cp.P.val[cp.R1], cp.P.val[cp.R2]);
+    if (energy_out) {
+        CK(cudaMemcpyAsync(energy_out, cp.P.val[cp.E].p, sizeof(cplx), cudaMemcpyDeviceToHost, D.st));
+        CK(cudaStreamSynchronize(D.st));
+    }
+    return out;
+}
+
+// sigma = A X  (program must hold the primal at T)
+Amp sigma(Dev& D, CCProg& cp, const Amp& X, int prec) {
+    std::vector<Tensor> r = cp.P.jvp(D, {X.t1, X.t2}, {cp.R1, cp.R2}, prec);
+    return Amp{r[0], r[1]};
+}
+
+// unique-amplitude transpose product A^T y (+ e_scale * dE/dT), program at T
+Amp vjp_unique(Dev& D, CCProg& cp, const Amp& Y, double e_scale, int prec) {
+    int64_t R = Y.t1.d[0];
+    Tensor c2 = empty(D, Y.t2.shape());
+    axpby(D, mkc(0.25), Y.t2, false, mkc(0.0), c2);
+    Tensor ce;
+    if (e_scale != 0.0) {
+        ce = empty(D, {R});
+        fill(D, ce, mkc(e_scale));
+    }
+    std::vector<Tensor> g = cp.P.vjp(D, {Y.t1, c2, ce}, {cp.R1, cp.R2, cp.E}, prec);
+    return Amp{g[0], antisym4(D, g[1])};
+}
+
+Amp grad_energy(Dev& D, CCProg& cp, int64_t O, int64_t V, int prec) {
+    Tensor ce = empty(D, {1});
+    fill(D, ce, mkc(1.0));
+    std::vector<Tensor> g = cp.P.vjp(D, {Tensor(), Tensor(), ce}, {cp.R1, cp.R2, cp.E}, prec);
+    (void)O;
+    (void)V;
+    return Amp{g[0], antisym4(D, g[1])};
+}
+
+double* dev_doubles(Dev& D, const std::vector<double>& v, std::shared_ptr<DevBuf>& hold) {
+    size_t n = sizeof(double) * std::max<size_t>(1, v.size());
+    double* p = (double*)D.pool.get(n);
+    hold.reset(new DevBuf{&D.pool, p, n});
+    CK(cudaMemcpyAsync(p, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, D.st));
+    CK(cudaStreamSynchronize(D.st));
+    return p;
+}
+
+// generic preconditioned DIIS loop on R right-hand sides:
+//   r = resid(x);  x <- extrapolate(x - r/(D + shift))
+template <class F>
+int solve_loop(lrcc_ctx* c, Amp& x, F&& resid, const std::vector<double>& shift, double tol, int max_iter,
+               std::vector<double>* final_res = nullptr) {
+    Dev& D = c->D;
+    int64_t R = x.t1.d[0];
+    std::shared_ptr<DevBuf> hold;
+    double* sh = dev_doubles(D, shift, hold);
+    Diis diis(D, (int)R, c->opt.diis_size);
+    std::vector<double> rn;
+    for (int it = 0; it < max_iter; ++it) {
+        Amp r = resid(x);
+        max_abs_amp(D, r, rn);
+        double m = *std::max_element(rn.begin(), rn.end());
+        if (!std::isfinite(m) || m > 1e250) throw LrccError(LRCC_ENOCONV, "residual is not finite");
+        if (m < tol) {
+            if (final_res) *final_res = rn;
+            return it;
+        }
+        Amp xn = amp_empty(D, R, c->O, c->V);
+        precond(D, &x, r, xn, c->eo, c->ev, sh);
+        Amp e = amp_empty(D, R, c->O, c->V);
+        amp_axpby(D, mkc(1.0), xn, mkc(0.0), e);
+        amp_axpby(D, mkc(-1.0), x, mkc(1.0), e);
+        x = diis.push_extrapolate(D, xn, e);
+    }
+    if (final_res) *final_res = rn;
+    throw LrccError(LRCC_ENOCONV, "no convergence after " + std::to_string(max_iter) + " iterations (max|r| = " +
+                                      std::to_string(rn.empty() ? -1.0 : *std::max_element(rn.begin(), rn.end())) + ")");
+}
+
+void do_ground(lrcc_ctx* c, cplx& E, int& itT, int& itL) {
+    Dev& D = c->D;
+    int O = c->O, V = c->V;
+    // MP2 start: one Jacobi step from T = 0
+    Amp T0 = amp_zeros(D, 1, O, V);
+    std::vector<double> zero(1, 0.0);
+    std::shared_ptr<DevBuf> hold;
+    double* sh = dev_doubles(D, zero, hold);
+    {
+        Timer tm(D);
+        Amp r0 = residual_T(D, *c->cc, T0, 0, LRCC_FP64);
+        Amp T = amp_empty(D, 1, O, V);
+        precond(D, nullptr, r0, T, c->eo, c->ev, sh);
+        auto res = [&](const Amp& x) { return amp_copy(D, residual_T(D, *c->cc, x, 0, LRCC_FP64)); };
+        itT = solve_loop(c, T, res, zero, c->opt.r_tol, c->opt.max_iter);
+        c->T = amp_copy(D, T);
+        residual_T(D, *c->cc, c->T, 0, LRCC_FP64, &E);  // primal cached at converged T
+        c->phase_ms[0] = tm.stop();
+    }
+    {
+        Timer tm(D);
+        Amp gE = grad_energy(D, *c->cc, O, V, LRCC_FP64);
+        Amp L0 = amp_empty(D, 1, O, V);
+        precond(D, nullptr, gE, L0, c->eo, c->ev, sh);
+        auto res = [&](const Amp& l) {
+            Amp r = vjp_unique(D, *c->cc, l, 0.0, LRCC_FP64);
+            amp_axpby(D, mkc(1.0), gE, mkc(1.0), r);
+            return r;
+        };
+        itL = solve_loop(c, L0, res, zero, c->opt.r_tol, c->opt.max_iter);
+        c->Lam = amp_copy(D, L0);
+        c->phase_ms[1] = tm.stop();
+    }
+    c->ground = true;
+}
+
+// F X for each RHS of X: exact 5-point stencil of the Lagrangian gradient
+// g(T) = A(T)^T lambda + dE/dT, a polynomial of degree <= 3 in T (Eq. 34).
+Amp fx_product(lrcc_ctx* c, const Amp& X) {
+    Dev& D = c->D;
+    int64_t R = X.t1.d[0];
+    int O = c->O, V = c->V;
+    Amp out = amp_empty(D, R, O, V);
+    std::vector<double> nrm;
+    max_abs_amp(D, X, nrm);
+    const double h = 0.5;
+    const int ks[4] = {-2, -1, 1, 2};
+    const double wk[4] = {1.0, -8.0, 8.0, -1.0};
+    for (int64_t r = 0; r < R; ++r) {
+        Tensor o1 = out.t1.index(r), o2 = out.t2.index(r);
+        if (!(nrm[r] > 0.0)) {
+            fill(D, o1, mkc(0.0));
+            fill(D, o2, mkc(0.0));
+            continue;
+        }
+        double s = 1.0 / nrm[r];
+        bool first = true;
+        for (int q = 0; q < 4; ++q) {
+            Amp Tk = amp_copy(D, c->T);
+            Tensor x1 = X.t1.index(r), x2 = X.t2.index(r);
+            Tensor tk1 = Tk.t1.index(0), tk2 = Tk.t2.index(0);
+            axpby(D, mkc(ks[q] * h * s), x1, false, mkc(1.0), tk1);
+            axpby(D, mkc(ks[q] * h * s), x2, false, mkc(1.0), tk2);
+            c->ccfx->P.eval(D, inputs_of(Tk, 0), LRCC_FP64);
+            Amp g = vjp_unique(D, *c->ccfx, c->Lam, 1.0, LRCC_FP64);
+            cplx w = mkc(wk[q] * nrm[r] / (12.0 * h));
+            Tensor g1 = g.t1.index(0), g2 = g.t2.index(0);
+            axpby(D, w, g1, false, first ? mkc(0.0) : mkc(1.0), o1);
+            axpby(D, w, g2, false, first ? mkc(0.0) : mkc(1.0), o2);
+            first = false;
+        }
+    }
+    return out;
+}
+
+void do_solve(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int n_c, double* alpha,
+              double* err_est) {
+    Dev& D = c->D;
+    int O = c->O, V = c->V;
+    for (int q = 0; q < 7; ++q) if (q >= 2) c->phase_ms[q] = 0;
+    // xi^A, eta^A per component (Eq. 31, 33)
+    std::vector<Amp> xi(c->ncomp), eta(c->ncomp);
+    std::vector<char> need(c->ncomp, 0);
+    for (int k = 0; k < n_c; ++k) need[comps[k]] = 1;
+    {
+        Timer tm(D);
+        for (int k = 0; k < c->ncomp; ++k) {
+            if (!need[k]) continue;
+            xi[k] = amp_copy(D, residual_T(D, *c->ccmu[k], c->T, 0, LRCC_FP64));
+            eta[k] = vjp_unique(D, *c->ccmu[k], c->Lam, 1.0, LRCC_FP64);
+        }
+        c->phase_ms[2] += tm.stop();
+    }
+    // right-hand sides (omega, component), rhs_chunk at a time
+    struct Rhs { int w, comp_idx; };
+    std::vector<Rhs> all;
+    for (int w = 0; w < n_w; ++w)
+        for (int k = 0; k < n_c; ++k) all.push_back({w, k});
+    std::vector<cplx> g((size_t)n_w * n_c * n_c, mkc(0.0));
+    std::vector<double> errs((size_t)n_w * n_c, 0.0);
+    int chunk = std::max(1, c->opt.rhs_chunk);
+    for (size_t c0 = 0; c0 < all.size(); c0 += chunk) {
+        size_t c1 = std::min(all.size(), c0 + chunk);
+        int64_t R = (int64_t)(c1 - c0);
+        Amp xiR = amp_empty(D, R, O, V), rhsY = amp_empty(D, R, O, V);
+        std::vector<double> mw(R), pw(R);
+        for (int64_t r = 0; r < R; ++r) {
+            const Rhs& q = all[c0 + r];
+            int comp = comps[q.comp_idx];
+            Tensor a1 = xiR.t1.index(r), a2 = xiR.t2.index(r);
+            axpby(D, mkc(1.0), xi[comp].t1.index(0), false, mkc(0.0), a1);
+            axpby(D, mkc(1.0), xi[comp].t2.index(0), false, mkc(0.0), a2);
+            mw[r] = -omegas[q.w];
+            pw[r] = omegas[q.w];
+        }
+        std::shared_ptr<DevBuf> h1, h2;
+        double* mwd = dev_doubles(D, mw, h1);
+        double* pwd = dev_doubles(D, pw, h2);
+        // X: (A - w) X = -xi
+        Amp X = amp_empty(D, R, O, V);
+        std::vector<double> resX, resY;
+        {
+            Timer tm(D);
+            precond(D, nullptr, xiR, X, c->eo, c->ev, mwd);
+            auto res = [&](const Amp& x) {
+                Amp s = sigma(D, *c->cc, x, c->opt.prec == LRCC_FP64 ? LRCC_FP64 : LRCC_FP64);
+                Amp r = amp_empty(D, R, O, V);
+                combine(D, s, x, mwd, &xiR, r);
+                return r;
+            };
+            solve_loop(c, X, res, mw, c->opt.x_tol, c->opt.max_iter, &resX);
+            c->phase_ms[3] += tm.stop();
+        }
+        // eta + F X
+        {
+            Timer tm(D);
+            Amp FX = fx_product(c, X);
+            for (int64_t r = 0; r < R; ++r) {
+                int comp = comps[all[c0 + r].comp_idx];
+                Tensor y1 = rhsY.t1.index(r), y2 = rhsY.t2.index(r);
+                axpby(D, mkc(1.0), eta[comp].t1.index(0), false, mkc(0.0), y1);
+                axpby(D, mkc(1.0), eta[comp].t2.index(0), false, mkc(0.0), y2);
+            }
+            amp_axpby(D, mkc(1.0), FX, mkc(1.0), rhsY);
+            c->phase_ms[4] += tm.stop();
+        }
+        // Y: Y (A + w) = -(eta + F X)
+        Amp Y = amp_empty(D, R, O, V);
+        {
+            Timer tm(D);
+            precond(D, nullptr, rhsY, Y, c->eo, c->ev, pwd);
+            auto res = [&](const Amp& y) {
+                Amp s = vjp_unique(D, *c->cc, y, 0.0, LRCC_FP64);
+                Amp r = amp_empty(D, R, O, V);
+                combine(D, s, y, pwd, &rhsY, r);
+                return r;
+            };
+            solve_loop(c, Y, res, pw, c->opt.x_tol, c->opt.max_iter, &resY);
+            c->phase_ms[5] += tm.stop();
+        }
+        // g_AB = Y^B . xi^A + eta^A . X^B
+        {
+            Timer tm(D);
+            for (int a = 0; a < n_c; ++a) {
+                int compA = comps[a];
+                Tensor d1 = amp_dot_fixed(D, Y, xi[compA]);
+                Tensor d2 = amp_dot_fixed(D, X, eta[compA]);
+                std::vector<cplx> h1v(R), h2v(R);
+                CK(cudaMemcpyAsync(h1v.data(), d1.p, sizeof(cplx) * R, cudaMemcpyDeviceToHost, D.st));
+                CK(cudaMemcpyAsync(h2v.data(), d2.p, sizeof(cplx) * R, cudaMemcpyDeviceToHost, D.st));
+                CK(cudaStreamSynchronize(D.st));
+                for (int64_t r = 0; r < R; ++r) {
+                    const Rhs& q = all[c0 + r];
+                    g[((size_t)q.w * n_c + a) * n_c + q.comp_idx] = mkc(h1v[r].x + h2v[r].x, h1v[r].y + h2v[r].y);
+                }
+            }
+            for (int64_t r = 0; r < R; ++r) {
+                const Rhs& q = all[c0 + r];
+                errs[(size_t)q.w * n_c + q.comp_idx] = std::max(resX[r], resY[r]);
+            }
+            c->phase_ms[6] += tm.stop();
+        }
+    }
+    // alpha_AB = -1/2 (g_AB + conj g_BA)   (Eq. 35, P(A,B) = swap + conjugate)
+    for (int w = 0; w < n_w; ++w)
+        for (int a = 0; a < n_c; ++a)
+            for (int b = 0; b < n_c; ++b) {
+                cplx gab = g[((size_t)w * n_c + a) * n_c + b], gba = g[((size_t)w * n_c + b) * n_c + a];
+                size_t o = ((size_t)w * n_c + a) * n_c + b;
+                alpha[2 * o] = -0.5 * (gab.x + gba.x);
+                alpha[2 * o + 1] = -0.5 * (gab.y - gba.y);
+            }
+    if (err_est) std::memcpy(err_est, errs.data(), sizeof(double) * errs.size());
+}
+
+lrcc_status fail(lrcc_ctx* c, const LrccError& e) {
+    if (c) c->err = e.what();
+    else g_setup_err = e.what();
+    return e.st;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void lrcc_default_options(lrcc_options* o) {
+    if (!o) return;
+    o->r_tol = 1e-10;
+    o->x_tol = 1e-9;
+    o->max_iter = 200;
+    o->diis_size = 8;
+    o->rhs_chunk = 12;
+    o->prec = LRCC_FP64;
+    o->inner_tol = 1e-3;
+    o->plus_omega = 0;
+    o->slab_rows = 0;
+}
+
+const char* lrcc_last_error(const lrcc_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
+
+lrcc_status lrcc_setup(const double* eps, const double* B, int L, const double* mu, int ncomp, int O, int V,
+                       const lrcc_options* opt, lrcc_ctx** out) {
+    if (!out) {
+        g_setup_err = "out is NULL";
+        return LRCC_EINVAL;
+    }
+    *out = nullptr;
+    lrcc_ctx* c = nullptr;
+    try {
+        REQUIRE(eps && B && mu, "null input array");
+        REQUIRE(O >= 2 && V >= 2 && L >= 1 && ncomp >= 1 && ncomp <= 3, "sizes out of range (O>=2, V>=2, L>=1, 1<=ncomp<=3)");
+        int64_t N = (int64_t)O + V;
+        for (int64_t p = 0; p < N; ++p) REQUIRE(std::isfinite(eps[p]), "eps not finite");
+        double homo = *std::max_element(eps, eps + O), lumo = *std::min_element(eps + O, eps + N);
+        REQUIRE(homo < lumo, "every occupied energy must be below every virtual energy");
+        // Hermiticity of B^L and mu (relative to the largest element)
+        auto herm = [&](const double* M, int64_t nmat, const char* what) {
+            double mx = 0.0, dev = 0.0;
+            for (int64_t l = 0; l < nmat; ++l) {
+                const double* m = M + 2 * l * N * N;
+                for (int64_t p = 0; p < N; ++p)
+                    for (int64_t q = 0; q < N; ++q) {
+                        double re = m[2 * (p * N + q)], im = m[2 * (p * N + q) + 1];
+                        double re2 = m[2 * (q * N + p)], im2 = m[2 * (q * N + p) + 1];
+                        REQUIRE(std::isfinite(re) && std::isfinite(im), std::string(what) + " not finite");
+                        mx = std::max(mx, std::hypot(re, im));
+                        dev = std::max(dev, std::hypot(re - re2, im + im2));
+                    }
+            }
+            REQUIRE(dev <= 1e-12 * std::max(mx, 1e-300), std::string(what) + " is not Hermitian");
+        };
+        herm(B, L, "B");
+        herm(mu, ncomp, "mu");
+        c = new lrcc_ctx();
+        if (opt) c->opt = *opt;
+        else lrcc_default_options(&c->opt);
+        REQUIRE(c->opt.prec >= LRCC_FP64 && c->opt.prec <= LRCC_MIXED_BF16X3, "bad precision mode");
+        REQUIRE(c->opt.max_iter >= 1 && c->opt.diis_size >= 2 && c->opt.rhs_chunk >= 1, "bad solver options");
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&c->D.sm_count, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaStreamCreateWithFlags(&c->D.st, cudaStreamNonBlocking));
+        c->O = O;
+        c->V = V;
+        c->L = L;
+        c->ncomp = ncomp;
+        c->eps.assign(eps, eps + N);
+        c->B = dev_copy_c(c->D, B, {L, N, N});
+        c->mu = dev_copy_c(c->D, mu, {ncomp, N, N});
+        build_ham(c);
+        CK(cudaStreamSynchronize(c->D.st));
+        *out = c;
+        return LRCC_OK;
+    } catch (const LrccError& e) {
+        g_setup_err = e.what();
+        delete c;
+        return e.st;
+    } catch (const std::exception& e) {
+        g_setup_err = e.what();
+        delete c;
+        return LRCC_ECUDA;
+    }
+}
+
+void lrcc_destroy(lrcc_ctx* c) {
+    if (!c) return;
+    cudaStream_t st = c->D.st;
+    if (st) cudaStreamSynchronize(st);
+    delete c;
+    if (st) cudaStreamDestroy(st);
+}
+
+lrcc_status lrcc_ccsd_ground(lrcc_ctx* c, double e_corr[2], int* iters_T, int* iters_L) {
+    if (!c) return LRCC_EINVAL;
+    try {
+        cplx E = mkc(0.0);
+        int itT = 0, itL = 0;
+        do_ground(c, E, itT, itL);
+        if (e_corr) {
+            e_corr[0] = E.x;
+            e_corr[1] = E.y;
+        }
+        if (iters_T) *iters_T = itT;
+        if (iters_L) *iters_L = itL;
+        return LRCC_OK;
+    } catch (const LrccError& e) {
+        return fail(c, e);
+    } catch (const std::exception& e) {
+        c->err = e.what();
+        return LRCC_ECUDA;
+    }
+}
+
+lrcc_status lrcc_solve(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int n_c, double* alpha,
+                       double* err_est) {
+    if (!c) return LRCC_EINVAL;
+    try {
+        if (!c->ground) throw LrccError(LRCC_ESTATE, "lrcc_solve before lrcc_ccsd_ground");
+        REQUIRE(omegas && comps && alpha && n_w >= 1 && n_c >= 1, "bad solve arguments");
+        for (int k = 0; k < n_c; ++k) REQUIRE(comps[k] >= 0 && comps[k] < c->ncomp, "component out of range");
+        for (int w = 0; w < n_w; ++w) REQUIRE(std::isfinite(omegas[w]), "omega not finite");
+        do_solve(c, omegas, n_w, comps, n_c, alpha, err_est);
+        return LRCC_OK;
+    } catch (const LrccError& e) {
+        return fail(c, e);
+    } catch (const std::exception& e) {
+        c->err = e.what();
+        return LRCC_ECUDA;
+    }
+}
+
+static lrcc_status residual_impl(lrcc_ctx* c, int kind, const double* t, const double* in, int R, int comp,
+                                 int prec, double* out, bool device) {
+    Dev& D = c->D;
+    int64_t O = c->O, V = c->V;
+    int64_t n1 = O * V, n2 = O * O * V * V, nt = n1 + n2;
+    REQUIRE(R >= 1 && in && out, "bad residual arguments");
+    REQUIRE(kind >= LRCC_RES_T && kind <= LRCC_RES_VJP_FULL, "bad residual kind");
+    REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_MIXED_BF16X3, "bad precision");
+    // stage inputs as [R][nt] on the device
+    Tensor inb;
+    if (device) inb = wrap((cplx*)in, {R, nt});
+    else inb = dev_copy_c(D, in, {R, nt});
+    auto to_amp = [&](const Tensor& flat, int64_t RR) {
+        Amp a = amp_empty(D, RR, O, V);
+        Tensor v1 = flat.slice(1, 0, n1), v2 = flat.slice(1, n1, n2);
+        // views [RR][O][V] and [RR][O][O][V][V] of the flat rows
+        Tensor s1 = v1;
+        s1.nd = 3; s1.d[0] = RR; s1.d[1] = O; s1.d[2] = V; s1.s[0] = nt; s1.s[1] = V; s1.s[2] = 1;
+        Tensor s2 = v2;
+        s2.nd = 5; s2.d[0] = RR; s2.d[1] = O; s2.d[2] = O; s2.d[3] = V; s2.d[4] = V;
+        s2.s[0] = nt; s2.s[1] = O * V * V; s2.s[2] = V * V; s2.s[3] = V; s2.s[4] = 1;
+        axpby(D, mkc(1.0), s1, false, mkc(0.0), a.t1);
+        // P: antisymmetric projection 1/4 (x - P_ij x - P_ab x + P_ij P_ab x)
+        perm_axpby(D, "Zijab->Zijab", mkc(0.25), s2, mkc(0.0), a.t2);
+        perm_axpby(D, "Zijab->Zjiab", mkc(-0.25), s2, mkc(1.0), a.t2);
+        perm_axpby(D, "Zijab->Zijba", mkc(-0.25), s2, mkc(1.0), a.t2);
+        perm_axpby(D, "Zijab->Zjiba", mkc(0.25), s2, mkc(1.0), a.t2);
+        return a;
+    };
+    Amp X = to_amp(inb, R);
+    Amp res;
+    std::vector<cplx> energies;
+    if (kind == LRCC_RES_SIGMA || kind == LRCC_RES_VJP || kind == LRCC_RES_VJP_FULL || kind == LRCC_RES_XI) {
+        REQUIRE(t, "t is required for SIGMA, VJP and XI");
+        Tensor tb = device ? wrap((cplx*)t, {1, nt}) : dev_copy_c(D, t, {1, nt});
+        Amp T = to_amp(tb, 1);
+        if (kind == LRCC_RES_XI) {
+            REQUIRE(comp >= 0 && comp < c->ncomp, "component out of range");
+            res = amp_copy(D, residual_T(D, *c->ccmu[comp], T, 0, LRCC_FP64));
+            // same xi for every RHS row of `in` is not meaningful; XI uses t only
+            Amp rep = amp_empty(D, R, O, V);
+            for (int64_t r = 0; r < R; ++r) {
+                Tensor a1 = rep.t1.index(r), a2 = rep.t2.index(r);
+                axpby(D, mkc(1.0), res.t1.index(0), false, mkc(0.0), a1);
+                axpby(D, mkc(1.0), res.t2.index(0), false, mkc(0.0), a2);
+            }
+            res = rep;
+        } else {
+            c->ccfx->P.eval(D, inputs_of(T, 0), prec);
+            if (kind == LRCC_RES_SIGMA) {
+                res = sigma(D, *c->ccfx, X, prec);
+            } else if (kind == LRCC_RES_VJP) {
+                res = vjp_unique(D, *c->ccfx, X, 0.0, prec);
+            } else {
+                // adjoint with cotangent `in` on every full entry, then P
+                Amp Xs = amp_copy(D, X);
+                axpby(D, mkc(4.0), X.t2, false, mkc(0.0), Xs.t2);
+                res = vjp_unique(D, *c->ccfx, Xs, 0.0, prec);
+                Tensor q = empty(D, res.t2.shape());
+                axpby(D, mkc(0.25), res.t2, false, mkc(0.0), q);
+                res.t2 = q;
+            }
+        }
+    } else {
+        res = amp_empty(D, R, O, V);
+        energies.resize(R);
+        for (int64_t r = 0; r < R; ++r) {
+            cplx e;
+            Amp rr = residual_T(D, *c->ccfx, X, r, prec, &e);
+            energies[r] = e;
+            Tensor a1 = res.t1.index(r), a2 = res.t2.index(r);
+            axpby(D, mkc(1.0), rr.t1.index(0), false, mkc(0.0), a1);
+            axpby(D, mkc(1.0), rr.t2.index(0), false, mkc(0.0), a2);
+        }
+    }
+    if (kind == LRCC_RES_ENERGY) {
+        if (device) {
+            CK(cudaMemcpyAsync(out, energies.data(), sizeof(cplx) * R, cudaMemcpyHostToDevice, D.st));
+            CK(cudaStreamSynchronize(D.st));
+        } else {
+            std::memcpy(out, energies.data(), sizeof(cplx) * R);
+        }
+        return LRCC_OK;
+    }
+    Tensor ob = device ? wrap((cplx*)out, {R, nt}) : empty(D, {R, nt});
+    {
+        Tensor v1 = ob.slice(1, 0, n1), v2 = ob.slice(1, n1, n2);
+        Tensor s1 = v1;
+        s1.nd = 3; s1.d[0] = R; s1.d[1] = O; s1.d[2] = V; s1.s[0] = nt; s1.s[1] = V; s1.s[2] = 1;
+        Tensor s2 = v2;
+        s2.nd = 5; s2.d[0] = R; s2.d[1] = O; s2.d[2] = O; s2.d[3] = V; s2.d[4] = V;
+        s2.s[0] = nt; s2.s[1] = O * V * V; s2.s[2] = V * V; s2.s[3] = V; s2.s[4] = 1;
+        axpby(D, mkc(1.0), res.t1, false, mkc(0.0), s1);
+        axpby(D, mkc(1.0), res.t2, false, mkc(0.0), s2);
+    }
+    if (!device) {
+        CK(cudaMemcpyAsync(out, ob.p, sizeof(cplx) * R * nt, cudaMemcpyDeviceToHost, D.st));
+    }
+    CK(cudaStreamSynchronize(D.st));
+    return LRCC_OK;
+}
+
+lrcc_status lrcc_residual(lrcc_ctx* c, int kind, const double* t, const double* in, int R, int comp, int prec,
+                          double* out) {
+    if (!c) return LRCC_EINVAL;
+    try {
+        return residual_impl(c, kind, t, in, R, comp, prec, out, false);
+    } catch (const LrccError& e) {
+        return fail(c, e);
+    } catch (const std::exception& e) {
+        c->err = e.what();
+        return LRCC_ECUDA;
+    }
+}
+
+lrcc_status lrcc_residual_dev(lrcc_ctx* c, int kind, const double* t, const double* in, int R, int comp, int prec,
+                              double* out, void* stream) {
+    if (!c) return LRCC_EINVAL;
+    try {
+        cudaStream_t st = (cudaStream_t)stream;
+        // order after the caller's stream, run on ours, order the caller after us
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, st));
+        CK(cudaStreamWaitEvent(c->D.st, ev, 0));
+        lrcc_status s = residual_impl(c, kind, t, in, R, comp, prec, out, true);
+        CK(cudaEventRecord(ev, c->D.st));
+        CK(cudaStreamWaitEvent(st, ev, 0));
+        CK(cudaEventDestroy(ev));
+        return s;
+    } catch (const LrccError& e) {
+        return fail(c, e);
+    } catch (const std::exception& e) {
+        c->err = e.what();
+        return LRCC_ECUDA;
+    }
+}
+
+lrcc_status lrcc_ladder_dev(lrcc_ctx* c, const double* x, double* z, int R, int transpose, int prec, void* stream) {
+    if (!c) return LRCC_EINVAL;
+    try {
+        REQUIRE(x && z && R >= 1, "bad ladder arguments");
+        REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_MIXED_BF16X3, "bad precision");
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, st));
+        CK(cudaStreamWaitEvent(c->D.st, ev, 0));
+        Tensor X = wrap((cplx*)x, {R, c->O, c->O, c->V, c->V});
+        Tensor Z = wrap((cplx*)z, {R, c->O, c->O, c->V, c->V});
+        ladder(c->D, c->lad, X, mkc(1.0), mkc(0.0), Z, transpose != 0, prec);
+        CK(cudaEventRecord(ev, c->D.st));
+        CK(cudaStreamWaitEvent(st, ev, 0));
+        CK(cudaEventDestroy(ev));
+        return LRCC_OK;
+    } catch (const LrccError& e) {
+        return fail(c, e);
+    } catch (const std::exception& e) {
+        c->err = e.what();
+        return LRCC_ECUDA;
+    }
+}
+
+lrcc_status lrcc_phase_times(const lrcc_ctx* c, double* ms7) {
+    if (!c || !ms7) return LRCC_EINVAL;
+    for (int k = 0; k < 7; ++k) ms7[k] = c->phase_ms[k];
+    return LRCC_OK;
+}
+
+int64_t lrcc_kernel_launches(const lrcc_ctx* c) { return c ? c->D.launches : 0; }
+
+lrcc_status lrcc_fns_truncate(lrcc_ctx* c, int by_count, double value, double omega, int* v_kept, double* occ_out) {
+    if (!c) return LRCC_EINVAL;
+    c->err = "lrcc_fns_truncate: not built yet";
+    (void)by_count; (void)value; (void)omega; (void)v_kept; (void)occ_out;
+    return LRCC_ESTATE;
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// Internal interfaces of the LR-CCSD library: device tensors, the caching
+// pool, the kernel launchers and the contraction engine.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/lrcc.h"
+
+typedef double2 cplx;
+
+static inline cplx mkc(double re, double im = 0.0) { return make_double2(re, im); }
+
+struct LrccError : std::runtime_error {
+    lrcc_status st;
+    LrccError(lrcc_status s, const std::string& m) : std::runtime_error(m), st(s) {}
+};
+
+#define CK(x)                                                                              \
+    do {                                                                                   \
+        cudaError_t e_ = (x);                                                              \
+        if (e_ != cudaSuccess)                                                             \
+            throw LrccError(e_ == cudaErrorMemoryAllocation ? LRCC_ENOMEM : LRCC_ECUDA,    \
+                            std::string(#x) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+#define REQUIRE(cond, msg)                                         \
+    do {                                                           \
+        if (!(cond)) throw LrccError(LRCC_EINVAL, std::string(msg)); \
+    } while (0)
+
+#define LAUNCH_CHECK(D)                                 \
+    do {                                                \
+        (D).launches++;                                 \
+        cudaError_t e_ = cudaGetLastError();            \
+        if (e_ != cudaSuccess)                          \
+            throw LrccError(LRCC_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// caching device allocator (stream-ordered reuse on the context's one stream)
+// ---------------------------------------------------------------------------
+struct Pool {
+    std::multimap<size_t, void*> cache;
+    size_t live = 0, cached = 0, peak = 0;
+    void* get(size_t n);
+    void put(void* p, size_t n);
+    void trim();
+    ~Pool();
+};
+
+struct DevBuf {
+    Pool* pool;
+    void* p;
+    size_t n;
+    ~DevBuf() { pool->put(p, n); }
+};
+
+struct Dev {
+    cudaStream_t st = nullptr;
+    Pool pool;
+    int64_t launches = 0;
+    int* err_flag = nullptr;  // device word set by kernels whose bounded waits expire
+    int sm_count = 148;
+};
+
+// ---------------------------------------------------------------------------
+// strided complex tensor (row-major by default), up to 8 dimensions
+// ---------------------------------------------------------------------------
+constexpr int MAXD = 8;
+
+struct Tensor {
+    std::shared_ptr<DevBuf> buf;
+    cplx* p = nullptr;
+    int nd = 0;
+    int64_t d[MAXD] = {0};
+    int64_t s[MAXD] = {0};
+
+    int64_t numel() const {
+        int64_t n = 1;
+        for (int i = 0; i < nd; ++i) n *= d[i];
+        return n;
+    }
+    bool contiguous() const {
+        int64_t st = 1;
+        for (int i = nd - 1; i >= 0; --i) {
+            if (d[i] != 1 && s[i] != st) return false;
+            st *= d[i];
+        }
+        return true;
+    }
+    bool defined() const { return p != nullptr || numel() == 0; }
+    Tensor slice(int dim, int64_t start, int64_t len) const {
+        Tensor t = *this;
+        t.p = p + start * s[dim];
+        t.d[dim] = len;
+        return t;
+    }
+    Tensor index(int64_t i) const {  // drop leading dim
+        Tensor t;
+        t.buf = buf;
+        t.p = p + i * s[0];
+        t.nd = nd - 1;
+        for (int k = 1; k < nd; ++k) { t.d[k - 1] = d[k]; t.s[k - 1] = s[k]; }
+        return t;
+    }
+    // reinterpret a contiguous tensor with a new shape
+    Tensor reshape(std::vector<int64_t> shape) const;
+    // permuted view: new dim k = old dim perm[k]
+    Tensor permute(const std::vector<int>& perm) const;
+    std::vector<int64_t> shape() const { return std::vector<int64_t>(d, d + nd); }
+};
+
+Tensor empty(Dev& D, std::vector<int64_t> shape);
+Tensor zeros(Dev& D, std::vector<int64_t> shape);
+// wrap external device memory (not owned)
+Tensor wrap(cplx* p, std::vector<int64_t> shape);
+
+// ---------------------------------------------------------------------------
+// elementwise kernels (kernels_elem.cu)
+// ---------------------------------------------------------------------------
+// y = alpha * op(x) + beta * y over identical shapes; beta == 0 overwrites.
+void axpby(Dev& D, cplx alpha, const Tensor& x, bool conjx, cplx beta, Tensor& y);
+void fill(Dev& D, Tensor& y, cplx v);
+// max |y| over all elements (host result; synchronises the stream)
+double max_abs(Dev& D, const Tensor& y);
+// per-leading-index max |y| into dev out[R] (double), no sync
+void max_abs_rows(Dev& D, const Tensor& y, double* out_dev);
+
+// ---------------------------------------------------------------------------
+// FP64 complex GEMM (gemm_f64.cu):  C[b][m][n] = alpha sum_k op(A)[b][m][k] op(B)[b][k][n] + beta C
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+    int64_t M, N, K, batch;
+    const cplx* A;
+    int64_t sAb, sAm, sAk;
+    bool cA;
+    const cplx* B;
+    int64_t sBb, sBk, sBn;
+    bool cB;
+    cplx* C;
+    int64_t sCb, sCm, sCn;
+    cplx alpha, beta;
+};
+void gemm_f64(Dev& D, const GemmArgs& g);
+
+// tensor-core split-precision GEMM (gemm_tc.cu); prec = LRCC_MIXED_*
+bool gemm_tc_available();
+void gemm_tc(Dev& D, const GemmArgs& g, int prec);
+
+// ---------------------------------------------------------------------------
+// contraction engine (engine.cu)
+// ---------------------------------------------------------------------------
+// einsum "ab,bc->ac"-style, single-letter labels, every label in >= 2 operands
+// prec: LRCC_FP64 or a mixed mode (large GEMMs go to the tensor cores)
+void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A, bool cA, const Tensor& B,
+         bool cB, cplx beta, Tensor& C, int prec = LRCC_FP64);
+// allocate C from the spec and operands, then C = alpha * A.B
+Tensor ein_new(Dev& D, const std::string& spec, cplx alpha, const Tensor& A, bool cA, const Tensor& B,
+               bool cB, int prec = LRCC_FP64);
+// permuted axpby by labels: y(spec rhs) = alpha * x(spec lhs) + beta * y
+void perm_axpby(Dev& D, const std::string& spec, cplx alpha, const Tensor& x, cplx beta, Tensor& y);
+
+// particle-particle ladder Z = 1/2 sum_ef <ab||ef> X_ij^ef (X, Z: [R][O][O][V][V]),
+// <ab|ef> = sum_L Bvv^L_ae Bvv^L_bf; transpose -> Bvv conjugated.
+struct LadderCtx {
+    Tensor Bvv;      // [L][V][V]
+    int slab_rows = 0;
+};
+void ladder(Dev& D, LadderCtx& L, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose, int prec);
+
+// pair index of (p<q) among n, row-major strict upper triangle
+__host__ __device__ inline int64_t pair_index(int64_t p, int64_t q, int64_t n) {
+    return p * (2 * n - p - 1) / 2 + (q - p - 1);
+}

@@ -1,0 +1,351 @@
+// Contraction program: primal evaluation and the forward / reverse sweeps.
+//
+// A slot holds a tensor; an op writes one slot as a sum of terms, each term a
+// bilinear contraction (EIN), a permuted copy (PERM) or the particle-particle
+// ladder (LADDER, linear in its operand with constant integrals).  The
+// transpose rules are the ones of bilinear maps: for C += c A.B,
+//   dC += c (dA.B + A.dB),   Abar += c Cbar.B,   Bbar += c A.Cbar
+// (holomorphic, no conjugation), a permutation transposes to the inverse
+// permutation, and the ladder transposes to the ladder built from B^T = conj B.
+// Tangents and cotangents carry a leading right-hand-side label 'Z'.
+#include "prog.h"
+
+#include <algorithm>
+
+namespace {
+std::string lhs_a(const std::string& s) { return s.substr(0, s.find(',')); }
+std::string lhs_b(const std::string& s) {
+    size_t c = s.find(','), a = s.find("->");
+    return s.substr(c + 1, a - c - 1);
+}
+std::string rhs(const std::string& s) { return s.substr(s.find("->") + 2); }
+std::string perm_in(const std::string& s) { return s.substr(0, s.find("->")); }
+
+Tensor add_lead(const Tensor& t, int64_t R) {
+    // view t [..] (contiguous) as [R][..] when t already has R leading
+    (void)R;
+    return t;
+}
+
+Tensor as5(const Tensor& t, int64_t R, int64_t O, int64_t V) { return t.reshape({R, O, O, V, V}); }
+}  // namespace
+
+int Prog::input(std::vector<int64_t> shape) {
+    Tensor t;
+    t.nd = (int)shape.size();
+    for (int k = 0; k < t.nd; ++k) t.d[k] = shape[k];
+    val.push_back(t);
+    active.push_back(1);
+    is_const.push_back(0);
+    inputs.push_back((int)val.size() - 1);
+    return (int)val.size() - 1;
+}
+
+int Prog::cst(const Tensor& t) {
+    val.push_back(t);
+    active.push_back(0);
+    is_const.push_back(1);
+    return (int)val.size() - 1;
+}
+
+int Prog::op(std::vector<Term> terms) {
+    Op o;
+    o.terms = terms;
+    val.push_back(Tensor());
+    bool act = false;
+    for (auto& t : terms) {
+        if (t.a >= 0 && active[t.a]) act = true;
+        if (t.b >= 0 && active[t.b]) act = true;
+    }
+    active.push_back(act);
+    is_const.push_back(0);
+    o.out = (int)val.size() - 1;
+    // record the output shape now (operands' shapes are known)
+    ops.push_back(o);
+    std::vector<int64_t> sh = out_shape(o);
+    Tensor t;
+    t.nd = (int)sh.size();
+    for (int k = 0; k < t.nd; ++k) t.d[k] = sh[k];
+    val[o.out] = t;
+    return o.out;
+}
+
+std::vector<int64_t> Prog::out_shape(const Op& op) const {
+    const Term& t = op.terms.at(0);
+    const Tensor& A = val[t.a];
+    std::vector<int64_t> sh;
+    if (t.kind == TK_LADDER) return A.shape();
+    if (t.kind == TK_PERM) {
+        std::string lx = perm_in(t.spec), ly = rhs(t.spec);
+        for (char c : ly) sh.push_back(A.d[lx.find(c)]);
+        return sh;
+    }
+    std::string la = lhs_a(t.spec), lb = lhs_b(t.spec), lc = rhs(t.spec);
+    const Tensor& B = val[t.b];
+    for (char c : lc) {
+        size_t p = la.find(c);
+        if (p != std::string::npos) sh.push_back(A.d[p]);
+        else sh.push_back(B.d[lb.find(c)]);
+    }
+    return sh;
+}
+
+void Prog::apply_term(Dev& D, const Term& t, cplx beta, Tensor& out, int prec) {
+    cplx c = t.c;
+    if (t.kind == TK_EIN) {
+        ein(D, t.spec, c, val[t.a], false, val[t.b], false, beta, out, prec);
+    } else if (t.kind == TK_PERM) {
+        perm_axpby(D, t.spec, c, val[t.a], beta, out);
+    } else {
+        Tensor x = as5(val[t.a], 1, O, V);
+        Tensor z = as5(out, 1, O, V);
+        ladder(D, *lad, x, c, beta, z, false, prec);
+    }
+}
+
+void Prog::eval(Dev& D, const std::vector<Tensor>& in, int prec) {
+    if (in.size() != inputs.size()) throw LrccError(LRCC_EINVAL, "program input count");
+    for (size_t k = 0; k < in.size(); ++k) {
+        const Tensor& d = val[inputs[k]];
+        REQUIRE(in[k].nd == d.nd, "program input rank");
+        for (int q = 0; q < d.nd; ++q) REQUIRE(in[k].d[q] == d.d[q], "program input shape");
+        val[inputs[k]] = in[k];
+    }
+    for (auto& o : ops) {
+        Tensor out = empty(D, val[o.out].shape());
+        bool first = true;
+        for (auto& t : o.terms) {
+            apply_term(D, t, first ? mkc(0.0) : mkc(1.0), out, prec);
+            first = false;
+        }
+        val[o.out] = out;
+    }
+}
+
+std::vector<Tensor> Prog::jvp(Dev& D, const std::vector<Tensor>& tin, const std::vector<int>& outs, int prec) {
+    const int n = (int)val.size();
+    std::vector<Tensor> tan(n);
+    int64_t R = tin.at(0).d[0];
+    for (size_t k = 0; k < inputs.size(); ++k) tan[inputs[k]] = tin[k];
+    // last use of each slot's tangent (as an operand), outputs kept
+    std::vector<int> last(n, -1);
+    for (int k = 0; k < (int)ops.size(); ++k)
+        for (auto& t : ops[k].terms) {
+            if (t.a >= 0) last[t.a] = k;
+            if (t.b >= 0) last[t.b] = k;
+        }
+    for (int o : outs) last[o] = (int)ops.size();
+    for (size_t k = 0; k < inputs.size(); ++k) last[inputs[k]] = (int)ops.size();
+    for (int k = 0; k < (int)ops.size(); ++k) {
+        const Op& o = ops[k];
+        if (!active[o.out]) continue;
+        std::vector<int64_t> sh = val[o.out].shape();
+        sh.insert(sh.begin(), R);
+        Tensor out = empty(D, sh);
+        bool first = true;
+        auto beta = [&]() { cplx b = first ? mkc(0.0) : mkc(1.0); first = false; return b; };
+        for (auto& t : o.terms) {
+            if (t.kind == TK_EIN) {
+                std::string la = lhs_a(t.spec), lb = lhs_b(t.spec), lc = rhs(t.spec);
+                if (active[t.a]) ein(D, "Z" + la + "," + lb + "->Z" + lc, t.c, tan[t.a], false, val[t.b], false, beta(), out, prec);
+                if (active[t.b]) ein(D, la + ",Z" + lb + "->Z" + lc, t.c, val[t.a], false, tan[t.b], false, beta(), out, prec);
+            } else if (t.kind == TK_PERM) {
+                if (active[t.a]) perm_axpby(D, "Z" + perm_in(t.spec) + "->Z" + rhs(t.spec), t.c, tan[t.a], beta(), out);
+            } else {
+                if (active[t.a]) {
+                    Tensor x = as5(tan[t.a], R, O, V), z = as5(out, R, O, V);
+                    ladder(D, *lad, x, t.c, beta(), z, false, prec);
+                }
+            }
+        }
+        if (first) fill(D, out, mkc(0.0));
+        tan[o.out] = out;
+        for (auto& t : o.terms) {
+            if (t.a >= 0 && last[t.a] == k) tan[t.a] = Tensor();
+            if (t.b >= 0 && last[t.b] == k) tan[t.b] = Tensor();
+        }
+    }
+    std::vector<Tensor> res;
+    for (int o : outs) res.push_back(tan[o]);
+    return res;
+}
+
+std::vector<Tensor> Prog::vjp(Dev& D, const std::vector<Tensor>& cot, const std::vector<int>& outs, int prec) {
+    const int n = (int)val.size();
+    std::vector<Tensor> adj(n);
+    std::vector<char> has(n, 0);
+    int64_t R = -1;
+    for (size_t k = 0; k < outs.size(); ++k) {
+        if (cot[k].p == nullptr) continue;
+        adj[outs[k]] = cot[k];
+        has[outs[k]] = 1;
+        R = cot[k].d[0];
+    }
+    if (R < 0) throw LrccError(LRCC_EINVAL, "vjp: all cotangents are zero");
+    // adjoints of output slots are only read, never accumulated into in place:
+    // copy them so later accumulation (if an output feeds another op) is safe
+    auto acc = [&](int slot, auto&& write) {
+        if (!active[slot]) return;
+        if (!has[slot]) {
+            std::vector<int64_t> sh = val[slot].shape();
+            sh.insert(sh.begin(), R);
+            adj[slot] = empty(D, sh);
+            write(adj[slot], mkc(0.0));
+            has[slot] = 1;
+        } else {
+            write(adj[slot], mkc(1.0));
+        }
+    };
+    std::vector<char> owned(n, 0);
+    for (int k = (int)ops.size() - 1; k >= 0; --k) {
+        const Op& o = ops[k];
+        if (!active[o.out] || !has[o.out]) continue;
+        Tensor cb = adj[o.out];
+        for (auto& t : o.terms) {
+            if (t.kind == TK_EIN) {
+                std::string la = lhs_a(t.spec), lb = lhs_b(t.spec), lc = rhs(t.spec);
+                if (active[t.a])
+                    acc(t.a, [&](Tensor& dst, cplx b) {
+                        ein(D, "Z" + lc + "," + lb + "->Z" + la, t.c, cb, false, val[t.b], false, b, dst, prec);
+                    });
+                if (active[t.b])
+                    acc(t.b, [&](Tensor& dst, cplx b) {
+                        ein(D, la + ",Z" + lc + "->Z" + lb, t.c, val[t.a], false, cb, false, b, dst, prec);
+                    });
+            } else if (t.kind == TK_PERM) {
+                if (active[t.a])
+                    acc(t.a, [&](Tensor& dst, cplx b) {
+                        perm_axpby(D, "Z" + rhs(t.spec) + "->Z" + perm_in(t.spec), t.c, cb, b, dst);
+                    });
+            } else {
+                if (active[t.a])
+                    acc(t.a, [&](Tensor& dst, cplx b) {
+                        Tensor x = as5(cb, R, O, V), z = as5(dst, R, O, V);
+                        ladder(D, *lad, x, t.c, b, z, true, prec);
+                    });
+            }
+        }
+        bool is_in = std::find(inputs.begin(), inputs.end(), o.out) != inputs.end();
+        if (!is_in) adj[o.out] = Tensor();
+    }
+    std::vector<Tensor> res;
+    for (int s : inputs) {
+        if (!has[s]) {
+            std::vector<int64_t> sh = val[s].shape();
+            sh.insert(sh.begin(), R);
+            res.push_back(zeros(D, sh));
+        } else {
+            res.push_back(adj[s]);
+        }
+    }
+    (void)owned;
+    return res;
+}
+
+// ---------------------------------------------------------------------------
+// integrals and the CCSD residual
+// ---------------------------------------------------------------------------
+Tensor anti_block(Dev& D, const Tensor& B, int64_t p0, int64_t np, int64_t q0, int64_t nq, int64_t r0, int64_t nr,
+                  int64_t s0, int64_t ns) {
+    auto sub = [&](int64_t x0, int64_t nx, int64_t y0, int64_t ny) { return B.slice(1, x0, nx).slice(2, y0, ny); };
+    Tensor out = empty(D, {np, nq, nr, ns});
+    // <pq|rs> = sum_L B^L_pr B^L_qs ;  <pq|sr> = sum_L B^L_ps B^L_qr
+    ein(D, "Lpr,Lqs->pqrs", mkc(1.0), sub(p0, np, r0, nr), false, sub(q0, nq, s0, ns), false, mkc(0.0), out);
+    ein(D, "Lps,Lqr->pqrs", mkc(-1.0), sub(p0, np, s0, ns), false, sub(q0, nq, r0, nr), false, mkc(1.0), out);
+    return out;
+}
+
+// Spin-orbital CCSD (Stanton, Gauss, Watts, Bartlett 1991 intermediates) for a
+// general Fock matrix, with the driver terms in their general complex form
+// (<ab||ij>, f_ai).  Terms are regrouped for a density-fitted ladder:
+//   1/2 sum_ef tau_ij^ef W_abef = ladder(tau) - 1/2 P(ab) sum_m t_m^b Q_amij
+//                                 + 1/8 sum_mn tau_mn^ab P_mnij,
+// Q_amij = sum_ef <am||ef> tau_ij^ef, P_mnij = sum_ef <mn||ef> tau_ij^ef, and the
+// last piece is merged into W_mnij (its 1/4 P_mnij becomes 1/2 P_mnij).
+void build_ccsd(CCProg& cp, const Ham& H, LadderCtx* lad) {
+    Prog& P = cp.P;
+    P.lad = lad;
+    int64_t O = H.foo.d[0], V = H.fvv.d[0];
+    P.O = (int)O;
+    P.V = (int)V;
+    const bool w = H.w;
+    int t1 = P.input({O, V}), t2 = P.input({O, O, V, V});
+    cp.t1 = t1;
+    cp.t2 = t2;
+    int foo = P.cst(H.foo), fov = P.cst(H.fov), fvo = P.cst(H.fvo), fvv = P.cst(H.fvv);
+    int oooo = -1, ooov = -1, oovo = -1, ovoo = -1, oovv = -1, vvoo = -1, ovov = -1, ovvo = -1, ovvv = -1, vovv = -1,
+        vvvo = -1;
+    if (w) {
+        oooo = P.cst(H.oooo); ooov = P.cst(H.ooov); oovo = P.cst(H.oovo); ovoo = P.cst(H.ovoo);
+        oovv = P.cst(H.oovv); vvoo = P.cst(H.vvoo); ovov = P.cst(H.ovov); ovvo = P.cst(H.ovvo);
+        ovvv = P.cst(H.ovvv); vovv = P.cst(H.vovv); vvvo = P.cst(H.vvvo);
+    }
+    int taut = P.op({PERM(1, "ijab->ijab", t2), EIN(0.5, "ia,jb->ijab", t1, t1), EIN(-0.5, "ib,ja->ijab", t1, t1)});
+    int tau = P.op({PERM(1, "ijab->ijab", t2), EIN(1, "ia,jb->ijab", t1, t1), EIN(-1, "ib,ja->ijab", t1, t1)});
+
+    std::vector<Term> fae = {PERM(1, "ae->ae", fvv), EIN(-0.5, "me,ma->ae", fov, t1)};
+    std::vector<Term> fmi = {PERM(1, "mi->mi", foo), EIN(0.5, "ie,me->mi", t1, fov)};
+    std::vector<Term> fme = {PERM(1, "me->me", fov)};
+    if (w) {
+        fae.push_back(EIN(1, "mf,mafe->ae", t1, ovvv));
+        fae.push_back(EIN(-0.5, "mnaf,mnef->ae", taut, oovv));
+        fmi.push_back(EIN(1, "ne,mnie->mi", t1, ooov));
+        fmi.push_back(EIN(0.5, "inef,mnef->mi", taut, oovv));
+        fme.push_back(EIN(1, "nf,mnef->me", t1, oovv));
+    }
+    int Fae = P.op(fae), Fmi = P.op(fmi), Fme = P.op(fme);
+
+    std::vector<Term> r1 = {PERM(1, "ai->ia", fvo), EIN(1, "ie,ae->ia", t1, Fae), EIN(-1, "ma,mi->ia", t1, Fmi),
+                            EIN(1, "imae,me->ia", t2, Fme)};
+    if (w) {
+        r1.push_back(EIN(-1, "nf,naif->ia", t1, ovov));
+        r1.push_back(EIN(-0.5, "imef,maef->ia", t2, ovvv));
+        r1.push_back(EIN(-0.5, "mnae,nmei->ia", t2, oovo));
+    }
+    cp.R1 = P.op(r1);
+
+    int Fbe = P.op({PERM(1, "be->be", Fae), EIN(-0.5, "mb,me->be", t1, Fme)});
+    int Fmj = P.op({PERM(1, "mj->mj", Fmi), EIN(0.5, "je,me->mj", t1, Fme)});
+    int Xa = P.op({EIN(1, "ijae,be->ijab", t2, Fbe)});
+    int Xb = P.op({EIN(1, "imab,mj->ijab", t2, Fmj)});
+    std::vector<Term> r2 = {PERM(1, "ijab->ijab", Xa), PERM(-1, "ijab->ijba", Xa), PERM(-1, "ijab->ijab", Xb),
+                            PERM(1, "ijab->jiab", Xb)};
+    if (w) {
+        r2.push_back(PERM(1, "abij->ijab", vvoo));
+        int Xw = P.op({EIN(1, "je,mnie->mnij", t1, ooov)});
+        int Pm = P.op({EIN(1, "ijef,mnef->mnij", tau, oovv)});
+        int Wmn = P.op({PERM(1, "mnij->mnij", oooo), PERM(1, "mnij->mnij", Xw), PERM(-1, "mnij->mnji", Xw),
+                        PERM(0.5, "mnij->mnij", Pm)});
+        r2.push_back(EIN(0.5, "mnab,mnij->ijab", tau, Wmn));
+        r2.push_back(LADDER(1, tau));
+        int Q = P.op({EIN(1, "amef,ijef->amij", vovv, tau)});
+        int S = P.op({EIN(1, "amij,mb->ijab", Q, t1)});
+        r2.push_back(PERM(-0.5, "ijab->ijab", S));
+        r2.push_back(PERM(0.5, "ijab->ijba", S));
+        int Zt = P.op({PERM(0.5, "jnfb->jnfb", t2), EIN(1, "jf,nb->jnfb", t1, t1)});
+        int Wmbej = P.op({PERM(1, "mbej->mbej", ovvo), EIN(1, "jf,mbef->mbej", t1, ovvv),
+                          EIN(-1, "nb,mnej->mbej", t1, oovo), EIN(-1, "jnfb,mnef->mbej", Zt, oovv)});
+        int ring1 = P.op({EIN(1, "imae,mbej->ijab", t2, Wmbej)});
+        int tmp = P.op({EIN(1, "ie,mbej->mbij", t1, ovvo)});
+        int ring = P.op({PERM(1, "ijab->ijab", ring1), EIN(-1, "ma,mbij->ijab", t1, tmp)});
+        r2.push_back(PERM(1, "ijab->ijab", ring));
+        r2.push_back(PERM(-1, "ijab->jiab", ring));
+        r2.push_back(PERM(-1, "ijab->ijba", ring));
+        r2.push_back(PERM(1, "ijab->jiba", ring));
+        int t3 = P.op({EIN(1, "ie,abej->ijab", t1, vvvo)});
+        r2.push_back(PERM(1, "ijab->ijab", t3));
+        r2.push_back(PERM(-1, "ijab->jiab", t3));
+        int t4 = P.op({EIN(1, "ma,mbij->ijab", t1, ovoo)});
+        r2.push_back(PERM(-1, "ijab->ijab", t4));
+        r2.push_back(PERM(1, "ijab->ijba", t4));
+    }
+    cp.R2 = P.op(r2);
+
+    std::vector<Term> e = {EIN(1, "ia,ia->", fov, t1)};
+    if (w) {
+        e.push_back(EIN(0.25, "ijab,ijab->", oovv, t2));
+        int Ej = P.op({EIN(1, "ijab,ia->jb", oovv, t1)});
+        e.push_back(EIN(0.5, "jb,jb->", Ej, t1));
+    }
+    cp.E = P.op(e);
+}

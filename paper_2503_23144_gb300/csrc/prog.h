@@ -1,0 +1,71 @@
+// Contraction program ("tape") for the coupled-cluster residual, with the
+// forward (Jacobian-vector) and reverse (transpose-Jacobian) sweeps that give
+// sigma = A X and A^T lambda over R right-hand sides at once.
+#pragma once
+#include "lrcc_internal.h"
+
+enum TermKind { TK_EIN = 0, TK_PERM = 1, TK_LADDER = 2 };
+
+struct Term {
+    TermKind kind;
+    cplx c;
+    std::string spec;  // "ab,bc->ac" (EIN) or "ab->ba" (PERM)
+    int a = -1, b = -1;
+};
+
+inline Term EIN(double c, const char* spec, int a, int b) { return Term{TK_EIN, mkc(c), spec, a, b}; }
+inline Term PERM(double c, const char* spec, int a) { return Term{TK_PERM, mkc(c), spec, a, -1}; }
+inline Term LADDER(double c, int a) { return Term{TK_LADDER, mkc(c), "", a, -1}; }
+
+struct Op {
+    int out;
+    std::vector<Term> terms;
+};
+
+struct Prog {
+    std::vector<Tensor> val;        // primal value of each slot
+    std::vector<char> active;       // slot depends on the inputs
+    std::vector<char> is_const;     // slot is a fixed constant tensor
+    std::vector<Op> ops;
+    std::vector<int> inputs;        // input slots (amplitudes)
+    LadderCtx* lad = nullptr;
+    int O = 0, V = 0;
+
+    int input(std::vector<int64_t> shape);
+    int cst(const Tensor& t);
+    int op(std::vector<Term> terms);
+
+    // primal evaluation for the given input values (R = 1, no leading batch)
+    void eval(Dev& D, const std::vector<Tensor>& in, int prec);
+    // forward sweep: tangents of inputs [R][...] -> tangents of `outs`
+    std::vector<Tensor> jvp(Dev& D, const std::vector<Tensor>& tin, const std::vector<int>& outs, int prec);
+    // reverse sweep: cotangents of `outs` [R][...] (undefined tensor = zero)
+    // -> cotangents of the inputs (holomorphic transpose, no conjugation)
+    std::vector<Tensor> vjp(Dev& D, const std::vector<Tensor>& cot, const std::vector<int>& outs, int prec);
+
+  private:
+    std::vector<int64_t> out_shape(const Op& op) const;
+    void apply_term(Dev& D, const Term& t, cplx beta, Tensor& out, int prec);
+};
+
+// Hamiltonian blocks on the device.  <pq||rs> = <pq|rs> - <pq|sr>.
+struct Ham {
+    bool w = false;  // two-body part present
+    Tensor foo, fov, fvo, fvv;
+    Tensor oooo, ooov, oovo, ovoo, oovv, vvoo, ovov, ovvo, ovvv, vovv, vvvo;
+};
+
+// slots of a CCSD residual program
+struct CCProg {
+    Prog P;
+    int t1 = -1, t2 = -1;   // inputs
+    int R1 = -1, R2 = -1, E = -1;
+};
+
+// Build the spin-orbital CCSD residual R(T), energy E(T) (general Fock
+// matrix; two-body terms only if H.w).
+void build_ccsd(CCProg& cp, const Ham& H, LadderCtx* lad);
+
+// Antisymmetrised block <PQ||RS> from B [L][N][N]; ranges (start, length).
+Tensor anti_block(Dev& D, const Tensor& B, int64_t p0, int64_t np, int64_t q0, int64_t nq, int64_t r0, int64_t nr,
+                  int64_t s0, int64_t ns);

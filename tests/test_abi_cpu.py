@@ -1,0 +1,88 @@
+"""Host-side checks of the C ABI (no GPU): the library builds and loads, it
+exports every function that include/lrcc.h declares, and argument validation
+rejects bad inputs before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2503_23144_gb300 import build, lrcc
+    if not os.path.exists(lrcc._LIB_PATH):
+        build.build()
+    return lrcc
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lrcc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lrcc_[a-z_]+)\s*\(", src)))
+
+
+def test_header_symbols_exported(lib):
+    names = _declared()
+    assert "lrcc_setup" in names and "lrcc_solve" in names
+    so = ctypes.CDLL(lib._LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), n
+    bound = {s[0] for s in lib.SIGNATURES}
+    assert set(names) <= bound
+
+
+def test_default_options(lib):
+    o = lib.lrcc_default_options()
+    assert o.max_iter == 200 and o.diis_size == 8 and o.prec == lib.LRCC_FP64
+    assert 0 < o.r_tol < 1e-6 and 0 < o.x_tol < 1e-6
+
+
+def _system(O=3, V=5, L=4, seed=0):
+    return synth.make_system(O, V, L, seed)
+
+
+def test_setup_rejects_non_hermitian(lib):
+    s = _system()
+    B = s["B"].copy()
+    B[0, 0, 1] += 0.1
+    with pytest.raises(lib.LrccError) as e:
+        lib.lrcc_setup(s["eps"], B, s["mu"], s["O"], s["V"])
+    assert e.value.status == lib.LRCC_EINVAL
+    mu = s["mu"].copy()
+    mu[1, 2, 3] += 0.1j
+    with pytest.raises(lib.LrccError) as e:
+        lib.lrcc_setup(s["eps"], s["B"], mu, s["O"], s["V"])
+    assert e.value.status == lib.LRCC_EINVAL
+
+
+def test_setup_rejects_bad_ordering_and_sizes(lib):
+    s = _system()
+    eps = s["eps"].copy()
+    eps[0] = 10.0                       # occupied above the virtuals
+    with pytest.raises(lib.LrccError) as e:
+        lib.lrcc_setup(eps, s["B"], s["mu"], s["O"], s["V"])
+    assert e.value.status == lib.LRCC_EINVAL
+    eps = s["eps"].copy()
+    eps[4] = np.nan
+    with pytest.raises(lib.LrccError) as e:
+        lib.lrcc_setup(eps, s["B"], s["mu"], s["O"], s["V"])
+    assert e.value.status == lib.LRCC_EINVAL
+    s1 = _system(O=1, V=5)
+    with pytest.raises(lib.LrccError) as e:
+        lib.lrcc_setup(s1["eps"], s1["B"], s1["mu"], 1, 5)
+    assert e.value.status == lib.LRCC_EINVAL
+
+
+def test_pack_roundtrip(lib):
+    rng = np.random.default_rng(0)
+    t1 = rng.standard_normal((2, 3, 4)) + 0j
+    t2 = rng.standard_normal((2, 3, 3, 4, 4)) + 1j
+    flat = lib.pack_amplitudes(t1, t2)
+    a, b = lib.unpack_amplitudes(flat, 3, 4)
+    assert np.array_equal(a, t1) and np.array_equal(b, t2)

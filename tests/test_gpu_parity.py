@@ -1,0 +1,165 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Sizes are chosen so that the oracle finishes in seconds while the GPU
+contractions span several 64x64 tiles and ragged tails (odd O and V)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import ccsd, fci
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2503_23144_gb300 import build, lrcc
+    build.build()
+    assert torch.cuda.is_available()
+    return lrcc
+
+
+def _ctx(L, s, **kw):
+    o = L.lrcc_default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return L.lrcc_setup(s["eps"], s["B"], s["mu"], s["O"], s["V"], o)
+
+
+def _rand(lay, R, seed, scale):
+    a = synth.random_amplitudes(lay.O, lay.V, R, seed=seed, scale=scale)
+    xs = [lay.join(torch.as_tensor(a["t1"][r]), torch.as_tensor(a["t2u"][r])) for r in range(R)]
+    return xs
+
+
+def _flat(lay, xs):
+    t1 = np.stack([lay.split(x)[0].numpy() for x in xs])
+    t2 = np.stack([lay.expand(lay.split(x)[1]).numpy() for x in xs])
+    return t1, t2
+
+
+def _unique(L, lay, flat):
+    t1, t2 = L.unpack_amplitudes(flat, lay.O, lay.V)
+    return [lay.join(torch.as_tensor(t1[r]), lay.pack(torch.as_tensor(t2[r]))) for r in range(flat.shape[0])]
+
+
+SYS = dict(O=5, V=19, L=30, seed=21)
+
+
+@pytest.fixture(scope="module")
+def small(L):
+    s = synth.make_system(**SYS)
+    model = ccsd.build(s)
+    return s, model, _ctx(L, s)
+
+
+def test_residual_and_energy_parity(L, small):
+    s, model, ctx = small
+    lay = model.lay
+    xs = _rand(lay, 2, 3, 0.1)
+    t1, t2 = _flat(lay, xs)
+    out = L.lrcc_residual(ctx, L.LRCC_RES_T, None, L.pack_amplitudes(t1, t2))
+    E = L.lrcc_residual(ctx, L.LRCC_RES_ENERGY, None, L.pack_amplitudes(t1, t2))
+    got = _unique(L, lay, out)
+    for r, x in enumerate(xs):
+        ref = model.R(x)
+        assert float((got[r] - ref).abs().max()) < 1e-12 * float(ref.abs().max())
+        e = complex(model.E(x))
+        assert abs(E[r] - e) < 1e-13 * abs(e)
+    # the doubles block of the output is antisymmetric
+    _, r2 = L.unpack_amplitudes(out, lay.O, lay.V)
+    assert np.abs(r2 + r2.transpose(0, 2, 1, 3, 4)).max() < 1e-14 * np.abs(r2).max()
+
+
+def test_sigma_and_transpose_parity(L, small):
+    s, model, ctx = small
+    lay = model.lay
+    t = _rand(lay, 1, 7, 0.1)[0]
+    xs = _rand(lay, 3, 8, 0.3)
+    tf = L.pack_amplitudes(*_flat(lay, [t]))[0]
+    xf = L.pack_amplitudes(*_flat(lay, xs))
+    sig = _unique(L, lay, L.lrcc_residual(ctx, L.LRCC_RES_SIGMA, tf, xf))
+    vjp = _unique(L, lay, L.lrcc_residual(ctx, L.LRCC_RES_VJP, tf, xf))
+    for r, x in enumerate(xs):
+        ref = model.jvp(t, x)
+        assert float((sig[r] - ref).abs().max()) < 1e-12 * float(ref.abs().max())
+        ref = model.vjp(t, x)
+        assert float((vjp[r] - ref).abs().max()) < 1e-12 * float(ref.abs().max())
+
+
+def test_xi_parity(L, small):
+    s, model, ctx = small
+    lay = model.lay
+    t = _rand(lay, 1, 9, 0.1)[0]
+    tf = L.pack_amplitudes(*_flat(lay, [t]))[0]
+    for comp in range(3):
+        got = _unique(L, lay, L.lrcc_residual(ctx, L.LRCC_RES_XI, tf, tf[None], comp=comp))[0]
+        ref = ccsd.dipole_model(s, comp).R(t)
+        assert float((got - ref).abs().max()) < 1e-13 * float(ref.abs().max())
+
+
+def test_ladder_parity(L, small):
+    s, model, ctx = small
+    O, V = s["O"], s["V"]
+    lay = model.lay
+    xs = _rand(lay, 3, 11, 1.0)
+    _, x2 = _flat(lay, xs)
+    vvvv = model.H.vvvv.numpy()
+    ref = 0.5 * np.einsum('abef,rijef->rijab', vvvv, x2)
+    refT = 0.5 * np.einsum('efab,rijef->rijab', vvvv, x2)
+    xd = torch.as_tensor(x2).cuda()
+    z = L.lrcc_ladder_dev(ctx, xd).cpu().numpy()
+    zt = L.lrcc_ladder_dev(ctx, xd, transpose=True).cpu().numpy()
+    assert np.abs(z - ref).max() < 1e-13 * np.abs(ref).max()
+    assert np.abs(zt - refT).max() < 1e-13 * np.abs(refT).max()
+
+
+def test_autograd_wrapper(L):
+    s = synth.make_system(2, 3, 4, seed=5)
+    ctx = _ctx(L, s)
+    n = ctx.n_amp
+    g = torch.Generator().manual_seed(0)
+    t = (0.1 * torch.randn(n, dtype=torch.complex128, generator=g)).cuda().requires_grad_(True)
+    F = L.ResidualFn()
+    assert torch.autograd.gradcheck(lambda x: F.apply(ctx, x), (t,), eps=1e-6, atol=1e-8, rtol=1e-6)
+
+
+def test_ground_state_and_alpha_c1(L):
+    cfg = synth.CONFIGS["c1"]
+    s = synth.make_system(cfg["O"], cfg["V"], cfg["L"], cfg["seed"])
+    oms = [0.0, 0.05]
+    ref, P = ccsd.polarizability(s, (0, 1, 2), oms, tol=1e-11, return_parts=True)
+    ctx = _ctx(L, s, r_tol=1e-11, x_tol=1e-10)
+    E, itT, itL = L.lrcc_ccsd_ground(ctx)
+    assert abs(E - complex(P["E"])) < 1e-11 * abs(E)
+    alpha, err = L.lrcc_solve(ctx, oms, [0, 1, 2])
+    assert np.abs(alpha - ref).max() < 1e-9 * np.abs(ref).max()
+    assert err.max() < 1e-10
+
+
+def test_two_electron_alpha_equals_sos(L):
+    cfg = synth.CONFIGS["c1b"]
+    s = synth.make_system(cfg["O"], cfg["V"], cfg["L"], cfg["seed"])
+    oms = list(cfg["omegas"])
+    ctx = _ctx(L, s, r_tol=1e-12, x_tol=1e-11)
+    E, _, _ = L.lrcc_ccsd_ground(ctx)
+    Ef, _, _, _, eref = fci.fci_states(ccsd.fock_of(s), s["B"], s["O"])
+    assert abs(E - (Ef[0] - eref)) < 1e-10
+    alpha, _ = L.lrcc_solve(ctx, oms, [0, 1, 2])
+    sos, _, _ = fci.sos_polarizability(ccsd.fock_of(s), s["B"], s["mu"], s["O"], (0, 1, 2), oms)
+    assert np.abs(alpha - sos).max() < 1e-9 * np.abs(sos).max()
+
+
+def test_rhs_chunking_invariance_and_state(L):
+    s = synth.make_system(3, 9, 12, seed=4)
+    ctx = _ctx(L, s)
+    with pytest.raises(L.LrccError) as e:
+        L.lrcc_solve(ctx, [0.0], [0])
+    assert e.value.status == L.LRCC_ESTATE
+    L.lrcc_ccsd_ground(ctx)
+    a12, _ = L.lrcc_solve(ctx, [0.0, 0.03], [0, 1, 2])
+    ctx2 = _ctx(L, s, rhs_chunk=4)
+    L.lrcc_ccsd_ground(ctx2)
+    a4, _ = L.lrcc_solve(ctx2, [0.0, 0.03], [0, 1, 2])
+    assert np.abs(a12 - a4).max() < 1e-9 * np.abs(a12).max()
