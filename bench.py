@@ -1,0 +1,318 @@
+"""Benchmark: LR-CCSD residual throughput on one GB300 (or N replicas).
+
+One step = the two residual maps that every response iteration applies, on a
+batch of right-hand sides (3 dipole components x 4 frequencies):
+sigma = A X (Eq. 30) and the transpose product A^T Y (left response,
+Eq. 32), at the converged CCSD amplitudes of the synthetic system.
+Metric: nominal complex flops per second,
+    F_sigma = 8 [R (P_O P_V^2 + O^3 V^3) + P_V^2 L]   per map,
+counted once per map regardless of the contraction order or precision scheme.
+Alongside: alpha(omega) solves/s of a full lrcc_solve on the same batch.
+
+--impl reference times the CPU oracle (the plain complex128 PyTorch CPU
+restatement) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+PREC_NAMES = {"fp64": 0, "tf32": 1, "bf16x3": 2}
+DTYPE_NAMES = {"fp64": "c128 (f64)", "tf32": "tf32 tensor-core + f64", "bf16x3": "bf16x3 tensor-core + f64"}
+
+
+def nominal_flops(O, V, L, R):
+    po, pv = O * (O - 1) // 2, V * (V - 1) // 2
+    return 8.0 * (R * (po * pv * pv + O ** 3 * V ** 3) + pv * pv * L)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        mine = [s for s in self.samples if s and s[0] == os.environ.get("LOCAL_RANK", "0")] or self.samples
+        sm = [float(s[1]) for s in mine if len(s) > 2 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in mine if len(s) > 2 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in mine:
+            for k, n in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(mine)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """CPU oracle on a bounded sample: sigma = A X for ONE right-hand side of the
+    same system (the oracle as it stands, all host cores)."""
+    if rank != 0:
+        return
+    import torch
+    from oracle import ccsd
+    cfg = synth.CONFIGS[args.workload]
+    s = synth.make_system(cfg["O"], cfg["V"], cfg["L"], cfg["seed"])
+    model = ccsd.build(s)
+    x0, _ = ccsd.mp2(model)
+    amp = synth.random_amplitudes(cfg["O"], cfg["V"], 1, seed=123, scale=0.05)
+    lay = model.lay
+    X = lay.join(torch.as_tensor(amp["t1"][0]), torch.as_tensor(amp["t2u"][0]))
+    for _ in range(max(0, args.warmup)):
+        model.jvp(x0, X)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        model.jvp(x0, X)
+        model.vjp(x0, X)
+        times.append(time.perf_counter() - t0)
+    F = 2 * nominal_flops(cfg["O"], cfg["V"], cfg["L"], 1)
+    v = F / statistics.median(times) / 1e12
+    cores = torch.get_num_threads()
+    line = {"impl": "reference", "metric": "LR-CCSD residual TFLOP/s", "value": v, "unit": "TFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128 (f64, CPU)", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: O={cfg['O']} V={cfg['V']} L={cfg['L']}, sigma + A^T Y, 1 RHS sample"},
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": "one right-hand side of the workload (the oracle's own sigma and A^T products)"},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(cfg):
+    """The oracle timed on one right-hand side of the same workload (10-30 s)."""
+    import torch
+    from oracle import ccsd
+    s = synth.make_system(cfg["O"], cfg["V"], cfg["L"], cfg["seed"])
+    model = ccsd.build(s)
+    x0, _ = ccsd.mp2(model)
+    amp = synth.random_amplitudes(cfg["O"], cfg["V"], 1, seed=123, scale=0.05)
+    X = model.lay.join(torch.as_tensor(amp["t1"][0]), torch.as_tensor(amp["t2u"][0]))
+    t0 = time.perf_counter()
+    model.jvp(x0, X)
+    model.vjp(x0, X)
+    dt = time.perf_counter() - t0
+    F = 2 * nominal_flops(cfg["O"], cfg["V"], cfg["L"], 1)
+    return {"value": F / dt / 1e12, "unit": "TFLOP/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"sigma + A^T Y for 1 of the {len(cfg['comps']) * len(cfg['omegas'])} right-hand sides "
+                      f"({dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--prec", default="bf16x3", choices=list(PREC_NAMES))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_2503_23144_gb300 import lrcc as L
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    cfg = synth.CONFIGS[args.workload]
+    O, V, Lx = cfg["O"], cfg["V"], cfg["L"]
+    comps, omegas = list(cfg["comps"]), list(cfg["omegas"])
+    R = len(comps) * len(omegas)
+    prec = PREC_NAMES[args.prec]
+    s = synth.make_system(O, V, Lx, cfg["seed"])
+    opt = L.lrcc_default_options()
+    opt.prec = prec
+    ctx = L.lrcc_setup(s["eps"], s["B"], s["mu"], O, V, opt)
+    E, itT, itL = L.lrcc_ccsd_ground(ctx)
+    # linearisation point: the converged CCSD amplitudes (read back once, outside timing)
+    t_host = L.lrcc_get_amplitudes(ctx, 0)
+    n1, n2 = O * V, O * O * V * V
+    x_host = np.empty((R, n1 + n2), dtype=np.complex128)
+    iu, ju = np.triu_indices(O, 1)
+    au, bu = np.triu_indices(V, 1)
+    for r in range(R):
+        a = synth.random_amplitudes(O, V, 1, seed=2000 + 17 * rank + r, scale=0.05)
+        t2 = np.zeros((O, O, V, V), dtype=np.complex128)
+        u = a["t2u"][0]
+        I, J, A, B = iu[:, None], ju[:, None], au[None, :], bu[None, :]
+        t2[I, J, A, B] = u
+        t2[J, I, A, B] = -u
+        t2[I, J, B, A] = -u
+        t2[J, I, B, A] = u
+        x_host[r, :n1] = a["t1"][0].reshape(-1)
+        x_host[r, n1:] = t2.reshape(-1)
+    # the residual hook projects the doubles block onto its antisymmetric part
+    dev = torch.device("cuda", local)
+    t_dev = torch.as_tensor(t_host).to(dev)
+    x_dev = torch.as_tensor(x_host).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        a = L.lrcc_residual_dev(ctx, L.LRCC_RES_SIGMA, t_dev, x_dev, prec=prec)
+        b = L.lrcc_residual_dev(ctx, L.LRCC_RES_VJP, t_dev, x_dev, prec=prec)
+        return a, b
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    launches0 = L.lrcc_kernel_launches(ctx)
+    clocks = Clocks()
+    clocks.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    L.lrcc_profile(ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flush between timed steps (256 MB > 129 MB L2)
+        ev[k][0].record()
+        step()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    L.lrcc_profile(ctx, False)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    launches = (L.lrcc_kernel_launches(ctx) - launches0) // args.steps
+    stats = L.lrcc_kernel_stats(ctx)
+    total = sum(ms)
+    if pg:
+        t = torch.tensor([total], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total = float(t.item())
+    F_step = 2 * nominal_flops(O, V, Lx, R)
+    value = world * F_step * args.steps / (total / 1e3) / 1e12
+
+    # end to end through the host-buffer ABI: H2D of X and T, D2H of both results
+    e2e_t = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        L.lrcc_residual(ctx, L.LRCC_RES_SIGMA, t_host, x_host, prec=prec)
+        L.lrcc_residual(ctx, L.LRCC_RES_VJP, t_host, x_host, prec=prec)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = F_step / min(e2e_t) / 1e12 * world
+    h2d = 2 * (x_host.nbytes + t_host.nbytes)
+    d2h = 2 * x_host.nbytes
+    clk = clocks.stop()
+
+    # alpha(omega) solves/s: a full lrcc_solve on the same batch (X, F X, Y, alpha)
+    solves = None
+    if not args.no_solve:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        alpha, err = L.lrcc_solve(ctx, omegas, comps)
+        dt = time.perf_counter() - t0
+        n64, nmix = L.lrcc_solve_counts(ctx)
+        solves = {"value": world * R / dt, "unit": "alpha(omega)/s", "seconds": dt, "rhs": R,
+                  "max_residual": float(err.max()), "precision": args.prec,
+                  "alpha_zz_0": float(alpha[0, -1, -1].real), "fp64_maps": n64, "mixed_maps": nmix,
+                  "phase_ms": [round(x, 1) for x in L.lrcc_phase_times(ctx)]}
+
+    # roofline of the dominant kernel family in the timed region
+    hbm, bf16, bf16s, src = load_peaks()
+    dom = max(stats.items(), key=lambda kv: kv[1]["ms"]) if stats else None
+    roof = None
+    if dom:
+        name, st = dom
+        achieved = st["flops"] / (st["ms"] / 1e3) / 1e12 / 1.0
+        if name == "gemm_tc_bf16x3":
+            peak, unit, bound = bf16 / 3.0, "TFLOP/s", "tensor"     # 3 bf16 products per real product
+            note = f"bf16 {src} peak / 3 (bf16x3 split); complex flops counted 8 per CMAC"
+        elif name == "gemm_tc_tf32":
+            peak, unit, bound = bf16 / 2.0, "TFLOP/s", "tensor"     # tf32 dense = bf16 / 2 nominal
+            note = f"bf16 {src} peak x tf32/bf16 nominal ratio 1/2"
+        else:
+            peak, unit, bound = 1.25, "TFLOP/s", "alu"              # FP64 nominal (FMA pipes)
+            note = "GB300 FP64 nominal 1.25 TFLOP/s"
+        roof = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "launches": st["count"],
+                "share_of_step": st["ms"] / total, "peak_note": note}
+
+    line = {
+        "metric": "LR-CCSD residual TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[args.prec],
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: O={O} V={V} L={Lx}, R={R} RHS (3 comps x {len(omegas)} omegas), "
+                               f"sigma + A^T Y per step", "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{world} (RHS sharding, no collective)"},
+        "e2e": {"value": e2e, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "clocks": clk, "roofline": roof, "alpha_solves": solves,
+        "ground_state": {"E_corr": [E.real, E.imag], "iters_T": itT, "iters_L": itL},
+        "kernels": {k: {"count": v["count"], "ms": v["ms"]} for k, v in stats.items()},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -189,12 +189,40 @@ lrcc_status lrcc_residual_dev(lrcc_ctx* ctx, int kind, const double* t_dev, cons
 lrcc_status lrcc_ladder_dev(lrcc_ctx* ctx, const double* x_dev, double* z_dev, int R,
                             int transpose, int prec, void* stream);
 
+/*
+ * lrcc_get_amplitudes -- copy the converged ground-state amplitudes to the host.
+ *   which  0: T (CCSD, Eq. 9-10), 1: Lambda (left CCSD).
+ *   out    host [O*V + O*O*V*V] complex (singles, then full antisymmetric doubles).
+ * LRCC_ESTATE before lrcc_ccsd_ground.
+ */
+lrcc_status lrcc_get_amplitudes(lrcc_ctx* ctx, int which, double* out);
+
+/* Residual-map applications in the last lrcc_solve: FP64 (outer) and
+ * tensor-core (inner) sigma / transpose products, summed over all RHS chunks. */
+lrcc_status lrcc_solve_counts(const lrcc_ctx* ctx, int* n_fp64, int* n_mixed);
+
 /* Device timing of the last lrcc_solve / lrcc_ccsd_ground phases (ms):
  * [0] ground T, [1] Lambda, [2] xi/eta, [3] X, [4] F.X, [5] Y, [6] alpha. */
 lrcc_status lrcc_phase_times(const lrcc_ctx* ctx, double* ms7);
 
 /* Number of kernels this library launched on ctx since creation. */
 int64_t lrcc_kernel_launches(const lrcc_ctx* ctx);
+
+/*
+ * Measurement hooks.  lrcc_profile(ctx, 1) starts recording a CUDA-event pair
+ * around every GEMM launch on the context's stream (and clears old records);
+ * lrcc_profile(ctx, 0) stops.  lrcc_kernel_stats aggregates the records by
+ * kernel name: call with idx = 0, 1, ... until it returns LRCC_EINVAL.
+ *   name     out, static string (kernel family)
+ *   count    out, launches
+ *   ms       out, summed device time of those launches
+ *   flops    out, summed algorithmic flops (8 per complex multiply-add)
+ *   bytes    out, summed algorithmic operand + result bytes
+ * Synchronises the context's stream.
+ */
+lrcc_status lrcc_profile(lrcc_ctx* ctx, int enable);
+lrcc_status lrcc_kernel_stats(lrcc_ctx* ctx, int idx, const char** name, int64_t* count, double* ms,
+                              double* flops, double* bytes);
 
 #ifdef __cplusplus
 }

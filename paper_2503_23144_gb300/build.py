@@ -65,7 +65,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, hh, extra), srcs))
     cuda_lib = "/usr/local/cuda/lib64"
-    cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-L", cuda_lib, "-lcuda", "-lcusolver",
+    cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-L", cuda_lib, "-lcusolver",
            "-Xlinker", "-rpath," + cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -252,6 +252,7 @@ void gemm_f64(Dev& D, const GemmArgs& g) {
     k.b_nfast = (g.sBn == 1) || (g.sBk != 1 && std::llabs(g.sBn) < std::llabs(g.sBk));
     if (k.atomic) prescale(D, g);
     dim3 grid((unsigned)tiles, (unsigned)g.batch, (unsigned)splits);
+    KTimer kt(D, "gemm_f64", 8.0 * g.M * g.N * g.K * g.batch, 16.0 * (g.M * g.K + g.K * g.N + g.M * g.N) * g.batch);
     k_gemm<<<grid, TH, 0, D.st>>>(k);
     LAUNCH_CHECK(D);
 }

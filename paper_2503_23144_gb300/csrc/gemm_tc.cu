@@ -1,9 +1,414 @@
-// Tensor-core split-precision complex GEMM (tcgen05 / TMEM / TMA).
+// Tensor-core complex GEMM on sm_103a: tcgen05.mma with TMEM accumulators,
+// operands staged by TMA into 128B-swizzled shared memory.
+//
+// Complex arithmetic uses the real embedding
+//   Re C = sum_k (Ar Br - Ai Bi),  Im C = sum_k (Ar Bi + Ai Br)
+// written as ONE real GEMM over an extended K: every complex k becomes S real
+// k' slots, and output column n becomes the accumulator column pair
+// (2n, 2n+1) = (Re, Im), so the epilogue writes whole complex numbers.
+//   kind::tf32  (S = 2):  A' = (Ar, Ai)                 B'_re = (Br, -Bi)   B'_im = (Bi, Br)
+//   kind::f16 bf16x3 (S = 6): hi/lo bf16 splits, products hi.hi + hi.lo + lo.hi
+//        A' = (Arh, Aih, Arh, Aih, Arl, Ail)
+//        B'_re = (Brh, -Bih, Brl, -Bil, Brh, -Bih)   B'_im = (Bih, Brh, Bil, Brl, Bih, Brh)
+// Accumulation is FP32 in TMEM; the epilogue scales by the complex alpha and
+// adds beta * C in FP64.
+//
+// CTA tile: 128 (M) x 256 (accumulator columns = 128 complex outputs), K stage
+// = 128 bytes of K per row, 4 stages (192 KB of shared memory), 128 threads:
+// thread 0 issues TMA, thread 32 issues MMAs, all four warps run the epilogue
+// (warp w owns TMEM lanes 32w..32w+31).  Every mbarrier wait is bounded; on
+// expiry the kernel raises the context's error word and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "lrcc_internal.h"
 
-bool gemm_tc_available() { return false; }
+namespace {
+
+constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int ROWB = 128;                 // bytes of K per row per stage
+constexpr int A_STAGE = BM * ROWB;        // 16 KB
+constexpr int B_STAGE = BN * ROWB;        // 32 KB
+constexpr int SMEM_BYTES = STAGES * (A_STAGE + B_STAGE) + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t WAIT_LIMIT = 1u << 25;  // polls (with backoff) before giving up
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok;
+}
+// bounded wait; false (and the error word set) if the phase never completes
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if (i > 32) __nanosleep(64);
+    }
+    atomicExch(err, 1);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+            su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row atoms 1024 B apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;             // descriptor version (sm_100 family)
+    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor: D f32, A/B format, both K-major, N, M
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_fmt, int M, int N) {
+    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (KIND == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct Epi {
+    int64_t M, N;
+    cplx* C;
+    int64_t sCb, sCm, sCn;
+    cplx alpha, beta;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int num_kb, int tiles_n,
+              Epi ep, int* err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_STAGE;
+    uint64_t* full = (uint64_t*)(sB + STAGES * B_STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accb = empty + STAGES;
+    uint32_t* tslot = (uint32_t*)(accb + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile_m = blockIdx.x / tiles_n, tile_n = blockIdx.x % tiles_n;
+    const int bz = blockIdx.y;
+    constexpr int KELEM = KIND == 0 ? 64 : 32;  // elements per 128-byte row
+    constexpr uint32_t IDESC = instr_desc(KIND == 0 ? 1u : 2u, BM, BN);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (threadIdx.x == 0) {
+        // TMA producer
+        for (int kb = 0; kb < num_kb; ++kb) {
+            int s = kb % STAGES;
+            uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u, err)) break;
+            mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
+            tma_load_3d(sA + s * A_STAGE, &ta, &full[s], kb * KELEM, tile_m * BM, bz);
+            tma_load_3d(sB + s * B_STAGE, &tb, &full[s], kb * KELEM, tile_n * BN, bz);
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer
+        int done = 0;
+        for (int kb = 0; kb < num_kb; ++kb) {
+            int s = kb % STAGES;
+            uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph, err)) break;
+            tc_fence_after();
+            uint64_t ad = smem_desc(su32(sA + s * A_STAGE));
+            uint64_t bd = smem_desc(su32(sB + s * B_STAGE));
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                // 32 bytes of K per MMA (16 bf16 or 8 tf32): +2 in the >>4 address field
+                mma<KIND>(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), IDESC, (kb | kk) != 0);
+            }
+            mma_commit(&empty[s]);
+            done = kb + 1;
+        }
+        (void)done;
+        mma_commit(accb);
+    }
+    __syncwarp();
+
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 (accumulator rows)
+    bool got = mbar_wait(accb, 0, err);
+    if (!got) got = mbar_wait(accb, 0, err);  // second bounded wait before releasing TMEM
+    __syncwarp();
+    tc_fence_after();
+    const int64_t m = (int64_t)tile_m * BM + warp * 32 + lane;
+    cplx* Cb = ep.C + (int64_t)bz * ep.sCb;
+    const bool beta0 = ep.beta.x == 0.0 && ep.beta.y == 0.0;
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+        if (got && m < ep.M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                int64_t n = ((int64_t)tile_n * BN + c * 32 + 2 * j) >> 1;
+                if (n < ep.N) {
+                    double re = (double)__uint_as_float(r[2 * j]), im = (double)__uint_as_float(r[2 * j + 1]);
+                    cplx* cp = Cb + m * ep.sCm + n * ep.sCn;
+                    cplx v = make_double2(ep.alpha.x * re - ep.alpha.y * im, ep.alpha.x * im + ep.alpha.y * re);
+                    if (!beta0) {
+                        cplx o = *cp;
+                        v.x += ep.beta.x * o.x - ep.beta.y * o.y;
+                        v.y += ep.beta.x * o.y + ep.beta.y * o.x;
+                    }
+                    *cp = v;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// operand embedding (split / convert), written into zero-filled padded buffers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// A' [b][Mp][Kp]: row m, slots S*k + s
+template <int KIND>
+__global__ void k_embed_a(const cplx* __restrict__ A, int64_t sAb, int64_t sAm, int64_t sAk, int cA, int64_t batch,
+                          int64_t M, int64_t K, int64_t Mp, int64_t Kp, void* __restrict__ out) {
+    int64_t total = batch * M * K;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = idx % K, t = idx / K, m = t % M, b = t / M;
+        cplx a = A[b * sAb + m * sAm + k * sAk];
+        if (cA) a.y = -a.y;
+        int64_t row = (b * Mp + m) * Kp;
+        if (KIND == 0) {
+            __nv_bfloat16* o = (__nv_bfloat16*)out + row + 6 * k;
+            __nv_bfloat16 rh = __double2bfloat16(a.x), ih = __double2bfloat16(a.y);
+            __nv_bfloat16 rl = __double2bfloat16(a.x - (double)__bfloat162float(rh));
+            __nv_bfloat16 il = __double2bfloat16(a.y - (double)__bfloat162float(ih));
+            o[0] = rh; o[1] = ih; o[2] = rh; o[3] = ih; o[4] = rl; o[5] = il;
+        } else {
+            uint32_t* o = (uint32_t*)out + row + 2 * k;
+            o[0] = to_tf32((float)a.x);
+            o[1] = to_tf32((float)a.y);
+        }
+    }
+}
+
+// B' [b][Np2][Kp]: rows 2n (real output) and 2n+1 (imaginary output)
+template <int KIND>
+__global__ void k_embed_b(const cplx* __restrict__ B, int64_t sBb, int64_t sBk, int64_t sBn, int cB, int64_t batch,
+                          int64_t K, int64_t N, int64_t Np2, int64_t Kp, void* __restrict__ out) {
+    int64_t total = batch * N * K;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k = idx % K, t = idx / K, n = t % N, b = t / N;
+        cplx v = B[b * sBb + k * sBk + n * sBn];
+        if (cB) v.y = -v.y;
+        int64_t r0 = (b * Np2 + 2 * n) * Kp, r1 = r0 + Kp;
+        if (KIND == 0) {
+            __nv_bfloat16 rh = __double2bfloat16(v.x), ih = __double2bfloat16(v.y);
+            __nv_bfloat16 rl = __double2bfloat16(v.x - (double)__bfloat162float(rh));
+            __nv_bfloat16 il = __double2bfloat16(v.y - (double)__bfloat162float(ih));
+            __nv_bfloat16 nih = __hneg(ih), nil = __hneg(il);
+            __nv_bfloat16* o = (__nv_bfloat16*)out + r0 + 6 * k;
+            o[0] = rh; o[1] = nih; o[2] = rl; o[3] = nil; o[4] = rh; o[5] = nih;
+            o = (__nv_bfloat16*)out + r1 + 6 * k;
+            o[0] = ih; o[1] = rh; o[2] = il; o[3] = rl; o[4] = ih; o[5] = rh;
+        } else {
+            uint32_t* o = (uint32_t*)out + r0 + 2 * k;
+            uint32_t br = to_tf32((float)v.x), bi = to_tf32((float)v.y);
+            o[0] = br;
+            o[1] = bi ^ 0x80000000u;
+            o = (uint32_t*)out + r1 + 2 * k;
+            o[0] = bi;
+            o[1] = br;
+        }
+    }
+}
+
+int grid_n(Dev& D, int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)D.sm_count * 16));
+}
+
+// cuTensorMapEncodeTiled from the driver, resolved through the runtime so the
+// library itself does not link libcuda (it still loads on machines without a
+// driver, where only host-side validation can run)
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+            throw LrccError(LRCC_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+void encode(CUtensorMap* map, void* base, int kind, uint64_t Kp, uint64_t rows, uint64_t batch, uint32_t box_rows) {
+    CUtensorMapDataType dt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    uint64_t es = kind == 0 ? 2 : 4;
+    cuuint64_t dims[3] = {Kp, rows, batch};
+    cuuint64_t strides[2] = {Kp * es, Kp * rows * es};
+    cuuint32_t box[3] = {(cuuint32_t)(ROWB / es), box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw LrccError(LRCC_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
+
+bool g_attr_set[2] = {false, false};
+
+}  // namespace
+
+bool gemm_tc_available() { return true; }
 
 void gemm_tc(Dev& D, const GemmArgs& g, int prec) {
-    (void)prec;
-    gemm_f64(D, g);
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+    REQUIRE(prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3, "gemm_tc: bad precision");
+    REQUIRE(D.err_flag != nullptr, "gemm_tc: no error word");
+    if (g.K <= 0) {
+        gemm_f64(D, g);  // pure beta scaling
+        return;
+    }
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    const int64_t S = kind == 0 ? 6 : 2, es = kind == 0 ? 2 : 4, kelem = ROWB / es;
+    const int64_t Kp = (S * g.K + kelem - 1) / kelem * kelem;
+    const int64_t Mp = (g.M + BM - 1) / BM * BM;
+    const int64_t Np2 = (2 * g.N + BN - 1) / BN * BN;
+    REQUIRE(g.batch <= 65535, "gemm_tc: batch too large");
+    size_t bytesA = (size_t)(g.batch * Mp * Kp * es), bytesB = (size_t)(g.batch * Np2 * Kp * es);
+    void* pa = D.pool.get(bytesA);
+    std::shared_ptr<DevBuf> ha(new DevBuf{&D.pool, pa, bytesA});
+    void* pb = D.pool.get(bytesB);
+    std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
+    CK(cudaMemsetAsync(pa, 0, bytesA, D.st));
+    CK(cudaMemsetAsync(pb, 0, bytesB, D.st));
+    if (kind == 0) {
+        k_embed_a<0><<<grid_n(D, g.batch * g.M * g.K), 256, 0, D.st>>>(g.A, g.sAb, g.sAm, g.sAk, g.cA, g.batch, g.M,
+                                                                         g.K, Mp, Kp, pa);
+        LAUNCH_CHECK(D);
+        k_embed_b<0><<<grid_n(D, g.batch * g.N * g.K), 256, 0, D.st>>>(g.B, g.sBb, g.sBk, g.sBn, g.cB, g.batch, g.K,
+                                                                         g.N, Np2, Kp, pb);
+        LAUNCH_CHECK(D);
+    } else {
+        k_embed_a<1><<<grid_n(D, g.batch * g.M * g.K), 256, 0, D.st>>>(g.A, g.sAb, g.sAm, g.sAk, g.cA, g.batch, g.M,
+                                                                         g.K, Mp, Kp, pa);
+        LAUNCH_CHECK(D);
+        k_embed_b<1><<<grid_n(D, g.batch * g.N * g.K), 256, 0, D.st>>>(g.B, g.sBb, g.sBk, g.sBn, g.cB, g.batch, g.K,
+                                                                         g.N, Np2, Kp, pb);
+        LAUNCH_CHECK(D);
+    }
+    CUtensorMap ta, tb;
+    encode(&ta, pa, kind, Kp, Mp, g.batch, BM);
+    encode(&tb, pb, kind, Kp, Np2, g.batch, BN);
+    Epi ep{g.M, g.N, g.C, g.sCb, g.sCm, g.sCn, g.alpha, g.beta};
+    int tiles_n = (int)(Np2 / BN);
+    int64_t tiles = (Mp / BM) * tiles_n;
+    REQUIRE(tiles < INT32_MAX, "gemm_tc: too many tiles");
+    int num_kb = (int)(Kp / kelem);
+    dim3 grid((unsigned)tiles, (unsigned)g.batch);
+    KTimer kt(D, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32", 8.0 * g.M * g.N * g.K * g.batch,
+              (double)(bytesA + bytesB) + 16.0 * g.M * g.N * g.batch);
+    if (kind == 0) {
+        if (!g_attr_set[0]) {
+            CK(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+            g_attr_set[0] = true;
+        }
+        k_tc_gemm<0><<<grid, 128, SMEM_BYTES, D.st>>>(ta, tb, num_kb, tiles_n, ep, D.err_flag);
+    } else {
+        if (!g_attr_set[1]) {
+            CK(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+            g_attr_set[1] = true;
+        }
+        k_tc_gemm<1><<<grid, 128, SMEM_BYTES, D.st>>>(ta, tb, num_kb, tiles_n, ep, D.err_flag);
+    }
+    LAUNCH_CHECK(D);
 }

@@ -26,12 +26,18 @@ struct lrcc_ctx {
     Amp T, Lam;                          // R = 1
     std::string err;
     double phase_ms[7] = {0};
+    int n_sigma64 = 0, n_sigma_mixed = 0;  // residual-map applications in the last solve
     ~lrcc_ctx() {
         cc.reset();
         ccmu.clear();
         ccfx.reset();
         if (eo) cudaFree(eo);
         if (ev) cudaFree(ev);
+        if (D.err_flag) cudaFree(D.err_flag);
+        for (auto& r : D.recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
     }
 };
 
@@ -196,7 +202,7 @@ double* dev_doubles(Dev& D, const std::vector<double>& v, std::shared_ptr<DevBuf
 //   r = resid(x);  x <- extrapolate(x - r/(D + shift))
 template <class F>
 int solve_loop(lrcc_ctx* c, Amp& x, F&& resid, const std::vector<double>& shift, double tol, int max_iter,
-               std::vector<double>* final_res = nullptr) {
+               std::vector<double>* final_res = nullptr, bool throw_on_max = true) {
     Dev& D = c->D;
     int64_t R = x.t1.d[0];
     std::shared_ptr<DevBuf> hold;
@@ -220,6 +226,7 @@ int solve_loop(lrcc_ctx* c, Amp& x, F&& resid, const std::vector<double>& shift,
         x = diis.push_extrapolate(D, xn, e);
     }
     if (final_res) *final_res = rn;
+    if (!throw_on_max) return max_iter;
     throw LrccError(LRCC_ENOCONV, "no convergence after " + std::to_string(max_iter) + " iterations (max|r| = " +
                                       std::to_string(rn.empty() ? -1.0 : *std::max_element(rn.begin(), rn.end())) + ")");
 }
@@ -261,7 +268,10 @@ void do_ground(lrcc_ctx* c, cplx& E, int& itT, int& itL) {
 }
 
 // F X for each RHS of X: exact 5-point stencil of the Lagrangian gradient
-// g(T) = A(T)^T lambda + dE/dT, a polynomial of degree <= 3 in T (Eq. 34).
+// g(T) = A(T)^T lambda + dE/dT, a polynomial of degree <= 3 in T (Eq. 34):
+//   F X = [g(T - 2hX) - 8 g(T - hX) + 8 g(T + hX) - g(T + 2hX)] / (12 h),
+// X scaled to unit max-norm first.  All 4 points of a chunk of right-hand
+// sides run as one batched primal evaluation and one batched reverse sweep.
 Amp fx_product(lrcc_ctx* c, const Amp& X) {
     Dev& D = c->D;
     int64_t R = X.t1.d[0];
@@ -272,31 +282,91 @@ Amp fx_product(lrcc_ctx* c, const Amp& X) {
     const double h = 0.5;
     const int ks[4] = {-2, -1, 1, 2};
     const double wk[4] = {1.0, -8.0, 8.0, -1.0};
-    for (int64_t r = 0; r < R; ++r) {
-        Tensor o1 = out.t1.index(r), o2 = out.t2.index(r);
-        if (!(nrm[r] > 0.0)) {
-            fill(D, o1, mkc(0.0));
-            fill(D, o2, mkc(0.0));
-            continue;
-        }
-        double s = 1.0 / nrm[r];
-        bool first = true;
-        for (int q = 0; q < 4; ++q) {
-            Amp Tk = amp_copy(D, c->T);
-            Tensor x1 = X.t1.index(r), x2 = X.t2.index(r);
-            Tensor tk1 = Tk.t1.index(0), tk2 = Tk.t2.index(0);
-            axpby(D, mkc(ks[q] * h * s), x1, false, mkc(1.0), tk1);
-            axpby(D, mkc(ks[q] * h * s), x2, false, mkc(1.0), tk2);
-            c->ccfx->P.eval(D, inputs_of(Tk, 0), LRCC_FP64);
-            Amp g = vjp_unique(D, *c->ccfx, c->Lam, 1.0, LRCC_FP64);
-            cplx w = mkc(wk[q] * nrm[r] / (12.0 * h));
-            Tensor g1 = g.t1.index(0), g2 = g.t2.index(0);
-            axpby(D, w, g1, false, first ? mkc(0.0) : mkc(1.0), o1);
-            axpby(D, w, g2, false, first ? mkc(0.0) : mkc(1.0), o2);
-            first = false;
+    // chunk so that the batched primal (about 24 doubles-sized slots per point) fits in ~24 GiB
+    double per_point = 24.0 * 16.0 * double(O) * O * V * V;
+    int64_t rc = std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)((24.0 * (1ull << 30)) / (4.0 * per_point))));
+    for (int64_t r0 = 0; r0 < R; r0 += rc) {
+        int64_t r1 = std::min(R, r0 + rc), nr = r1 - r0, n = 4 * nr;
+        Amp Tk = amp_empty(D, n, O, V);
+        Amp Lk = amp_empty(D, n, O, V);
+        for (int q = 0; q < 4; ++q)
+            for (int64_t i = 0; i < nr; ++i) {
+                int64_t slot = q * nr + i, r = r0 + i;
+                Tensor a1 = Tk.t1.index(slot), a2 = Tk.t2.index(slot);
+                Tensor l1 = Lk.t1.index(slot), l2 = Lk.t2.index(slot);
+                axpby(D, mkc(1.0), c->T.t1.index(0), false, mkc(0.0), a1);
+                axpby(D, mkc(1.0), c->T.t2.index(0), false, mkc(0.0), a2);
+                axpby(D, mkc(1.0), c->Lam.t1.index(0), false, mkc(0.0), l1);
+                axpby(D, mkc(1.0), c->Lam.t2.index(0), false, mkc(0.0), l2);
+                double sc = nrm[r] > 0.0 ? ks[q] * h / nrm[r] : 0.0;
+                axpby(D, mkc(sc), X.t1.index(r), false, mkc(1.0), a1);
+                axpby(D, mkc(sc), X.t2.index(r), false, mkc(1.0), a2);
+            }
+        c->ccfx->P.eval(D, {Tk.t1, Tk.t2}, LRCC_FP64, true);
+        Amp g = vjp_unique(D, *c->ccfx, Lk, 1.0, LRCC_FP64);
+        for (int64_t i = 0; i < nr; ++i) {
+            int64_t r = r0 + i;
+            Tensor o1 = out.t1.index(r), o2 = out.t2.index(r);
+            for (int q = 0; q < 4; ++q) {
+                cplx w = mkc(nrm[r] > 0.0 ? wk[q] * nrm[r] / (12.0 * h) : 0.0);
+                axpby(D, w, g.t1.index(q * nr + i), false, q == 0 ? mkc(0.0) : mkc(1.0), o1);
+                axpby(D, w, g.t2.index(q * nr + i), false, q == 0 ? mkc(0.0) : mkc(1.0), o2);
+            }
         }
     }
     return out;
+}
+
+// Linear response solve (M - shift_r) z = -b  for R right-hand sides where
+// M z is `apply(z, prec)` (sigma or the transpose product):
+//  FP64: preconditioned DIIS on the FP64 residual.
+//  mixed: iterative refinement; outer residual r = M z + shift z + b in FP64,
+//  inner correction d from (M + shift) d = -r by DIIS on tensor-core products
+//  until the inner residual drops by inner_tol, then z += d.
+template <class Apply>
+void response_solve(lrcc_ctx* c, Amp& z, const Amp& b, const std::vector<double>& shift, const double* shift_dev,
+                    Apply&& apply, std::vector<double>& final_res, int& n64, int& nmix) {
+    Dev& D = c->D;
+    int64_t R = b.t1.d[0];
+    int O = c->O, V = c->V;
+    precond(D, nullptr, b, z, c->eo, c->ev, shift_dev);
+    auto res64 = [&](const Amp& x) {
+        Amp s = apply(x, LRCC_FP64);
+        n64++;
+        Amp r = amp_empty(D, R, O, V);
+        combine(D, s, x, shift_dev, &b, r);
+        return r;
+    };
+    if (c->opt.prec == LRCC_FP64) {
+        solve_loop(c, z, res64, shift, c->opt.x_tol, c->opt.max_iter, &final_res);
+        return;
+    }
+    const int prec = c->opt.prec;
+    std::vector<double> rn;
+    for (int outer = 0; outer < 30; ++outer) {
+        Amp r = res64(z);
+        max_abs_amp(D, r, rn);
+        double m = *std::max_element(rn.begin(), rn.end());
+        if (!std::isfinite(m) || m > 1e250) throw LrccError(LRCC_ENOCONV, "residual is not finite");
+        if (m < c->opt.x_tol) {
+            final_res = rn;
+            return;
+        }
+        Amp d = amp_empty(D, R, O, V);
+        precond(D, nullptr, r, d, c->eo, c->ev, shift_dev);
+        auto resm = [&](const Amp& x) {
+            Amp s = apply(x, prec);
+            nmix++;
+            Amp q = amp_empty(D, R, O, V);
+            combine(D, s, x, shift_dev, &r, q);
+            return q;
+        };
+        double tol = std::max(c->opt.inner_tol * m, 0.5 * c->opt.x_tol);
+        solve_loop(c, d, resm, shift, tol, std::min(c->opt.max_iter, 60), nullptr, false);
+        amp_axpby(D, mkc(1.0), d, mkc(1.0), z);
+    }
+    final_res = rn;
+    throw LrccError(LRCC_ENOCONV, "iterative refinement did not converge");
 }
 
 void do_solve(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int n_c, double* alpha,
@@ -304,6 +374,8 @@ void do_solve(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int 
     Dev& D = c->D;
     int O = c->O, V = c->V;
     for (int q = 0; q < 7; ++q) if (q >= 2) c->phase_ms[q] = 0;
+    c->n_sigma64 = 0;
+    c->n_sigma_mixed = 0;
     // xi^A, eta^A per component (Eq. 31, 33)
     std::vector<Amp> xi(c->ncomp), eta(c->ncomp);
     std::vector<char> need(c->ncomp, 0);
@@ -347,14 +419,8 @@ void do_solve(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int 
         std::vector<double> resX, resY;
         {
             Timer tm(D);
-            precond(D, nullptr, xiR, X, c->eo, c->ev, mwd);
-            auto res = [&](const Amp& x) {
-                Amp s = sigma(D, *c->cc, x, c->opt.prec == LRCC_FP64 ? LRCC_FP64 : LRCC_FP64);
-                Amp r = amp_empty(D, R, O, V);
-                combine(D, s, x, mwd, &xiR, r);
-                return r;
-            };
-            solve_loop(c, X, res, mw, c->opt.x_tol, c->opt.max_iter, &resX);
+            auto apply = [&](const Amp& x, int p) { return sigma(D, *c->cc, x, p); };
+            response_solve(c, X, xiR, mw, mwd, apply, resX, c->n_sigma64, c->n_sigma_mixed);
             c->phase_ms[3] += tm.stop();
         }
         // eta + F X
@@ -374,14 +440,8 @@ void do_solve(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int 
         Amp Y = amp_empty(D, R, O, V);
         {
             Timer tm(D);
-            precond(D, nullptr, rhsY, Y, c->eo, c->ev, pwd);
-            auto res = [&](const Amp& y) {
-                Amp s = vjp_unique(D, *c->cc, y, 0.0, LRCC_FP64);
-                Amp r = amp_empty(D, R, O, V);
-                combine(D, s, y, pwd, &rhsY, r);
-                return r;
-            };
-            solve_loop(c, Y, res, pw, c->opt.x_tol, c->opt.max_iter, &resY);
+            auto apply = [&](const Amp& y, int p) { return vjp_unique(D, *c->cc, y, 0.0, p); };
+            response_solve(c, Y, rhsY, pw, pwd, apply, resY, c->n_sigma64, c->n_sigma_mixed);
             c->phase_ms[5] += tm.stop();
         }
         // g_AB = Y^B . xi^A + eta^A . X^B
@@ -417,6 +477,18 @@ void do_solve(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int 
                 alpha[2 * o + 1] = -0.5 * (gab.y - gba.y);
             }
     if (err_est) std::memcpy(err_est, errs.data(), sizeof(double) * errs.size());
+}
+
+// kernels with bounded waits raise a device error word instead of hanging
+void check_device_error(Dev& D) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, D.err_flag, sizeof(int), cudaMemcpyDeviceToHost, D.st));
+    CK(cudaStreamSynchronize(D.st));
+    if (h != 0) {
+        CK(cudaMemsetAsync(D.err_flag, 0, sizeof(int), D.st));
+        CK(cudaStreamSynchronize(D.st));
+        throw LrccError(LRCC_ETIMEOUT, "a device-side wait expired (tensor-core pipeline did not complete)");
+    }
 }
 
 lrcc_status fail(lrcc_ctx* c, const LrccError& e) {
@@ -489,6 +561,8 @@ lrcc_status lrcc_setup(const double* eps, const double* B, int L, const double* 
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&c->D.sm_count, cudaDevAttrMultiProcessorCount, dev));
         CK(cudaStreamCreateWithFlags(&c->D.st, cudaStreamNonBlocking));
+        CK(cudaMalloc(&c->D.err_flag, sizeof(int)));
+        CK(cudaMemset(c->D.err_flag, 0, sizeof(int)));
         c->O = O;
         c->V = V;
         c->L = L;
@@ -525,6 +599,7 @@ lrcc_status lrcc_ccsd_ground(lrcc_ctx* c, double e_corr[2], int* iters_T, int* i
         cplx E = mkc(0.0);
         int itT = 0, itL = 0;
         do_ground(c, E, itT, itL);
+        check_device_error(c->D);
         if (e_corr) {
             e_corr[0] = E.x;
             e_corr[1] = E.y;
@@ -549,6 +624,7 @@ lrcc_status lrcc_solve(lrcc_ctx* c, const double* omegas, int n_w, const int* co
         for (int k = 0; k < n_c; ++k) REQUIRE(comps[k] >= 0 && comps[k] < c->ncomp, "component out of range");
         for (int w = 0; w < n_w; ++w) REQUIRE(std::isfinite(omegas[w]), "omega not finite");
         do_solve(c, omegas, n_w, comps, n_c, alpha, err_est);
+        check_device_error(c->D);
         return LRCC_OK;
     } catch (const LrccError& e) {
         return fail(c, e);
@@ -664,7 +740,9 @@ lrcc_status lrcc_residual(lrcc_ctx* c, int kind, const double* t, const double* 
                           double* out) {
     if (!c) return LRCC_EINVAL;
     try {
-        return residual_impl(c, kind, t, in, R, comp, prec, out, false);
+        lrcc_status s = residual_impl(c, kind, t, in, R, comp, prec, out, false);
+        check_device_error(c->D);
+        return s;
     } catch (const LrccError& e) {
         return fail(c, e);
     } catch (const std::exception& e) {
@@ -684,6 +762,7 @@ lrcc_status lrcc_residual_dev(lrcc_ctx* c, int kind, const double* t, const doub
         CK(cudaEventRecord(ev, st));
         CK(cudaStreamWaitEvent(c->D.st, ev, 0));
         lrcc_status s = residual_impl(c, kind, t, in, R, comp, prec, out, true);
+        check_device_error(c->D);
         CK(cudaEventRecord(ev, c->D.st));
         CK(cudaStreamWaitEvent(st, ev, 0));
         CK(cudaEventDestroy(ev));
@@ -709,6 +788,7 @@ lrcc_status lrcc_ladder_dev(lrcc_ctx* c, const double* x, double* z, int R, int 
         Tensor X = wrap((cplx*)x, {R, c->O, c->O, c->V, c->V});
         Tensor Z = wrap((cplx*)z, {R, c->O, c->O, c->V, c->V});
         ladder(c->D, c->lad, X, mkc(1.0), mkc(0.0), Z, transpose != 0, prec);
+        check_device_error(c->D);
         CK(cudaEventRecord(ev, c->D.st));
         CK(cudaStreamWaitEvent(st, ev, 0));
         CK(cudaEventDestroy(ev));
@@ -721,6 +801,28 @@ lrcc_status lrcc_ladder_dev(lrcc_ctx* c, const double* x, double* z, int R, int 
     }
 }
 
+lrcc_status lrcc_get_amplitudes(lrcc_ctx* c, int which, double* out) {
+    if (!c || !out || (which != 0 && which != 1)) return LRCC_EINVAL;
+    try {
+        if (!c->ground) throw LrccError(LRCC_ESTATE, "no ground state yet");
+        const Amp& a = which == 0 ? c->T : c->Lam;
+        int64_t n1 = a.t1.numel(), n2 = a.t2.numel();
+        CK(cudaMemcpyAsync(out, a.t1.p, sizeof(cplx) * n1, cudaMemcpyDeviceToHost, c->D.st));
+        CK(cudaMemcpyAsync(out + 2 * n1, a.t2.p, sizeof(cplx) * n2, cudaMemcpyDeviceToHost, c->D.st));
+        CK(cudaStreamSynchronize(c->D.st));
+        return LRCC_OK;
+    } catch (const LrccError& e) {
+        return fail(c, e);
+    }
+}
+
+lrcc_status lrcc_solve_counts(const lrcc_ctx* c, int* n_fp64, int* n_mixed) {
+    if (!c) return LRCC_EINVAL;
+    if (n_fp64) *n_fp64 = c->n_sigma64;
+    if (n_mixed) *n_mixed = c->n_sigma_mixed;
+    return LRCC_OK;
+}
+
 lrcc_status lrcc_phase_times(const lrcc_ctx* c, double* ms7) {
     if (!c || !ms7) return LRCC_EINVAL;
     for (int k = 0; k < 7; ++k) ms7[k] = c->phase_ms[k];
@@ -728,6 +830,51 @@ lrcc_status lrcc_phase_times(const lrcc_ctx* c, double* ms7) {
 }
 
 int64_t lrcc_kernel_launches(const lrcc_ctx* c) { return c ? c->D.launches : 0; }
+
+static void clear_recs(Dev& D) {
+    for (auto& r : D.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    D.recs.clear();
+}
+
+lrcc_status lrcc_profile(lrcc_ctx* c, int enable) {
+    if (!c) return LRCC_EINVAL;
+    cudaStreamSynchronize(c->D.st);
+    if (enable) clear_recs(c->D);
+    c->D.timing = enable != 0;
+    return LRCC_OK;
+}
+
+lrcc_status lrcc_kernel_stats(lrcc_ctx* c, int idx, const char** name, int64_t* count, double* ms, double* flops,
+                              double* bytes) {
+    if (!c || idx < 0) return LRCC_EINVAL;
+    if (cudaStreamSynchronize(c->D.st) != cudaSuccess) return LRCC_ECUDA;
+    std::vector<std::string> names;
+    for (auto& r : c->D.recs)
+        if (std::find(names.begin(), names.end(), std::string(r.name)) == names.end()) names.push_back(r.name);
+    if (idx >= (int)names.size()) return LRCC_EINVAL;
+    int64_t n = 0;
+    double t = 0, f = 0, b = 0;
+    const char* nm = nullptr;
+    for (auto& r : c->D.recs) {
+        if (names[idx] != r.name) continue;
+        float e = 0;
+        cudaEventElapsedTime(&e, r.a, r.b);
+        n++;
+        t += e;
+        f += r.flops;
+        b += r.bytes;
+        nm = r.name;
+    }
+    if (name) *name = nm;
+    if (count) *count = n;
+    if (ms) *ms = t;
+    if (flops) *flops = f;
+    if (bytes) *bytes = b;
+    return LRCC_OK;
+}
 
 lrcc_status lrcc_fns_truncate(lrcc_ctx* c, int by_count, double value, double omega, int* v_kept, double* occ_out) {
     if (!c) return LRCC_EINVAL;

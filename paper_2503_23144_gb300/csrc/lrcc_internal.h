@@ -61,12 +61,42 @@ struct DevBuf {
     ~DevBuf() { pool->put(p, n); }
 };
 
+// per-launch CUDA-event records (enabled for measurement only)
+struct KRec {
+    const char* name;
+    cudaEvent_t a, b;
+    double flops, bytes;
+};
+
 struct Dev {
     cudaStream_t st = nullptr;
     Pool pool;
     int64_t launches = 0;
     int* err_flag = nullptr;  // device word set by kernels whose bounded waits expire
     int sm_count = 148;
+    bool timing = false;
+    std::vector<KRec> recs;
+};
+
+// RAII event pair around one launch on D.st when D.timing is set
+struct KTimer {
+    Dev& D;
+    KRec r;
+    bool on;
+    KTimer(Dev& d, const char* name, double flops, double bytes) : D(d), on(d.timing) {
+        if (!on) return;
+        r.name = name;
+        r.flops = flops;
+        r.bytes = bytes;
+        cudaEventCreate(&r.a);
+        cudaEventCreate(&r.b);
+        cudaEventRecord(r.a, D.st);
+    }
+    ~KTimer() {
+        if (!on) return;
+        cudaEventRecord(r.b, D.st);
+        D.recs.push_back(r);
+    }
 };
 
 // ---------------------------------------------------------------------------

@@ -21,12 +21,6 @@ std::string lhs_b(const std::string& s) {
 std::string rhs(const std::string& s) { return s.substr(s.find("->") + 2); }
 std::string perm_in(const std::string& s) { return s.substr(0, s.find("->")); }
 
-Tensor add_lead(const Tensor& t, int64_t R) {
-    // view t [..] (contiguous) as [R][..] when t already has R leading
-    (void)R;
-    return t;
-}
-
 Tensor as5(const Tensor& t, int64_t R, int64_t O, int64_t V) { return t.reshape({R, O, O, V, V}); }
 }  // namespace
 
@@ -35,6 +29,7 @@ int Prog::input(std::vector<int64_t> shape) {
     t.nd = (int)shape.size();
     for (int k = 0; k < t.nd; ++k) t.d[k] = shape[k];
     val.push_back(t);
+    shape0.push_back(shape);
     active.push_back(1);
     is_const.push_back(0);
     inputs.push_back((int)val.size() - 1);
@@ -43,6 +38,7 @@ int Prog::input(std::vector<int64_t> shape) {
 
 int Prog::cst(const Tensor& t) {
     val.push_back(t);
+    shape0.push_back(t.shape());
     active.push_back(0);
     is_const.push_back(1);
     return (int)val.size() - 1;
@@ -51,68 +47,98 @@ int Prog::cst(const Tensor& t) {
 int Prog::op(std::vector<Term> terms) {
     Op o;
     o.terms = terms;
-    val.push_back(Tensor());
     bool act = false;
     for (auto& t : terms) {
         if (t.a >= 0 && active[t.a]) act = true;
         if (t.b >= 0 && active[t.b]) act = true;
     }
+    val.push_back(Tensor());
     active.push_back(act);
     is_const.push_back(0);
     o.out = (int)val.size() - 1;
-    // record the output shape now (operands' shapes are known)
+    shape0.push_back(out_shape(o));
     ops.push_back(o);
-    std::vector<int64_t> sh = out_shape(o);
-    Tensor t;
-    t.nd = (int)sh.size();
-    for (int k = 0; k < t.nd; ++k) t.d[k] = sh[k];
-    val[o.out] = t;
     return o.out;
 }
 
 std::vector<int64_t> Prog::out_shape(const Op& op) const {
     const Term& t = op.terms.at(0);
-    const Tensor& A = val[t.a];
+    const std::vector<int64_t>& A = shape0[t.a];
     std::vector<int64_t> sh;
-    if (t.kind == TK_LADDER) return A.shape();
+    if (t.kind == TK_LADDER) return A;
     if (t.kind == TK_PERM) {
         std::string lx = perm_in(t.spec), ly = rhs(t.spec);
-        for (char c : ly) sh.push_back(A.d[lx.find(c)]);
+        for (char c : ly) sh.push_back(A[lx.find(c)]);
         return sh;
     }
     std::string la = lhs_a(t.spec), lb = lhs_b(t.spec), lc = rhs(t.spec);
-    const Tensor& B = val[t.b];
+    const std::vector<int64_t>& B = shape0[t.b];
     for (char c : lc) {
         size_t p = la.find(c);
-        if (p != std::string::npos) sh.push_back(A.d[p]);
-        else sh.push_back(B.d[lb.find(c)]);
+        if (p != std::string::npos) sh.push_back(A[p]);
+        else sh.push_back(B[lb.find(c)]);
     }
     return sh;
 }
 
+// view of an unbatched tensor repeated RB times along a new leading dim (stride 0)
+static Tensor broadcast(const Tensor& t, int64_t R) {
+    Tensor v = t;
+    for (int k = v.nd; k > 0; --k) {
+        v.d[k] = v.d[k - 1];
+        v.s[k] = v.s[k - 1];
+    }
+    v.d[0] = R;
+    v.s[0] = 0;
+    v.nd = t.nd + 1;
+    return v;
+}
+
 void Prog::apply_term(Dev& D, const Term& t, cplx beta, Tensor& out, int prec) {
-    cplx c = t.c;
+    const cplx c = t.c;
     if (t.kind == TK_EIN) {
-        ein(D, t.spec, c, val[t.a], false, val[t.b], false, beta, out, prec);
+        std::string la = lhs_a(t.spec), lb = lhs_b(t.spec), lc = rhs(t.spec);
+        std::string za = zp(t.a), zb = zp(t.b);
+        bool out_batched = RB > 0 && (active[t.a] || active[t.b] || out.nd > (int)lc.size());
+        if (RB > 0 && za.empty() && zb.empty() && out_batched) {
+            // both operands constant, batched output: compute once and broadcast
+            Tensor tmp = ein_new(D, t.spec, c, val[t.a], false, val[t.b], false, prec);
+            axpby(D, mkc(1.0), broadcast(tmp, RB), false, beta, out);
+            return;
+        }
+        std::string zc = out_batched ? "Z" : "";
+        ein(D, za + la + "," + zb + lb + "->" + zc + lc, c, val[t.a], false, val[t.b], false, beta, out, prec);
     } else if (t.kind == TK_PERM) {
-        perm_axpby(D, t.spec, c, val[t.a], beta, out);
+        std::string lx = perm_in(t.spec), ly = rhs(t.spec);
+        bool out_batched = RB > 0 && out.nd > (int)ly.size();
+        if (out_batched && zp(t.a).empty()) {
+            Tensor x = broadcast(val[t.a], RB);
+            perm_axpby(D, "Z" + lx + "->Z" + ly, c, x, beta, out);
+        } else {
+            std::string z = out_batched ? "Z" : "";
+            perm_axpby(D, z + lx + "->" + z + ly, c, val[t.a], beta, out);
+        }
     } else {
-        Tensor x = as5(val[t.a], 1, O, V);
-        Tensor z = as5(out, 1, O, V);
+        int64_t R = (RB > 0 && active[t.a]) ? RB : 1;
+        Tensor x = as5(val[t.a], R, O, V);
+        Tensor z = as5(out, R, O, V);
         ladder(D, *lad, x, c, beta, z, false, prec);
     }
 }
 
-void Prog::eval(Dev& D, const std::vector<Tensor>& in, int prec) {
+void Prog::eval(Dev& D, const std::vector<Tensor>& in, int prec, bool batched) {
     if (in.size() != inputs.size()) throw LrccError(LRCC_EINVAL, "program input count");
+    RB = batched ? in.at(0).d[0] : 0;
     for (size_t k = 0; k < in.size(); ++k) {
-        const Tensor& d = val[inputs[k]];
-        REQUIRE(in[k].nd == d.nd, "program input rank");
-        for (int q = 0; q < d.nd; ++q) REQUIRE(in[k].d[q] == d.d[q], "program input shape");
+        std::vector<int64_t> want = shape0[inputs[k]];
+        if (batched) want.insert(want.begin(), RB);
+        REQUIRE(in[k].shape() == want, "program input shape");
         val[inputs[k]] = in[k];
     }
     for (auto& o : ops) {
-        Tensor out = empty(D, val[o.out].shape());
+        std::vector<int64_t> sh = shape0[o.out];
+        if (RB > 0 && active[o.out]) sh.insert(sh.begin(), RB);
+        Tensor out = empty(D, sh);
         bool first = true;
         for (auto& t : o.terms) {
             apply_term(D, t, first ? mkc(0.0) : mkc(1.0), out, prec);
@@ -126,8 +152,8 @@ std::vector<Tensor> Prog::jvp(Dev& D, const std::vector<Tensor>& tin, const std:
     const int n = (int)val.size();
     std::vector<Tensor> tan(n);
     int64_t R = tin.at(0).d[0];
+    REQUIRE(RB == 0 || RB == R, "jvp: tangent batch must match the primal batch");
     for (size_t k = 0; k < inputs.size(); ++k) tan[inputs[k]] = tin[k];
-    // last use of each slot's tangent (as an operand), outputs kept
     std::vector<int> last(n, -1);
     for (int k = 0; k < (int)ops.size(); ++k)
         for (auto& t : ops[k].terms) {
@@ -139,7 +165,7 @@ std::vector<Tensor> Prog::jvp(Dev& D, const std::vector<Tensor>& tin, const std:
     for (int k = 0; k < (int)ops.size(); ++k) {
         const Op& o = ops[k];
         if (!active[o.out]) continue;
-        std::vector<int64_t> sh = val[o.out].shape();
+        std::vector<int64_t> sh = shape0[o.out];
         sh.insert(sh.begin(), R);
         Tensor out = empty(D, sh);
         bool first = true;
@@ -147,8 +173,10 @@ std::vector<Tensor> Prog::jvp(Dev& D, const std::vector<Tensor>& tin, const std:
         for (auto& t : o.terms) {
             if (t.kind == TK_EIN) {
                 std::string la = lhs_a(t.spec), lb = lhs_b(t.spec), lc = rhs(t.spec);
-                if (active[t.a]) ein(D, "Z" + la + "," + lb + "->Z" + lc, t.c, tan[t.a], false, val[t.b], false, beta(), out, prec);
-                if (active[t.b]) ein(D, la + ",Z" + lb + "->Z" + lc, t.c, val[t.a], false, tan[t.b], false, beta(), out, prec);
+                if (active[t.a])
+                    ein(D, "Z" + la + "," + zp(t.b) + lb + "->Z" + lc, t.c, tan[t.a], false, val[t.b], false, beta(), out, prec);
+                if (active[t.b])
+                    ein(D, zp(t.a) + la + ",Z" + lb + "->Z" + lc, t.c, val[t.a], false, tan[t.b], false, beta(), out, prec);
             } else if (t.kind == TK_PERM) {
                 if (active[t.a]) perm_axpby(D, "Z" + perm_in(t.spec) + "->Z" + rhs(t.spec), t.c, tan[t.a], beta(), out);
             } else {
@@ -182,12 +210,11 @@ std::vector<Tensor> Prog::vjp(Dev& D, const std::vector<Tensor>& cot, const std:
         R = cot[k].d[0];
     }
     if (R < 0) throw LrccError(LRCC_EINVAL, "vjp: all cotangents are zero");
-    // adjoints of output slots are only read, never accumulated into in place:
-    // copy them so later accumulation (if an output feeds another op) is safe
+    REQUIRE(RB == 0 || RB == R, "vjp: cotangent batch must match the primal batch");
     auto acc = [&](int slot, auto&& write) {
         if (!active[slot]) return;
         if (!has[slot]) {
-            std::vector<int64_t> sh = val[slot].shape();
+            std::vector<int64_t> sh = shape0[slot];
             sh.insert(sh.begin(), R);
             adj[slot] = empty(D, sh);
             write(adj[slot], mkc(0.0));
@@ -196,7 +223,6 @@ std::vector<Tensor> Prog::vjp(Dev& D, const std::vector<Tensor>& cot, const std:
             write(adj[slot], mkc(1.0));
         }
     };
-    std::vector<char> owned(n, 0);
     for (int k = (int)ops.size() - 1; k >= 0; --k) {
         const Op& o = ops[k];
         if (!active[o.out] || !has[o.out]) continue;
@@ -206,11 +232,11 @@ std::vector<Tensor> Prog::vjp(Dev& D, const std::vector<Tensor>& cot, const std:
                 std::string la = lhs_a(t.spec), lb = lhs_b(t.spec), lc = rhs(t.spec);
                 if (active[t.a])
                     acc(t.a, [&](Tensor& dst, cplx b) {
-                        ein(D, "Z" + lc + "," + lb + "->Z" + la, t.c, cb, false, val[t.b], false, b, dst, prec);
+                        ein(D, "Z" + lc + "," + zp(t.b) + lb + "->Z" + la, t.c, cb, false, val[t.b], false, b, dst, prec);
                     });
                 if (active[t.b])
                     acc(t.b, [&](Tensor& dst, cplx b) {
-                        ein(D, la + ",Z" + lc + "->Z" + lb, t.c, val[t.a], false, cb, false, b, dst, prec);
+                        ein(D, zp(t.a) + la + ",Z" + lc + "->Z" + lb, t.c, val[t.a], false, cb, false, b, dst, prec);
                     });
             } else if (t.kind == TK_PERM) {
                 if (active[t.a])
@@ -231,14 +257,13 @@ std::vector<Tensor> Prog::vjp(Dev& D, const std::vector<Tensor>& cot, const std:
     std::vector<Tensor> res;
     for (int s : inputs) {
         if (!has[s]) {
-            std::vector<int64_t> sh = val[s].shape();
+            std::vector<int64_t> sh = shape0[s];
             sh.insert(sh.begin(), R);
             res.push_back(zeros(D, sh));
         } else {
             res.push_back(adj[s]);
         }
     }
-    (void)owned;
     return res;
 }
 

@@ -24,19 +24,22 @@ struct Op {
 
 struct Prog {
     std::vector<Tensor> val;        // primal value of each slot
+    std::vector<std::vector<int64_t>> shape0;  // unbatched shape of each slot
     std::vector<char> active;       // slot depends on the inputs
     std::vector<char> is_const;     // slot is a fixed constant tensor
     std::vector<Op> ops;
     std::vector<int> inputs;        // input slots (amplitudes)
     LadderCtx* lad = nullptr;
     int O = 0, V = 0;
+    int64_t RB = 0;                 // primal batch: 0 = unbatched, else leading dim of active slots
 
     int input(std::vector<int64_t> shape);
     int cst(const Tensor& t);
     int op(std::vector<Term> terms);
 
-    // primal evaluation for the given input values (R = 1, no leading batch)
-    void eval(Dev& D, const std::vector<Tensor>& in, int prec);
+    // primal evaluation for the given input values; with batched = true every
+    // input carries a leading batch dimension and so does every active slot
+    void eval(Dev& D, const std::vector<Tensor>& in, int prec, bool batched = false);
     // forward sweep: tangents of inputs [R][...] -> tangents of `outs`
     std::vector<Tensor> jvp(Dev& D, const std::vector<Tensor>& tin, const std::vector<int>& outs, int prec);
     // reverse sweep: cotangents of `outs` [R][...] (undefined tensor = zero)
@@ -45,6 +48,8 @@ struct Prog {
 
   private:
     std::vector<int64_t> out_shape(const Op& op) const;
+    // label prefix of a slot's primal value ("Z" when batched)
+    std::string zp(int slot) const { return (RB > 0 && active[slot]) ? "Z" : ""; }
     void apply_term(Dev& D, const Term& t, cplx beta, Tensor& out, int prec);
 };
 

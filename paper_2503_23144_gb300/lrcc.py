@@ -58,6 +58,11 @@ SIGNATURES = [
     ("lrcc_ladder_dev", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
     ("lrcc_phase_times", ctypes.c_int, [_vp, _dp]),
     ("lrcc_kernel_launches", ctypes.c_int64, [_vp]),
+    ("lrcc_profile", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lrcc_get_amplitudes", ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    ("lrcc_solve_counts", ctypes.c_int, [_vp, _ip, _ip]),
+    ("lrcc_kernel_stats", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                         ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp]),
 ]
 
 
@@ -228,6 +233,40 @@ def lrcc_phase_times(ctx: Context) -> np.ndarray:
 
 def lrcc_kernel_launches(ctx: Context) -> int:
     return int(library().lrcc_kernel_launches(ctx.h))
+
+
+def lrcc_get_amplitudes(ctx: Context, which: int = 0) -> np.ndarray:
+    """which 0: T, 1: Lambda -> flat [O*V + O*O*V*V] complex."""
+    out = np.zeros(ctx.n_amp, dtype=np.complex128)
+    ctx.check(library().lrcc_get_amplitudes(ctx.h, which, _cd(out.view(np.float64))))
+    return out
+
+
+def lrcc_solve_counts(ctx: Context):
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    ctx.check(library().lrcc_solve_counts(ctx.h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def lrcc_profile(ctx: Context, enable: bool) -> None:
+    ctx.check(library().lrcc_profile(ctx.h, int(enable)))
+
+
+def lrcc_kernel_stats(ctx: Context) -> dict:
+    """{name: dict(count, ms, flops, bytes)} aggregated over recorded launches."""
+    out = {}
+    i = 0
+    while True:
+        nm = ctypes.c_char_p()
+        cnt = ctypes.c_int64()
+        ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        st = library().lrcc_kernel_stats(ctx.h, i, ctypes.byref(nm), ctypes.byref(cnt), ctypes.byref(ms),
+                                         ctypes.byref(fl), ctypes.byref(by))
+        if st != LRCC_OK:
+            break
+        out[nm.value.decode()] = dict(count=cnt.value, ms=ms.value, flops=fl.value, bytes=by.value)
+        i += 1
+    return out
 
 
 def _make_residual_fn():

@@ -163,3 +163,58 @@ def test_rhs_chunking_invariance_and_state(L):
     L.lrcc_ccsd_ground(ctx2)
     a4, _ = L.lrcc_solve(ctx2, [0.0, 0.03], [0, 1, 2])
     assert np.abs(a12 - a4).max() < 1e-9 * np.abs(a12).max()
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 3e-3), (2, 1e-4)])
+def test_ladder_tensor_core_vs_fp64(L, prec, tol):
+    """Split-precision tcgen05 ladder (TF32, bf16x3) against the FP64 ladder on
+    shapes with several M tiles, K pipelines longer than the stage ring, and
+    ragged edges."""
+    for (O, V, Lx, R, seed) in [(5, 19, 30, 3, 1), (6, 40, 64, 4, 2)]:
+        s = synth.make_system(O, V, Lx, seed)
+        ctx = _ctx(L, s)
+        g = torch.Generator(device="cuda").manual_seed(seed)
+        x = torch.randn(R, O, O, V, V, dtype=torch.complex128, device="cuda", generator=g)
+        x = x - x.transpose(1, 2)
+        x = x - x.transpose(3, 4)
+        z64 = L.lrcc_ladder_dev(ctx, x)
+        z = L.lrcc_ladder_dev(ctx, x, prec=prec)
+        assert (z - z64).abs().max().item() < tol * z64.abs().max().item()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_alpha_within_1e6(L, prec):
+    """Iterative refinement with tensor-core inner products: every alpha within
+    1e-6 relative of the FP64 path (and of the oracle)."""
+    s = synth.make_system(5, 19, 30, seed=21)
+    oms = [0.0, 0.04, 0.08]
+    ref = ccsd.polarizability(s, (0, 1, 2), oms, tol=1e-11)
+    c64 = _ctx(L, s, x_tol=1e-9)
+    L.lrcc_ccsd_ground(c64)
+    a64, _ = L.lrcc_solve(c64, oms, [0, 1, 2])
+    cm = _ctx(L, s, x_tol=1e-9, prec=prec, rhs_chunk=9)
+    L.lrcc_ccsd_ground(cm)
+    am, err = L.lrcc_solve(cm, oms, [0, 1, 2])
+    n64, nmix = L.lrcc_solve_counts(cm)
+    assert nmix > 0
+    scale = np.abs(a64).max()
+    assert np.abs(am - a64).max() < 1e-6 * scale
+    assert np.abs(am - ref).max() < 1e-6 * scale
+    assert np.abs(a64 - ref).max() < 1e-9 * scale
+
+
+def test_amplitude_readback(L, small):
+    s, model, ctx = small
+    with pytest.raises(L.LrccError) as e:
+        L.lrcc_get_amplitudes(ctx, 0)
+    assert e.value.status == L.LRCC_ESTATE
+    E, _, _ = L.lrcc_ccsd_ground(ctx)
+    t = L.lrcc_get_amplitudes(ctx, 0)
+    lam = L.lrcc_get_amplitudes(ctx, 1)
+    lay = model.lay
+    tu = _unique(L, lay, t[None])[0]
+    assert float(model.R(tu).abs().max()) < 1e-9
+    assert abs(complex(model.E(tu)) - E) < 1e-12 * abs(E)
+    lu = _unique(L, lay, lam[None])[0]
+    gE = model.lagrangian_grad(tu, torch.zeros_like(tu))
+    assert float((model.vjp(tu, lu) + gE).abs().max()) < 1e-9
