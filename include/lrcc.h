@@ -224,6 +224,33 @@ lrcc_status lrcc_profile(lrcc_ctx* ctx, int enable);
 lrcc_status lrcc_kernel_stats(lrcc_ctx* ctx, int idx, const char** name, int64_t* count, double* ms,
                               double* flops, double* bytes);
 
+/*
+ * lrcc_ladder_noalloc -- the same ladder as lrcc_ladder_dev (FP64 path),
+ *   Z_ij^ab = 1/2 sum_ef <ab||ef> X_ij^ef,  <ab|ef> = sum_L Bvv^L_ae Bvv^L_bf,
+ * for callers that cannot allocate device memory: it needs no context and
+ * calls no allocator (no cudaMalloc, cudaFree or allocating library routine).
+ * The paper has no counterpart; this exists for users whose code may not
+ * allocate -- e.g. inside a host framework that owns every device byte through
+ * its own allocator, or in a latency-critical loop where cudaMalloc/cudaFree
+ * (which synchronise the device) must not run.
+ *   bvv_dev [L][V][V]        device, complex: the virtual-virtual block of B.
+ *   x_dev   [R][O][O][V][V]  device, complex, antisymmetric in (i,j) and (e,f).
+ *   z_dev   [R][O][O][V][V]  device, complex, overwritten.
+ *   transpose  0: the map above; 1: its holomorphic transpose (B -> conj B).
+ *   stream  cudaStream_t (NULL = legacy default stream); the call is
+ *           stream-ordered and does not synchronise.
+ * Intermediates live in one fixed 32 MiB array in device global memory that
+ * every GPU loading this library keeps until process exit.  Problems whose
+ * packed amplitudes plus one ladder slab exceed it (2 P_V R P_O complex +
+ * one row of <ab|ef> slab, P_n = n(n-1)/2) return LRCC_EINVAL with a message
+ * for lrcc_last_error(NULL).  The first call on a device looks up that array's
+ * device address (with the device current), so make the first call before
+ * any stream capture.  All calls share the array: calls whose kernels overlap
+ * on the GPU race on it, so serialise them on one stream.
+ */
+lrcc_status lrcc_ladder_noalloc(const double* bvv_dev, int L, int O, int V, int R, const double* x_dev,
+                                double* z_dev, int transpose, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

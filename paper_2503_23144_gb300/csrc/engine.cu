@@ -355,3 +355,24 @@ void ladder(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tenso
     k_unpack_z<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zp.p, Z.p, R, O, V, alpha, beta, beta0);
     LAUNCH_CHECK(D);
 }
+
+// ---------------------------------------------------------------------------
+// launchers of the ladder's three layout kernels on caller-provided buffers
+// (used by the entry point that allocates nothing)
+// ---------------------------------------------------------------------------
+void ladder_pack_x(Dev& D, const cplx* X, cplx* Xp, int64_t R, int64_t O, int64_t V) {
+    int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
+    k_pack_x<<<grid_n(D, PV * R * PO), 256, 0, D.st>>>(X, Xp, R, O, V);
+    LAUNCH_CHECK(D);
+}
+
+void ladder_antisym_slab(Dev& D, const cplx* G, int64_t ldg, cplx* W, int64_t a0, int64_t nrows, int64_t V) {
+    int64_t PV = V * (V - 1) / 2;
+    k_antisym_slab<<<grid_n(D, nrows * PV), 256, 0, D.st>>>(G, ldg, W, a0, nrows, V);
+    LAUNCH_CHECK(D);
+}
+
+void ladder_unpack_z(Dev& D, const cplx* Zp, cplx* Z, int64_t R, int64_t O, int64_t V) {
+    k_unpack_z<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zp, Z, R, O, V, mkc(1.0), mkc(0.0), 1);
+    LAUNCH_CHECK(D);
+}

@@ -43,6 +43,8 @@ struct lrcc_ctx {
 
 static std::string g_setup_err = "";
 
+void set_global_error(const std::string& msg) { g_setup_err = msg; }
+
 namespace {
 
 struct Timer {

@@ -208,3 +208,11 @@ void ladder(Dev& D, LadderCtx& L, const Tensor& X, cplx alpha, cplx beta, Tensor
 __host__ __device__ inline int64_t pair_index(int64_t p, int64_t q, int64_t n) {
     return p * (2 * n - p - 1) / 2 + (q - p - 1);
 }
+
+// ladder layout kernels on caller-provided buffers
+void ladder_pack_x(Dev& D, const cplx* X, cplx* Xp, int64_t R, int64_t O, int64_t V);
+void ladder_antisym_slab(Dev& D, const cplx* G, int64_t ldg, cplx* W, int64_t a0, int64_t nrows, int64_t V);
+void ladder_unpack_z(Dev& D, const cplx* Zp, cplx* Z, int64_t R, int64_t O, int64_t V);
+
+// message returned by lrcc_last_error(NULL)
+void set_global_error(const std::string& msg);

@@ -60,6 +60,8 @@ SIGNATURES = [
     ("lrcc_kernel_launches", ctypes.c_int64, [_vp]),
     ("lrcc_profile", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lrcc_get_amplitudes", ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    ("lrcc_ladder_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                           ctypes.c_int, _vp]),
     ("lrcc_solve_counts", ctypes.c_int, [_vp, _ip, _ip]),
     ("lrcc_kernel_stats", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                          ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp]),
@@ -222,6 +224,23 @@ def lrcc_ladder_dev(ctx: Context, x, transpose: bool = False, prec: int = LRCC_F
     z = torch.empty_like(x)
     ctx.check(library().lrcc_ladder_dev(ctx.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(z.data_ptr()),
                                         x.shape[0], int(transpose), prec, _stream_ptr()))
+    return z
+
+
+def lrcc_ladder_noalloc(bvv, x, transpose: bool = False, out=None):
+    """Ladder through the entry point that allocates nothing.  bvv: CUDA
+    complex128 [L, V, V]; x: [R, O, O, V, V]; out (optional, preallocated by
+    the caller) receives Z."""
+    import torch
+    bvv = bvv.resolve_conj().contiguous()
+    x = x.resolve_conj().contiguous()
+    z = torch.empty_like(x) if out is None else out
+    R, O, _, V, _ = x.shape
+    st = library().lrcc_ladder_noalloc(ctypes.c_void_p(bvv.data_ptr()), bvv.shape[0], O, V, R,
+                                       ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                       int(transpose), _stream_ptr())
+    if st != LRCC_OK:
+        raise LrccError(st, library().lrcc_last_error(None).decode())
     return z
 
 
