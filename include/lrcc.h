@@ -221,6 +221,8 @@ int64_t lrcc_kernel_launches(const lrcc_ctx* ctx);
  * Synchronises the context's stream.
  */
 lrcc_status lrcc_profile(lrcc_ctx* ctx, int enable);
+/* Write every recorded launch as CSV (kernel,M,N,K,batch,ms,flops) to path. */
+lrcc_status lrcc_profile_dump(lrcc_ctx* ctx, const char* path);
 lrcc_status lrcc_kernel_stats(lrcc_ctx* ctx, int idx, const char** name, int64_t* count, double* ms,
                               double* flops, double* bytes);
 

@@ -180,7 +180,9 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
     }
     if (g.batch == 1) { g.sAb = g.sBb = g.sCb = 0; }
     double flops = 8.0 * double(g.M) * double(g.N) * double(g.K) * double(g.batch);
-    bool tc = prec != LRCC_FP64 && gemm_tc_available() && flops > 2e9 && g.M >= 64 && g.N >= 32 && g.K >= 32;
+    // mixed mode: every contraction with real work goes to the tensor cores
+    // (the O-sized contractions too: FP64 on this part is 1.25 TFLOP/s)
+    bool tc = prec != LRCC_FP64 && gemm_tc_available() && flops >= 2e8;
     if (tc) gemm_tc(D, g, prec);
     else gemm_f64(D, g);
     if (!c_ok) perm_axpby(D, lc + "->" + sp.c, alpha, Ct, beta, C);
@@ -307,8 +309,136 @@ int grid_n(Dev& D, int64_t n) {
 
 }  // namespace
 
+// Build the embedded <ab||ef> matrix W' (rows a<b, K over e<f) once for a
+// mixed precision, if it fits in a third of the free device memory.
+static bool ensure_wcache(Dev& D, LadderCtx& LC, int64_t V, int prec) {
+    if (LC.wcache && LC.wcache_prec == prec) return true;
+    if (LC.wcache_disabled) return false;
+    const int64_t PV = V * (V - 1) / 2, L = LC.Bvv.d[0];
+    int64_t Mp, Kp;
+    size_t bytes = tc_embed_bytes(prec, PV, PV, 1, Mp, Kp, false);
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    if ((double)bytes > 0.33 * double(fr + D.pool.cached)) {
+        LC.wcache_disabled = true;
+        return false;
+    }
+    LC.wcache.reset();
+    void* p = D.pool.get(bytes);
+    LC.wcache.reset(new DevBuf{&D.pool, p, bytes});
+    CK(cudaMemsetAsync(p, 0, bytes, D.st));
+    int64_t budget = LC.slab_rows > 0 ? LC.slab_rows : (int64_t(4) << 30) / 16;
+    int64_t na = std::max<int64_t>(1, budget / std::max<int64_t>(1, V * V * V));
+    for (int64_t a0 = 0; a0 < V - 1; a0 += na) {
+        int64_t a1 = std::min<int64_t>(V - 1, a0 + na);
+        int64_t nb = V - a0 - 1;
+        Tensor G = empty(D, {(a1 - a0) * V, nb * V});
+        GemmArgs g1;
+        g1.M = (a1 - a0) * V; g1.N = nb * V; g1.K = L; g1.batch = 1;
+        g1.A = LC.Bvv.p + a0 * V; g1.sAb = 0; g1.sAm = 1; g1.sAk = V * V; g1.cA = false;
+        g1.B = LC.Bvv.p + (a0 + 1) * V; g1.sBb = 0; g1.sBk = V * V; g1.sBn = 1; g1.cB = false;
+        g1.C = G.p; g1.sCb = 0; g1.sCm = nb * V; g1.sCn = 1;
+        g1.alpha = mkc(1.0); g1.beta = mkc(0.0);
+        gemm_tc(D, g1, prec);
+        int64_t row0 = a0 * (2 * V - a0 - 1) / 2, row1 = a1 * (2 * V - a1 - 1) / 2;
+        int64_t nrows = row1 - row0;
+        Tensor W = empty(D, {nrows, PV});
+        k_antisym_slab<<<grid_n(D, nrows * PV), 256, 0, D.st>>>(G.p, nb * V, W.p, a0, nrows, V);
+        LAUNCH_CHECK(D);
+        int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
+        tc_embed_a(D, prec, W.p, 0, PV, 1, false, 1, nrows, PV, Mp, Kp, (char*)p + (size_t)(row0 * Kp * es));
+    }
+    LC.wcache_prec = prec;
+    LC.w_Mp = Mp;
+    LC.w_Kp = Kp;
+    return true;
+}
+
+// Z = alpha * 1/2 sum_ef <ab||ef> X + beta Z with the cached W';
+// transpose: conj(W' conj(Xp)) (B^T = conj B).
+static void ladder_cached(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose,
+                          int prec) {
+    int64_t R = X.d[0], O = X.d[1], V = X.d[3];
+    int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
+    Tensor Xp = empty(D, {PV, R * PO});
+    k_pack_x<<<grid_n(D, PV * R * PO), 256, 0, D.st>>>(X.p, Xp.p, R, O, V);
+    LAUNCH_CHECK(D);
+    int64_t Np2, Kp;
+    size_t bytesB = tc_embed_bytes(prec, R * PO, PV, 1, Np2, Kp, true);
+    REQUIRE(Kp == LC.w_Kp, "ladder cache: K padding mismatch");
+    void* pb = D.pool.get(bytesB);
+    std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
+    CK(cudaMemsetAsync(pb, 0, bytesB, D.st));
+    tc_embed_b(D, prec, Xp.p, 0, R * PO, 1, transpose, 1, PV, R * PO, Np2, Kp, pb);
+    Tensor Zp = empty(D, {PV, R * PO});
+    tc_gemm_embedded(D, prec, LC.wcache->p, pb, 1, PV, R * PO, LC.w_Mp, Np2, Kp, Zp.p, 0, R * PO, 1, mkc(1.0),
+                     mkc(0.0), transpose, 8.0 * PV * PV * R * PO);
+    bool beta0 = beta.x == 0.0 && beta.y == 0.0;
+    k_unpack_z<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zp.p, Z.p, R, O, V, alpha, beta, beta0);
+    LAUNCH_CHECK(D);
+}
+
+// FP64 <ab||ef> matrix W [P_V][P_V] (rows a<b, columns e<f), built once if it
+// fits in a third of the free device memory.
+static bool ensure_w64(Dev& D, LadderCtx& LC, int64_t V) {
+    if (LC.w64.p) return true;
+    if (LC.w64_disabled) return false;
+    const int64_t PV = V * (V - 1) / 2, L = LC.Bvv.d[0];
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    if (16.0 * PV * PV > 0.33 * double(fr + D.pool.cached)) {
+        LC.w64_disabled = true;
+        return false;
+    }
+    Tensor W = empty(D, {PV, PV});
+    int64_t budget = LC.slab_rows > 0 ? LC.slab_rows : (int64_t(4) << 30) / 16;
+    int64_t na = std::max<int64_t>(1, budget / std::max<int64_t>(1, V * V * V));
+    for (int64_t a0 = 0; a0 < V - 1; a0 += na) {
+        int64_t a1 = std::min<int64_t>(V - 1, a0 + na);
+        int64_t nb = V - a0 - 1;
+        Tensor G = empty(D, {(a1 - a0) * V, nb * V});
+        GemmArgs g1;
+        g1.M = (a1 - a0) * V; g1.N = nb * V; g1.K = L; g1.batch = 1;
+        g1.A = LC.Bvv.p + a0 * V; g1.sAb = 0; g1.sAm = 1; g1.sAk = V * V; g1.cA = false;
+        g1.B = LC.Bvv.p + (a0 + 1) * V; g1.sBb = 0; g1.sBk = V * V; g1.sBn = 1; g1.cB = false;
+        g1.C = G.p; g1.sCb = 0; g1.sCm = nb * V; g1.sCn = 1;
+        g1.alpha = mkc(1.0); g1.beta = mkc(0.0);
+        gemm_f64(D, g1);
+        int64_t row0 = a0 * (2 * V - a0 - 1) / 2, row1 = a1 * (2 * V - a1 - 1) / 2;
+        k_antisym_slab<<<grid_n(D, (row1 - row0) * PV), 256, 0, D.st>>>(G.p, nb * V, W.p + row0 * PV, a0,
+                                                                         row1 - row0, V);
+        LAUNCH_CHECK(D);
+    }
+    LC.w64 = W;
+    return true;
+}
+
 void ladder(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose, int prec) {
     REQUIRE(X.nd == 5 && Z.nd == 5 && X.contiguous() && Z.contiguous(), "ladder needs contiguous [R][O][O][V][V]");
+    if (prec == LRCC_FP64 && X.d[1] >= 2 && X.d[3] >= 2 && ensure_w64(D, LC, X.d[3])) {
+        int64_t R = X.d[0], O = X.d[1], V = X.d[3];
+        int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
+        Tensor Xp = empty(D, {PV, R * PO});
+        k_pack_x<<<grid_n(D, PV * R * PO), 256, 0, D.st>>>(X.p, Xp.p, R, O, V);
+        LAUNCH_CHECK(D);
+        Tensor Zp = empty(D, {PV, R * PO});
+        GemmArgs g2;
+        g2.M = PV; g2.N = R * PO; g2.K = PV; g2.batch = 1;
+        g2.A = LC.w64.p; g2.sAb = 0; g2.sAm = PV; g2.sAk = 1; g2.cA = transpose;  // B^T = conj B: conj(W)
+        g2.B = Xp.p; g2.sBb = 0; g2.sBk = R * PO; g2.sBn = 1; g2.cB = false;
+        g2.C = Zp.p; g2.sCb = 0; g2.sCm = R * PO; g2.sCn = 1;
+        g2.alpha = mkc(1.0); g2.beta = mkc(0.0);
+        gemm_f64(D, g2);
+        bool beta0 = beta.x == 0.0 && beta.y == 0.0;
+        k_unpack_z<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zp.p, Z.p, R, O, V, alpha, beta, beta0);
+        LAUNCH_CHECK(D);
+        return;
+    }
+    if (prec != LRCC_FP64 && gemm_tc_available() && X.d[1] >= 2 && X.d[3] >= 2 &&
+        ensure_wcache(D, LC, X.d[3], prec)) {
+        ladder_cached(D, LC, X, alpha, beta, Z, transpose, prec);
+        return;
+    }
     int64_t R = X.d[0], O = X.d[1], V = X.d[3];
     int64_t L = LC.Bvv.d[0];
     REQUIRE(LC.Bvv.d[1] == V && LC.Bvv.d[2] == V, "ladder: Bvv shape");

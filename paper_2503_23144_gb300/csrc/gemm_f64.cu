@@ -144,6 +144,67 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
     }
 }
 
+// Skinny GEMM (N <= NMAX): one thread per output row m keeps all N complex
+// accumulators in registers; B is staged K-chunk by K-chunk in shared memory.
+// Used for the O-sized index contractions (N or M = O), where 64x64 tiles
+// would waste most of the FMA work.
+constexpr int SK_KC = 32, SK_TH = 128;
+
+template <int NMAX>
+__global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
+    __shared__ cplx Bs[SK_KC][NMAX];
+    const int64_t m = blockIdx.x * (int64_t)SK_TH + threadIdx.x;
+    const int64_t b = blockIdx.y;
+    const cplx* A = g.A + b * g.sAb;
+    const cplx* B = g.B + b * g.sBb;
+    const int N = (int)g.N;
+    const int64_t kbeg = blockIdx.z * g.kper, kend = min(g.K, kbeg + g.kper);
+    cplx acc[NMAX];
+#pragma unroll
+    for (int n = 0; n < NMAX; ++n) acc[n] = make_double2(0.0, 0.0);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += SK_KC) {
+        int kc = (int)min((int64_t)SK_KC, kend - k0);
+        for (int e = threadIdx.x; e < SK_KC * NMAX; e += SK_TH) {
+            int kk = g.b_nfast ? e / NMAX : e % SK_KC;
+            int nn = g.b_nfast ? e % NMAX : e / SK_KC;
+            cplx w = make_double2(0.0, 0.0);
+            if (kk < kc && nn < N) w = B[(k0 + kk) * g.sBk + nn * g.sBn];
+            if (g.cB) w.y = -w.y;
+            Bs[kk][nn] = w;
+        }
+        __syncthreads();
+        if (m < g.M) {
+            for (int kk = 0; kk < kc; ++kk) {
+                cplx a = A[m * g.sAm + (k0 + kk) * g.sAk];
+                if (g.cA) a.y = -a.y;
+#pragma unroll
+                for (int n = 0; n < NMAX; ++n) cfma(acc[n], a, Bs[kk][n]);
+            }
+        }
+        __syncthreads();
+    }
+    if (m >= g.M) return;
+    cplx* C = g.C + b * g.sCb;
+#pragma unroll
+    for (int n = 0; n < NMAX; ++n) {
+        if (n >= N) break;
+        cplx v = acc[n];
+        cplx r = make_double2(g.alpha.x * v.x - g.alpha.y * v.y, g.alpha.x * v.y + g.alpha.y * v.x);
+        cplx* c = C + m * g.sCm + n * g.sCn;
+        if (g.atomic) {
+            atomicAdd(&c->x, r.x);
+            atomicAdd(&c->y, r.y);
+            continue;
+        }
+        if (g.beta.x != 0.0 || g.beta.y != 0.0) {
+            cplx o = *c;
+            r.x += g.beta.x * o.x - g.beta.y * o.y;
+            r.y += g.beta.x * o.y + g.beta.y * o.x;
+        }
+        *c = r;
+    }
+}
+
 // C[b] += alpha * sum_k A[b][k] B[b][k]   (M = N = 1), C pre-scaled by beta
 __global__ void k_dot(int64_t K, const cplx* A, int64_t sAb, int64_t sAk, int cA, const cplx* B,
                       int64_t sBb, int64_t sBk, int cB, cplx* C, int64_t sCb, cplx alpha) {
@@ -204,7 +265,10 @@ __global__ void k_scale(int64_t M, int64_t N, int64_t batch, cplx* C, int64_t sC
 
 }  // namespace
 
-static void prescale(Dev& D, const GemmArgs& g) {
+void gemm_prescale(Dev& D, const GemmArgs& g);
+static void prescale(Dev& D, const GemmArgs& g) { gemm_prescale(D, g); }
+
+void gemm_prescale(Dev& D, const GemmArgs& g) {
     if (g.beta.x == 1.0 && g.beta.y == 0.0) return;
     int64_t total = g.M * g.N * g.batch;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, D.sm_count * 16));
@@ -226,6 +290,49 @@ void gemm_f64(Dev& D, const GemmArgs& g) {
         int gx = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::max<int64_t>(1, 4 * D.sm_count / g.batch)));
         dim3 grid(gx, (unsigned)g.batch);
         k_dot<<<grid, th, 0, D.st>>>(g.K, g.A, g.sAb, g.sAk, g.cA, g.B, g.sBb, g.sBk, g.cB, g.C, g.sCb, g.alpha);
+        LAUNCH_CHECK(D);
+        return;
+    }
+    // skinny shapes: one of M, N at most 32 (swap roles so that N is the small one)
+    if (std::min(g.M, g.N) <= 32 && (std::max(g.M, g.N) >= 256 || g.K >= 4096)) {
+        GemmK k{};
+        bool swap = g.M < g.N;
+        k.M = swap ? g.N : g.M;
+        k.N = swap ? g.M : g.N;
+        k.K = g.K;
+        if (!swap) {
+            k.A = g.A; k.sAb = g.sAb; k.sAm = g.sAm; k.sAk = g.sAk; k.cA = g.cA;
+            k.B = g.B; k.sBb = g.sBb; k.sBk = g.sBk; k.sBn = g.sBn; k.cB = g.cB;
+            k.C = g.C; k.sCb = g.sCb; k.sCm = g.sCm; k.sCn = g.sCn;
+        } else {  // C^T = B^T A^T
+            k.A = g.B; k.sAb = g.sBb; k.sAm = g.sBn; k.sAk = g.sBk; k.cA = g.cB;
+            k.B = g.A; k.sBb = g.sAb; k.sBk = g.sAk; k.sBn = g.sAm; k.cB = g.cA;
+            k.C = g.C; k.sCb = g.sCb; k.sCm = g.sCn; k.sCn = g.sCm;
+        }
+        k.alpha = g.alpha;
+        k.beta = g.beta;
+        k.b_nfast = (k.sBn == 1) || (k.sBk != 1 && std::llabs(k.sBn) < std::llabs(k.sBk));
+        // split K until there are about 4 CTAs per SM
+        int64_t blocks = ((k.M + SK_TH - 1) / SK_TH) * g.batch;
+        int64_t sp = std::max<int64_t>(1, std::min<int64_t>((4 * (int64_t)D.sm_count + blocks - 1) / blocks,
+                                                            (g.K + 4 * SK_KC - 1) / (4 * SK_KC)));
+        sp = std::min<int64_t>(sp, 1024);
+        k.kper = (g.K + sp - 1) / sp;
+        k.kper = (k.kper + SK_KC - 1) / SK_KC * SK_KC;
+        sp = (g.K + k.kper - 1) / k.kper;
+        k.atomic = sp > 1;
+        if (k.atomic) prescale(D, g);
+        dim3 grid((unsigned)((k.M + SK_TH - 1) / SK_TH), (unsigned)g.batch, (unsigned)sp);
+        KTimer kt(D, "gemm_f64", 8.0 * g.M * g.N * g.K * g.batch, 16.0 * (g.M * g.K + g.K * g.N + g.M * g.N) * g.batch,
+                  g.M, g.N, g.K, g.batch);
+        if (k.N <= 1) k_gemm_skinny<1><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 2) k_gemm_skinny<2><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 4) k_gemm_skinny<4><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 8) k_gemm_skinny<8><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 12) k_gemm_skinny<12><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 16) k_gemm_skinny<16><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 24) k_gemm_skinny<24><<<grid, SK_TH, 0, D.st>>>(k);
+        else k_gemm_skinny<32><<<grid, SK_TH, 0, D.st>>>(k);
         LAUNCH_CHECK(D);
         return;
     }
@@ -252,7 +359,8 @@ void gemm_f64(Dev& D, const GemmArgs& g) {
     k.b_nfast = (g.sBn == 1) || (g.sBk != 1 && std::llabs(g.sBn) < std::llabs(g.sBk));
     if (k.atomic) prescale(D, g);
     dim3 grid((unsigned)tiles, (unsigned)g.batch, (unsigned)splits);
-    KTimer kt(D, "gemm_f64", 8.0 * g.M * g.N * g.K * g.batch, 16.0 * (g.M * g.K + g.K * g.N + g.M * g.N) * g.batch);
+    KTimer kt(D, "gemm_f64", 8.0 * g.M * g.N * g.K * g.batch, 16.0 * (g.M * g.K + g.K * g.N + g.M * g.N) * g.batch,
+              g.M, g.N, g.K, g.batch);
     k_gemm<<<grid, TH, 0, D.st>>>(k);
     LAUNCH_CHECK(D);
 }

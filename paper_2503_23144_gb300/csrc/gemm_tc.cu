@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "lrcc_internal.h"
 
@@ -35,6 +36,7 @@ constexpr int B_STAGE = BN * ROWB;        // 32 KB
 constexpr int SMEM_BYTES = STAGES * (A_STAGE + B_STAGE) + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 256;
 constexpr uint32_t WAIT_LIMIT = 1u << 25;  // polls (with backoff) before giving up
+constexpr uint32_t WAIT_LIMIT_INJECT = 1u << 14;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -56,8 +58,8 @@ __device__ __forceinline__ uint32_t mbar_try(uint64_t* bar, uint32_t parity) {
     return ok;
 }
 // bounded wait; false (and the error word set) if the phase never completes
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         if (mbar_try(bar, parity)) return true;
         if (i > 32) __nanosleep(64);
     }
@@ -133,12 +135,15 @@ struct Epi {
     cplx* C;
     int64_t sCb, sCm, sCn;
     cplx alpha, beta;
+    int conj_acc;  // use conj(accumulator): conj(A.conj(B)) = conj(A).B
+    int atomic;    // split-K: accumulate alpha*acc into C with FP64 atomics (C pre-scaled)
+    int kb_per_split;
 };
 
 template <int KIND>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int num_kb, int tiles_n,
-              Epi ep, int* err) {
+              Epi ep, int* err, int skip_tma, uint32_t wait_limit) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
@@ -151,6 +156,8 @@ __global__ void __launch_bounds__(128, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile_m = blockIdx.x / tiles_n, tile_n = blockIdx.x % tiles_n;
     const int bz = blockIdx.y;
+    const int kb0 = blockIdx.z * ep.kb_per_split;
+    const int kb1 = min(num_kb, kb0 + ep.kb_per_split);
     constexpr int KELEM = KIND == 0 ? 64 : 32;  // elements per 128-byte row
     constexpr uint32_t IDESC = instr_desc(KIND == 0 ? 1u : 2u, BM, BN);
 
@@ -177,28 +184,31 @@ __global__ void __launch_bounds__(128, 1)
 
     if (threadIdx.x == 0) {
         // TMA producer
-        for (int kb = 0; kb < num_kb; ++kb) {
-            int s = kb % STAGES;
-            uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (!mbar_wait(&empty[s], ph ^ 1u, err)) break;
+        for (int kb = kb0; kb < kb1; ++kb) {
+            int i = kb - kb0;
+            int s = i % STAGES;
+            uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u, err, wait_limit)) break;
             mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
+            if (skip_tma) continue;  // fault injection: the full barrier's bytes never arrive
             tma_load_3d(sA + s * A_STAGE, &ta, &full[s], kb * KELEM, tile_m * BM, bz);
             tma_load_3d(sB + s * B_STAGE, &tb, &full[s], kb * KELEM, tile_n * BN, bz);
         }
     } else if (threadIdx.x == 32) {
         // MMA issuer
         int done = 0;
-        for (int kb = 0; kb < num_kb; ++kb) {
-            int s = kb % STAGES;
-            uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph, err)) break;
+        for (int kb = kb0; kb < kb1; ++kb) {
+            int i = kb - kb0;
+            int s = i % STAGES;
+            uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph, err, wait_limit)) break;
             tc_fence_after();
             uint64_t ad = smem_desc(su32(sA + s * A_STAGE));
             uint64_t bd = smem_desc(su32(sB + s * B_STAGE));
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 // 32 bytes of K per MMA (16 bf16 or 8 tf32): +2 in the >>4 address field
-                mma<KIND>(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), IDESC, (kb | kk) != 0);
+                mma<KIND>(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), IDESC, (kb > kb0 || kk > 0) ? 1u : 0u);
             }
             mma_commit(&empty[s]);
             done = kb + 1;
@@ -209,8 +219,8 @@ __global__ void __launch_bounds__(128, 1)
     __syncwarp();
 
     // epilogue: warp w reads TMEM lanes 32w..32w+31 (accumulator rows)
-    bool got = mbar_wait(accb, 0, err);
-    if (!got) got = mbar_wait(accb, 0, err);  // second bounded wait before releasing TMEM
+    bool got = mbar_wait(accb, 0, err, wait_limit);
+    if (!got) got = mbar_wait(accb, 0, err, wait_limit);  // second bounded wait before releasing TMEM
     __syncwarp();
     tc_fence_after();
     const int64_t m = (int64_t)tile_m * BM + warp * 32 + lane;
@@ -220,14 +230,20 @@ __global__ void __launch_bounds__(128, 1)
     for (int c = 0; c < BN / 32; ++c) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-        if (got && m < ep.M) {
+        if (got && kb1 > kb0 && m < ep.M) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 int64_t n = ((int64_t)tile_n * BN + c * 32 + 2 * j) >> 1;
                 if (n < ep.N) {
                     double re = (double)__uint_as_float(r[2 * j]), im = (double)__uint_as_float(r[2 * j + 1]);
+                    if (ep.conj_acc) im = -im;
                     cplx* cp = Cb + m * ep.sCm + n * ep.sCn;
                     cplx v = make_double2(ep.alpha.x * re - ep.alpha.y * im, ep.alpha.x * im + ep.alpha.y * re);
+                    if (ep.atomic) {
+                        atomicAdd(&cp->x, v.x);
+                        atomicAdd(&cp->y, v.y);
+                        continue;
+                    }
                     if (!beta0) {
                         cplx o = *cp;
                         v.x += ep.beta.x * o.x - ep.beta.y * o.y;
@@ -350,65 +366,103 @@ bool g_attr_set[2] = {false, false};
 
 bool gemm_tc_available() { return true; }
 
+size_t tc_embed_bytes(int prec, int64_t rows, int64_t K, int64_t batch, int64_t& rows_p, int64_t& Kp, bool is_b) {
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    const int64_t S = kind == 0 ? 6 : 2, es = kind == 0 ? 2 : 4, kelem = ROWB / es;
+    Kp = (S * K + kelem - 1) / kelem * kelem;
+    rows_p = is_b ? (2 * rows + BN - 1) / BN * BN : (rows + BM - 1) / BM * BM;
+    return (size_t)(batch * rows_p * Kp * es);
+}
+
+void tc_embed_a(Dev& D, int prec, const cplx* A, int64_t sAb, int64_t sAm, int64_t sAk, bool cA, int64_t batch,
+                int64_t M, int64_t K, int64_t Mp, int64_t Kp, void* out) {
+    if (prec == LRCC_MIXED_BF16X3)
+        k_embed_a<0><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, Mp, Kp, out);
+    else
+        k_embed_a<1><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, Mp, Kp, out);
+    LAUNCH_CHECK(D);
+}
+
+void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64_t sBn, bool cB, int64_t batch,
+                int64_t K, int64_t N, int64_t Np2, int64_t Kp, void* out) {
+    if (prec == LRCC_MIXED_BF16X3)
+        k_embed_b<0><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBk, sBn, cB, batch, K, N, Np2, Kp, out);
+    else
+        k_embed_b<1><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBk, sBn, cB, batch, K, N, Np2, Kp, out);
+    LAUNCH_CHECK(D);
+}
+
+// C = alpha * op(A' B'^T) + beta C on embedded operands A' [batch][Mp][Kp], B' [batch][Np2][Kp]
+void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
+                      int64_t Mp, int64_t Np2, int64_t Kp, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
+                      cplx beta, bool conj_acc, double useful_flops) {
+    REQUIRE(D.err_flag != nullptr, "gemm_tc: no error word");
+    REQUIRE(batch <= 65535, "gemm_tc: batch too large");
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    const int64_t es = kind == 0 ? 2 : 4, kelem = ROWB / es;
+    CUtensorMap ta, tb;
+    encode(&ta, const_cast<void*>(pa), kind, Kp, Mp, batch, BM);
+    encode(&tb, const_cast<void*>(pb), kind, Kp, Np2, batch, BN);
+    int tiles_n = (int)(Np2 / BN);
+    int64_t tiles = (Mp / BM) * tiles_n;
+    REQUIRE(tiles < INT32_MAX, "gemm_tc: too many tiles");
+    int num_kb = (int)(Kp / kelem);
+    // split K when the tile grid cannot fill the SMs
+    int64_t ctas = tiles * batch;
+    int splits = 1;
+    if (ctas < 2 * D.sm_count && num_kb >= 32)
+        splits = (int)std::min<int64_t>((2 * D.sm_count + ctas - 1) / ctas, num_kb / 16);
+    splits = std::max(1, std::min(splits, 256));
+    int kps = (num_kb + splits - 1) / splits;
+    splits = (num_kb + kps - 1) / kps;
+    Epi ep{M, N, C, sCb, sCm, sCn, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0, kps};
+    if (splits > 1) {
+        GemmArgs pg{};
+        pg.M = M; pg.N = N; pg.batch = batch; pg.C = C; pg.sCb = sCb; pg.sCm = sCm; pg.sCn = sCn; pg.beta = beta;
+        gemm_prescale(D, pg);
+    }
+    // host-side fault injection for the failure-detection test: the producer
+    // skips its TMA issues so the consumers' bounded waits expire (short limit)
+    const char* inj = getenv("LRCC_INJECT_TMA_SKIP");
+    int skip = (inj && inj[0] == '1') ? 1 : 0;
+    uint32_t limit = skip ? WAIT_LIMIT_INJECT : WAIT_LIMIT;
+    dim3 grid((unsigned)tiles, (unsigned)batch, (unsigned)splits);
+    KTimer kt(D, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32", useful_flops,
+              (double)(batch * (Mp + Np2) * Kp * es) + 16.0 * M * N * batch, M, N, Kp, batch);
+    if (kind == 0) {
+        if (!g_attr_set[0]) {
+            CK(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+            g_attr_set[0] = true;
+        }
+        k_tc_gemm<0><<<grid, 128, SMEM_BYTES, D.st>>>(ta, tb, num_kb, tiles_n, ep, D.err_flag, skip, limit);
+    } else {
+        if (!g_attr_set[1]) {
+            CK(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+            g_attr_set[1] = true;
+        }
+        k_tc_gemm<1><<<grid, 128, SMEM_BYTES, D.st>>>(ta, tb, num_kb, tiles_n, ep, D.err_flag, skip, limit);
+    }
+    LAUNCH_CHECK(D);
+}
+
 void gemm_tc(Dev& D, const GemmArgs& g, int prec) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
     REQUIRE(prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3, "gemm_tc: bad precision");
-    REQUIRE(D.err_flag != nullptr, "gemm_tc: no error word");
     if (g.K <= 0) {
         gemm_f64(D, g);  // pure beta scaling
         return;
     }
-    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
-    const int64_t S = kind == 0 ? 6 : 2, es = kind == 0 ? 2 : 4, kelem = ROWB / es;
-    const int64_t Kp = (S * g.K + kelem - 1) / kelem * kelem;
-    const int64_t Mp = (g.M + BM - 1) / BM * BM;
-    const int64_t Np2 = (2 * g.N + BN - 1) / BN * BN;
-    REQUIRE(g.batch <= 65535, "gemm_tc: batch too large");
-    size_t bytesA = (size_t)(g.batch * Mp * Kp * es), bytesB = (size_t)(g.batch * Np2 * Kp * es);
+    int64_t Mp, Kp, Np2, Kp2;
+    size_t bytesA = tc_embed_bytes(prec, g.M, g.K, g.batch, Mp, Kp, false);
+    size_t bytesB = tc_embed_bytes(prec, g.N, g.K, g.batch, Np2, Kp2, true);
     void* pa = D.pool.get(bytesA);
     std::shared_ptr<DevBuf> ha(new DevBuf{&D.pool, pa, bytesA});
     void* pb = D.pool.get(bytesB);
     std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
     CK(cudaMemsetAsync(pa, 0, bytesA, D.st));
     CK(cudaMemsetAsync(pb, 0, bytesB, D.st));
-    if (kind == 0) {
-        k_embed_a<0><<<grid_n(D, g.batch * g.M * g.K), 256, 0, D.st>>>(g.A, g.sAb, g.sAm, g.sAk, g.cA, g.batch, g.M,
-                                                                         g.K, Mp, Kp, pa);
-        LAUNCH_CHECK(D);
-        k_embed_b<0><<<grid_n(D, g.batch * g.N * g.K), 256, 0, D.st>>>(g.B, g.sBb, g.sBk, g.sBn, g.cB, g.batch, g.K,
-                                                                         g.N, Np2, Kp, pb);
-        LAUNCH_CHECK(D);
-    } else {
-        k_embed_a<1><<<grid_n(D, g.batch * g.M * g.K), 256, 0, D.st>>>(g.A, g.sAb, g.sAm, g.sAk, g.cA, g.batch, g.M,
-                                                                         g.K, Mp, Kp, pa);
-        LAUNCH_CHECK(D);
-        k_embed_b<1><<<grid_n(D, g.batch * g.N * g.K), 256, 0, D.st>>>(g.B, g.sBb, g.sBk, g.sBn, g.cB, g.batch, g.K,
-                                                                         g.N, Np2, Kp, pb);
-        LAUNCH_CHECK(D);
-    }
-    CUtensorMap ta, tb;
-    encode(&ta, pa, kind, Kp, Mp, g.batch, BM);
-    encode(&tb, pb, kind, Kp, Np2, g.batch, BN);
-    Epi ep{g.M, g.N, g.C, g.sCb, g.sCm, g.sCn, g.alpha, g.beta};
-    int tiles_n = (int)(Np2 / BN);
-    int64_t tiles = (Mp / BM) * tiles_n;
-    REQUIRE(tiles < INT32_MAX, "gemm_tc: too many tiles");
-    int num_kb = (int)(Kp / kelem);
-    dim3 grid((unsigned)tiles, (unsigned)g.batch);
-    KTimer kt(D, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32", 8.0 * g.M * g.N * g.K * g.batch,
-              (double)(bytesA + bytesB) + 16.0 * g.M * g.N * g.batch);
-    if (kind == 0) {
-        if (!g_attr_set[0]) {
-            CK(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-            g_attr_set[0] = true;
-        }
-        k_tc_gemm<0><<<grid, 128, SMEM_BYTES, D.st>>>(ta, tb, num_kb, tiles_n, ep, D.err_flag);
-    } else {
-        if (!g_attr_set[1]) {
-            CK(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-            g_attr_set[1] = true;
-        }
-        k_tc_gemm<1><<<grid, 128, SMEM_BYTES, D.st>>>(ta, tb, num_kb, tiles_n, ep, D.err_flag);
-    }
-    LAUNCH_CHECK(D);
+    tc_embed_a(D, prec, g.A, g.sAb, g.sAm, g.sAk, g.cA, g.batch, g.M, g.K, Mp, Kp, pa);
+    tc_embed_b(D, prec, g.B, g.sBb, g.sBk, g.sBn, g.cB, g.batch, g.K, g.N, Np2, Kp, pb);
+    tc_gemm_embedded(D, prec, pa, pb, g.batch, g.M, g.N, Mp, Np2, Kp, g.C, g.sCb, g.sCm, g.sCn, g.alpha, g.beta,
+                     false, 8.0 * g.M * g.N * g.K * g.batch);
 }

@@ -6,40 +6,7 @@
 #include <cstring>
 #include <string>
 
-#include "solver.h"
-
-struct lrcc_ctx {
-    Dev D;
-    lrcc_options opt;
-    int O = 0, V = 0, L = 0, ncomp = 0;
-    std::vector<double> eps;
-    double* eo = nullptr;  // device
-    double* ev = nullptr;
-    Tensor B, mu;          // [L][N][N], [ncomp][N][N]
-    Ham H;
-    std::vector<Ham> Hmu;
-    LadderCtx lad;
-    std::unique_ptr<CCProg> cc;          // two-body program, primal cached at T
-    std::vector<std::unique_ptr<CCProg>> ccmu;  // one-body programs (xi, eta)
-    std::unique_ptr<CCProg> ccfx;        // scratch program for the F.X stencil
-    bool ground = false;
-    Amp T, Lam;                          // R = 1
-    std::string err;
-    double phase_ms[7] = {0};
-    int n_sigma64 = 0, n_sigma_mixed = 0;  // residual-map applications in the last solve
-    ~lrcc_ctx() {
-        cc.reset();
-        ccmu.clear();
-        ccfx.reset();
-        if (eo) cudaFree(eo);
-        if (ev) cudaFree(ev);
-        if (D.err_flag) cudaFree(D.err_flag);
-        for (auto& r : D.recs) {
-            cudaEventDestroy(r.a);
-            cudaEventDestroy(r.b);
-        }
-    }
-};
+#include "ctx.h"
 
 static std::string g_setup_err = "";
 
@@ -74,7 +41,7 @@ Tensor dev_copy_c(Dev& D, const double* host, std::vector<int64_t> shape) {
     return t;
 }
 
-void build_ham(lrcc_ctx* c) {
+void build_ham_impl(lrcc_ctx* c) {
     Dev& D = c->D;
     int O = c->O, V = c->V;
     int64_t N = O + V;
@@ -136,6 +103,7 @@ void build_ham(lrcc_ctx* c) {
     CK(cudaMemcpy(c->eo, eo.data(), sizeof(double) * O, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->ev, ev.data(), sizeof(double) * V, cudaMemcpyHostToDevice));
     c->ground = false;
+    c->ham_built = true;
 }
 
 // amplitudes of one RHS as program inputs (leading R dropped)
@@ -233,90 +201,77 @@ int solve_loop(lrcc_ctx* c, Amp& x, F&& resid, const std::vector<double>& shift,
                                       std::to_string(rn.empty() ? -1.0 : *std::max_element(rn.begin(), rn.end())) + ")");
 }
 
+template <class Apply>
+void response_solve(lrcc_ctx* c, Amp& z, const Amp& b, const std::vector<double>& shift, const double* shift_dev,
+                    Apply&& apply, std::vector<double>& final_res, int& n64, int& nmix);
+
 void do_ground(lrcc_ctx* c, cplx& E, int& itT, int& itL) {
     Dev& D = c->D;
     int O = c->O, V = c->V;
-    // MP2 start: one Jacobi step from T = 0
-    Amp T0 = amp_zeros(D, 1, O, V);
     std::vector<double> zero(1, 0.0);
     std::shared_ptr<DevBuf> hold;
     double* sh = dev_doubles(D, zero, hold);
     {
         Timer tm(D);
+        // MP2 start: one Jacobi step from T = 0
+        Amp T0 = amp_zeros(D, 1, O, V);
         Amp r0 = residual_T(D, *c->cc, T0, 0, LRCC_FP64);
         Amp T = amp_empty(D, 1, O, V);
         precond(D, nullptr, r0, T, c->eo, c->ev, sh);
+        itT = 0;
+        if (c->opt.prec != LRCC_FP64) {
+            // tensor-core residual until it stalls near its own precision, then FP64
+            const int p = c->opt.prec;
+            auto resm = [&](const Amp& x) { return amp_copy(D, residual_T(D, *c->cc, x, 0, p)); };
+            itT += solve_loop(c, T, resm, zero, std::max(1e-6, c->opt.r_tol), c->opt.max_iter, nullptr, false);
+        }
         auto res = [&](const Amp& x) { return amp_copy(D, residual_T(D, *c->cc, x, 0, LRCC_FP64)); };
-        itT = solve_loop(c, T, res, zero, c->opt.r_tol, c->opt.max_iter);
+        itT += solve_loop(c, T, res, zero, c->opt.r_tol, c->opt.max_iter);
         c->T = amp_copy(D, T);
         residual_T(D, *c->cc, c->T, 0, LRCC_FP64, &E);  // primal cached at converged T
         c->phase_ms[0] = tm.stop();
     }
     {
+        // Lambda: A^T lambda = -dE/dT  (same refinement scheme as the left response)
         Timer tm(D);
         Amp gE = grad_energy(D, *c->cc, O, V, LRCC_FP64);
-        Amp L0 = amp_empty(D, 1, O, V);
-        precond(D, nullptr, gE, L0, c->eo, c->ev, sh);
-        auto res = [&](const Amp& l) {
-            Amp r = vjp_unique(D, *c->cc, l, 0.0, LRCC_FP64);
-            amp_axpby(D, mkc(1.0), gE, mkc(1.0), r);
-            return r;
-        };
-        itL = solve_loop(c, L0, res, zero, c->opt.r_tol, c->opt.max_iter);
-        c->Lam = amp_copy(D, L0);
+        Amp Lm = amp_empty(D, 1, O, V);
+        std::vector<double> res;
+        int n64 = 0, nmix = 0;
+        auto apply = [&](const Amp& y, int p) { return vjp_unique(D, *c->cc, y, 0.0, p); };
+        double xt = c->opt.x_tol;
+        c->opt.x_tol = c->opt.r_tol;
+        try {
+            response_solve(c, Lm, gE, zero, sh, apply, res, n64, nmix);
+        } catch (...) {
+            c->opt.x_tol = xt;
+            throw;
+        }
+        c->opt.x_tol = xt;
+        itL = n64 + nmix;
+        c->Lam = amp_copy(D, Lm);
         c->phase_ms[1] = tm.stop();
     }
     c->ground = true;
 }
 
-// F X for each RHS of X: exact 5-point stencil of the Lagrangian gradient
-// g(T) = A(T)^T lambda + dE/dT, a polynomial of degree <= 3 in T (Eq. 34):
-//   F X = [g(T - 2hX) - 8 g(T - hX) + 8 g(T + hX) - g(T + 2hX)] / (12 h),
-// X scaled to unit max-norm first.  All 4 points of a chunk of right-hand
-// sides run as one batched primal evaluation and one batched reverse sweep.
+// F X for each RHS of X (Eq. 34): the directional derivative along X of the
+// Lagrangian gradient g(T) = A(T)^T lambda + dE/dT, taken exactly by
+// differentiating the reverse sweep (forward-over-reverse) at the converged T.
 Amp fx_product(lrcc_ctx* c, const Amp& X) {
     Dev& D = c->D;
     int64_t R = X.t1.d[0];
     int O = c->O, V = c->V;
-    Amp out = amp_empty(D, R, O, V);
-    std::vector<double> nrm;
-    max_abs_amp(D, X, nrm);
-    const double h = 0.5;
-    const int ks[4] = {-2, -1, 1, 2};
-    const double wk[4] = {1.0, -8.0, 8.0, -1.0};
-    // chunk so that the batched primal (about 24 doubles-sized slots per point) fits in ~24 GiB
-    double per_point = 24.0 * 16.0 * double(O) * O * V * V;
-    int64_t rc = std::max<int64_t>(1, std::min<int64_t>(R, (int64_t)((24.0 * (1ull << 30)) / (4.0 * per_point))));
-    for (int64_t r0 = 0; r0 < R; r0 += rc) {
-        int64_t r1 = std::min(R, r0 + rc), nr = r1 - r0, n = 4 * nr;
-        Amp Tk = amp_empty(D, n, O, V);
-        Amp Lk = amp_empty(D, n, O, V);
-        for (int q = 0; q < 4; ++q)
-            for (int64_t i = 0; i < nr; ++i) {
-                int64_t slot = q * nr + i, r = r0 + i;
-                Tensor a1 = Tk.t1.index(slot), a2 = Tk.t2.index(slot);
-                Tensor l1 = Lk.t1.index(slot), l2 = Lk.t2.index(slot);
-                axpby(D, mkc(1.0), c->T.t1.index(0), false, mkc(0.0), a1);
-                axpby(D, mkc(1.0), c->T.t2.index(0), false, mkc(0.0), a2);
-                axpby(D, mkc(1.0), c->Lam.t1.index(0), false, mkc(0.0), l1);
-                axpby(D, mkc(1.0), c->Lam.t2.index(0), false, mkc(0.0), l2);
-                double sc = nrm[r] > 0.0 ? ks[q] * h / nrm[r] : 0.0;
-                axpby(D, mkc(sc), X.t1.index(r), false, mkc(1.0), a1);
-                axpby(D, mkc(sc), X.t2.index(r), false, mkc(1.0), a2);
-            }
-        c->ccfx->P.eval(D, {Tk.t1, Tk.t2}, LRCC_FP64, true);
-        Amp g = vjp_unique(D, *c->ccfx, Lk, 1.0, LRCC_FP64);
-        for (int64_t i = 0; i < nr; ++i) {
-            int64_t r = r0 + i;
-            Tensor o1 = out.t1.index(r), o2 = out.t2.index(r);
-            for (int q = 0; q < 4; ++q) {
-                cplx w = mkc(nrm[r] > 0.0 ? wk[q] * nrm[r] / (12.0 * h) : 0.0);
-                axpby(D, w, g.t1.index(q * nr + i), false, q == 0 ? mkc(0.0) : mkc(1.0), o1);
-                axpby(D, w, g.t2.index(q * nr + i), false, q == 0 ? mkc(0.0) : mkc(1.0), o2);
-            }
-        }
-    }
-    return out;
+    CCProg& cp = *c->cc;  // holds the primal at the converged T
+    Tensor l2 = empty(D, c->Lam.t2.shape());
+    axpby(D, mkc(0.25), c->Lam.t2, false, mkc(0.0), l2);
+    Tensor ce = empty(D, {1});
+    fill(D, ce, mkc(1.0));
+    std::vector<Tensor> d = cp.P.jvp_of_vjp(D, {X.t1, X.t2}, {c->Lam.t1, l2, ce}, {cp.R1, cp.R2, cp.E}, LRCC_FP64);
+    (void)O;
+    (void)V;
+    (void)R;
+    return Amp{d[0], antisym4(D, d[1])};
 }
 
 // Linear response solve (M - shift_r) z = -b  for R right-hand sides where
@@ -501,6 +456,10 @@ lrcc_status fail(lrcc_ctx* c, const LrccError& e) {
 
 }  // namespace
 
+void ensure_ham(lrcc_ctx* c) {
+    if (!c->ham_built) build_ham_impl(c);
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -572,7 +531,6 @@ lrcc_status lrcc_setup(const double* eps, const double* B, int L, const double* 
         c->eps.assign(eps, eps + N);
         c->B = dev_copy_c(c->D, B, {L, N, N});
         c->mu = dev_copy_c(c->D, mu, {ncomp, N, N});
-        build_ham(c);
         CK(cudaStreamSynchronize(c->D.st));
         *out = c;
         return LRCC_OK;
@@ -600,6 +558,7 @@ lrcc_status lrcc_ccsd_ground(lrcc_ctx* c, double e_corr[2], int* iters_T, int* i
     try {
         cplx E = mkc(0.0);
         int itT = 0, itL = 0;
+        ensure_ham(c);
         do_ground(c, E, itT, itL);
         check_device_error(c->D);
         if (e_corr) {
@@ -644,6 +603,7 @@ static lrcc_status residual_impl(lrcc_ctx* c, int kind, const double* t, const d
     REQUIRE(R >= 1 && in && out, "bad residual arguments");
     REQUIRE(kind >= LRCC_RES_T && kind <= LRCC_RES_VJP_FULL, "bad residual kind");
     REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_MIXED_BF16X3, "bad precision");
+    ensure_ham(c);
     // stage inputs as [R][nt] on the device
     Tensor inb;
     if (device) inb = wrap((cplx*)in, {R, nt});
@@ -782,6 +742,7 @@ lrcc_status lrcc_ladder_dev(lrcc_ctx* c, const double* x, double* z, int R, int 
     try {
         REQUIRE(x && z && R >= 1, "bad ladder arguments");
         REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_MIXED_BF16X3, "bad precision");
+        ensure_ham(c);
         cudaStream_t st = (cudaStream_t)stream;
         cudaEvent_t ev;
         CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -849,6 +810,25 @@ lrcc_status lrcc_profile(lrcc_ctx* c, int enable) {
     return LRCC_OK;
 }
 
+lrcc_status lrcc_profile_dump(lrcc_ctx* c, const char* path) {
+    if (!c || !path) return LRCC_EINVAL;
+    if (cudaStreamSynchronize(c->D.st) != cudaSuccess) return LRCC_ECUDA;
+    FILE* f = fopen(path, "w");
+    if (!f) {
+        c->err = std::string("cannot open ") + path;
+        return LRCC_EINVAL;
+    }
+    fprintf(f, "kernel,M,N,K,batch,ms,flops\n");
+    for (auto& r : c->D.recs) {
+        float e = 0;
+        cudaEventElapsedTime(&e, r.a, r.b);
+        fprintf(f, "%s,%lld,%lld,%lld,%lld,%.6f,%.6e\n", r.name, (long long)r.m, (long long)r.n, (long long)r.k,
+                (long long)r.batch, e, r.flops);
+    }
+    fclose(f);
+    return LRCC_OK;
+}
+
 lrcc_status lrcc_kernel_stats(lrcc_ctx* c, int idx, const char** name, int64_t* count, double* ms, double* flops,
                               double* bytes) {
     if (!c || idx < 0) return LRCC_EINVAL;
@@ -878,11 +858,6 @@ lrcc_status lrcc_kernel_stats(lrcc_ctx* c, int idx, const char** name, int64_t* 
     return LRCC_OK;
 }
 
-lrcc_status lrcc_fns_truncate(lrcc_ctx* c, int by_count, double value, double omega, int* v_kept, double* occ_out) {
-    if (!c) return LRCC_EINVAL;
-    c->err = "lrcc_fns_truncate: not built yet";
-    (void)by_count; (void)value; (void)omega; (void)v_kept; (void)occ_out;
-    return LRCC_ESTATE;
-}
+
 
 }  // extern "C"

@@ -66,6 +66,7 @@ struct KRec {
     const char* name;
     cudaEvent_t a, b;
     double flops, bytes;
+    int64_t m = 0, n = 0, k = 0, batch = 0;  // GEMM shape (0 for other kernels)
 };
 
 struct Dev {
@@ -83,11 +84,17 @@ struct KTimer {
     Dev& D;
     KRec r;
     bool on;
-    KTimer(Dev& d, const char* name, double flops, double bytes) : D(d), on(d.timing) {
+    KTimer(Dev& d, const char* name, double flops, double bytes, int64_t m = 0, int64_t n = 0, int64_t k = 0,
+           int64_t batch = 0)
+        : D(d), on(d.timing) {
         if (!on) return;
         r.name = name;
         r.flops = flops;
         r.bytes = bytes;
+        r.m = m;
+        r.n = n;
+        r.k = k;
+        r.batch = batch;
         cudaEventCreate(&r.a);
         cudaEventCreate(&r.b);
         cudaEventRecord(r.a, D.st);
@@ -178,10 +185,22 @@ struct GemmArgs {
     cplx alpha, beta;
 };
 void gemm_f64(Dev& D, const GemmArgs& g);
+// C *= beta on the GEMM's output view (before split-K accumulation)
+void gemm_prescale(Dev& D, const GemmArgs& g);
 
 // tensor-core split-precision GEMM (gemm_tc.cu); prec = LRCC_MIXED_*
 bool gemm_tc_available();
 void gemm_tc(Dev& D, const GemmArgs& g, int prec);
+// pieces: embedded-operand sizes (rows padded to the tile, K to 128 bytes),
+// the split/convert kernels, and the GEMM on already embedded operands
+size_t tc_embed_bytes(int prec, int64_t rows, int64_t K, int64_t batch, int64_t& rows_p, int64_t& Kp, bool is_b);
+void tc_embed_a(Dev& D, int prec, const cplx* A, int64_t sAb, int64_t sAm, int64_t sAk, bool cA, int64_t batch,
+                int64_t M, int64_t K, int64_t Mp, int64_t Kp, void* out);
+void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64_t sBn, bool cB, int64_t batch,
+                int64_t K, int64_t N, int64_t Np2, int64_t Kp, void* out);
+void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
+                      int64_t Mp, int64_t Np2, int64_t Kp, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
+                      cplx beta, bool conj_acc, double useful_flops);
 
 // ---------------------------------------------------------------------------
 // contraction engine (engine.cu)
@@ -201,6 +220,15 @@ void perm_axpby(Dev& D, const std::string& spec, cplx alpha, const Tensor& x, cp
 struct LadderCtx {
     Tensor Bvv;      // [L][V][V]
     int slab_rows = 0;
+    // cached embedded <ab||ef> matrix W' [Mp][Kp] (rows a<b, K = pairs e<f) for
+    // one mixed precision, built on first use when it fits in device memory
+    std::shared_ptr<DevBuf> wcache;
+    int wcache_prec = -1;
+    int64_t w_Mp = 0, w_Kp = 0;
+    bool wcache_disabled = false;
+    // cached FP64 <ab||ef> matrix [P_V][P_V] for the FP64 ladder, when it fits
+    Tensor w64;
+    bool w64_disabled = false;
 };
 void ladder(Dev& D, LadderCtx& L, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose, int prec);
 

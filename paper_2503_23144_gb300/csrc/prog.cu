@@ -162,9 +162,19 @@ std::vector<Tensor> Prog::jvp(Dev& D, const std::vector<Tensor>& tin, const std:
         }
     for (int o : outs) last[o] = (int)ops.size();
     for (size_t k = 0; k < inputs.size(); ++k) last[inputs[k]] = (int)ops.size();
+    // only ops whose result reaches a requested output
+    std::vector<char> need(n, 0);
+    for (int o : outs) need[o] = 1;
+    for (int k = (int)ops.size() - 1; k >= 0; --k) {
+        if (!need[ops[k].out]) continue;
+        for (auto& t : ops[k].terms) {
+            if (t.a >= 0) need[t.a] = 1;
+            if (t.b >= 0) need[t.b] = 1;
+        }
+    }
     for (int k = 0; k < (int)ops.size(); ++k) {
         const Op& o = ops[k];
-        if (!active[o.out]) continue;
+        if (!active[o.out] || !need[o.out]) continue;
         std::vector<int64_t> sh = shape0[o.out];
         sh.insert(sh.begin(), R);
         Tensor out = empty(D, sh);
@@ -262,6 +272,138 @@ std::vector<Tensor> Prog::vjp(Dev& D, const std::vector<Tensor>& cot, const std:
             res.push_back(zeros(D, sh));
         } else {
             res.push_back(adj[s]);
+        }
+    }
+    return res;
+}
+
+std::vector<Tensor> Prog::jvp_of_vjp(Dev& D, const std::vector<Tensor>& tin, const std::vector<Tensor>& cot,
+                                     const std::vector<int>& outs, int prec) {
+    REQUIRE(RB == 0, "jvp_of_vjp needs the unbatched primal");
+    const int n = (int)val.size();
+    const int64_t R = tin.at(0).d[0];
+    // 1. tangents of every active slot (kept)
+    std::vector<Tensor> tan(n);
+    for (size_t k = 0; k < inputs.size(); ++k) tan[inputs[k]] = tin[k];
+    for (int k = 0; k < (int)ops.size(); ++k) {
+        const Op& o = ops[k];
+        if (!active[o.out]) continue;
+        std::vector<int64_t> sh = shape0[o.out];
+        sh.insert(sh.begin(), R);
+        Tensor out = empty(D, sh);
+        bool first = true;
+        auto beta = [&]() { cplx b = first ? mkc(0.0) : mkc(1.0); first = false; return b; };
+        for (auto& t : o.terms) {
+            if (t.kind == TK_EIN) {
+                std::string la = lhs_a(t.spec), lb = lhs_b(t.spec), lc = rhs(t.spec);
+                if (active[t.a]) ein(D, "Z" + la + "," + lb + "->Z" + lc, t.c, tan[t.a], false, val[t.b], false, beta(), out, prec);
+                if (active[t.b]) ein(D, la + ",Z" + lb + "->Z" + lc, t.c, val[t.a], false, tan[t.b], false, beta(), out, prec);
+            } else if (t.kind == TK_PERM) {
+                if (active[t.a]) perm_axpby(D, "Z" + perm_in(t.spec) + "->Z" + rhs(t.spec), t.c, tan[t.a], beta(), out);
+            } else if (active[t.a]) {
+                Tensor x = as5(tan[t.a], R, O, V), z = as5(out, R, O, V);
+                ladder(D, *lad, x, t.c, beta(), z, false, prec);
+            }
+        }
+        if (first) fill(D, out, mkc(0.0));
+        tan[o.out] = out;
+    }
+    // 2. adjoints (unbatched: leading dim 1 dropped) and 3. their tangents, in one reverse sweep
+    std::vector<Tensor> adj(n), dadj(n);
+    for (size_t k = 0; k < outs.size(); ++k)
+        if (cot[k].p) adj[outs[k]] = cot[k].index(0);
+    auto acc1 = [&](int slot, auto&& write) {  // unbatched adjoint accumulation
+        if (!active[slot]) return;
+        if (!adj[slot].p) {
+            adj[slot] = empty(D, shape0[slot]);
+            write(adj[slot], mkc(0.0));
+        } else {
+            write(adj[slot], mkc(1.0));
+        }
+    };
+    auto accR = [&](int slot, auto&& write) {  // batched tangent-of-adjoint accumulation
+        if (!active[slot]) return;
+        if (!dadj[slot].p) {
+            std::vector<int64_t> sh = shape0[slot];
+            sh.insert(sh.begin(), R);
+            dadj[slot] = empty(D, sh);
+            write(dadj[slot], mkc(0.0));
+        } else {
+            write(dadj[slot], mkc(1.0));
+        }
+    };
+    for (int k = (int)ops.size() - 1; k >= 0; --k) {
+        const Op& o = ops[k];
+        if (!active[o.out]) continue;
+        Tensor cb = adj[o.out], dcb = dadj[o.out];
+        if (!cb.p && !dcb.p) continue;
+        for (auto& t : o.terms) {
+            if (t.kind == TK_EIN) {
+                std::string la = lhs_a(t.spec), lb = lhs_b(t.spec), lc = rhs(t.spec);
+                if (active[t.a]) {
+                    if (cb.p)
+                        acc1(t.a, [&](Tensor& dst, cplx b) {
+                            ein(D, lc + "," + lb + "->" + la, t.c, cb, false, val[t.b], false, b, dst, prec);
+                        });
+                    if (dcb.p)
+                        accR(t.a, [&](Tensor& dst, cplx b) {
+                            ein(D, "Z" + lc + "," + lb + "->Z" + la, t.c, dcb, false, val[t.b], false, b, dst, prec);
+                        });
+                    if (cb.p && active[t.b])
+                        accR(t.a, [&](Tensor& dst, cplx b) {
+                            ein(D, lc + ",Z" + lb + "->Z" + la, t.c, cb, false, tan[t.b], false, b, dst, prec);
+                        });
+                }
+                if (active[t.b]) {
+                    if (cb.p)
+                        acc1(t.b, [&](Tensor& dst, cplx b) {
+                            ein(D, la + "," + lc + "->" + lb, t.c, val[t.a], false, cb, false, b, dst, prec);
+                        });
+                    if (dcb.p)
+                        accR(t.b, [&](Tensor& dst, cplx b) {
+                            ein(D, la + ",Z" + lc + "->Z" + lb, t.c, val[t.a], false, dcb, false, b, dst, prec);
+                        });
+                    if (cb.p && active[t.a])
+                        accR(t.b, [&](Tensor& dst, cplx b) {
+                            ein(D, "Z" + la + "," + lc + "->Z" + lb, t.c, tan[t.a], false, cb, false, b, dst, prec);
+                        });
+                }
+            } else if (t.kind == TK_PERM) {
+                if (!active[t.a]) continue;
+                std::string lx = perm_in(t.spec), ly = rhs(t.spec);
+                if (cb.p)
+                    acc1(t.a, [&](Tensor& dst, cplx b) { perm_axpby(D, ly + "->" + lx, t.c, cb, b, dst); });
+                if (dcb.p)
+                    accR(t.a, [&](Tensor& dst, cplx b) { perm_axpby(D, "Z" + ly + "->Z" + lx, t.c, dcb, b, dst); });
+            } else {
+                if (!active[t.a]) continue;
+                if (cb.p)
+                    acc1(t.a, [&](Tensor& dst, cplx b) {
+                        Tensor x = as5(cb, 1, O, V), z = as5(dst, 1, O, V);
+                        ladder(D, *lad, x, t.c, b, z, true, prec);
+                    });
+                if (dcb.p)
+                    accR(t.a, [&](Tensor& dst, cplx b) {
+                        Tensor x = as5(dcb, R, O, V), z = as5(dst, R, O, V);
+                        ladder(D, *lad, x, t.c, b, z, true, prec);
+                    });
+            }
+        }
+        bool is_in = std::find(inputs.begin(), inputs.end(), o.out) != inputs.end();
+        if (!is_in) {
+            adj[o.out] = Tensor();
+            dadj[o.out] = Tensor();
+            tan[o.out] = Tensor();
+        }
+    }
+    std::vector<Tensor> res;
+    for (int s : inputs) {
+        if (!dadj[s].p) {
+            std::vector<int64_t> sh = shape0[s];
+            sh.insert(sh.begin(), R);
+            res.push_back(zeros(D, sh));
+        } else {
+            res.push_back(dadj[s]);
         }
     }
     return res;

@@ -45,6 +45,12 @@ struct Prog {
     // reverse sweep: cotangents of `outs` [R][...] (undefined tensor = zero)
     // -> cotangents of the inputs (holomorphic transpose, no conjugation)
     std::vector<Tensor> vjp(Dev& D, const std::vector<Tensor>& cot, const std::vector<int>& outs, int prec);
+    // forward-over-reverse: the directional derivative, along the input
+    // tangents tin [R][...], of the reverse sweep with fixed cotangents cot
+    // (leading dim 1, shared by all R directions).  Returns [R][...] per input.
+    // Needs the unbatched primal (eval with batched = false).
+    std::vector<Tensor> jvp_of_vjp(Dev& D, const std::vector<Tensor>& tin, const std::vector<Tensor>& cot,
+                                   const std::vector<int>& outs, int prec);
 
   private:
     std::vector<int64_t> out_shape(const Op& op) const;

@@ -59,6 +59,7 @@ SIGNATURES = [
     ("lrcc_phase_times", ctypes.c_int, [_vp, _dp]),
     ("lrcc_kernel_launches", ctypes.c_int64, [_vp]),
     ("lrcc_profile", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("lrcc_profile_dump", ctypes.c_int, [_vp, ctypes.c_char_p]),
     ("lrcc_get_amplitudes", ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     ("lrcc_ladder_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                            ctypes.c_int, _vp]),
@@ -269,6 +270,10 @@ def lrcc_solve_counts(ctx: Context):
 
 def lrcc_profile(ctx: Context, enable: bool) -> None:
     ctx.check(library().lrcc_profile(ctx.h, int(enable)))
+
+
+def lrcc_profile_dump(ctx: Context, path: str) -> None:
+    ctx.check(library().lrcc_profile_dump(ctx.h, path.encode()))
 
 
 def lrcc_kernel_stats(ctx: Context) -> dict:

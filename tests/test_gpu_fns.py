@@ -1,0 +1,62 @@
+"""FNS++ truncation on the GPU (lrcc_fns_truncate) against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import ccsd, fns
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2503_23144_gb300 import build, lrcc
+    build.build()
+    assert torch.cuda.is_available()
+    return lrcc
+
+
+def _ctx(L, s, **kw):
+    o = L.lrcc_default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return L.lrcc_setup(s["eps"], s["B"], s["mu"], s["O"], s["V"], o)
+
+
+def test_fnspp_truncated_alpha_and_occupations(L):
+    s = synth.make_system(4, 31, 40, seed=2)
+    keep, oms = 13, [0.0, 0.05]
+    new, occ_ref, _ = fns.truncate(s, True, keep)
+    a_ref = ccsd.polarizability(new, (0, 1, 2), oms, tol=1e-11)
+    ctx = _ctx(L, s, x_tol=1e-10)
+    vk, occ = L.lrcc_fns_truncate(ctx, True, keep)
+    assert vk == keep
+    assert np.abs(occ - occ_ref).max() < 1e-12 * occ_ref.max()
+    L.lrcc_ccsd_ground(ctx)
+    a, _ = L.lrcc_solve(ctx, oms, [0, 1, 2])
+    assert np.abs(a - a_ref).max() < 1e-9 * np.abs(a_ref).max()
+
+
+def test_fnspp_threshold_mode_and_frequency(L):
+    s = synth.make_system(3, 24, 30, seed=5)
+    thr, w = 2e-3, 0.03
+    new, occ_ref, _ = fns.truncate(s, False, thr, omega=w)
+    ctx = _ctx(L, s)
+    vk, occ = L.lrcc_fns_truncate(ctx, False, thr, omega=w)
+    assert vk == new["V"] == int(np.sum(occ_ref >= thr))
+    assert np.abs(occ - occ_ref).max() < 1e-12 * occ_ref.max()
+
+
+def test_fnspp_untruncated_reproduces_full_alpha(L):
+    s = synth.make_system(3, 14, 20, seed=9)
+    oms = [0.0, 0.06]
+    c_full = _ctx(L, s, x_tol=1e-10)
+    L.lrcc_ccsd_ground(c_full)
+    a_full, _ = L.lrcc_solve(c_full, oms, [0, 1, 2])
+    c_tr = _ctx(L, s, x_tol=1e-10)
+    vk, _ = L.lrcc_fns_truncate(c_tr, True, 14)
+    assert vk == 14
+    L.lrcc_ccsd_ground(c_tr)
+    a_tr, _ = L.lrcc_solve(c_tr, oms, [0, 1, 2])
+    assert np.abs(a_tr - a_full).max() < 1e-10 * np.abs(a_full).max()

@@ -177,9 +177,10 @@ def test_ladder_tensor_core_vs_fp64(L, prec, tol):
         x = torch.randn(R, O, O, V, V, dtype=torch.complex128, device="cuda", generator=g)
         x = x - x.transpose(1, 2)
         x = x - x.transpose(3, 4)
-        z64 = L.lrcc_ladder_dev(ctx, x)
-        z = L.lrcc_ladder_dev(ctx, x, prec=prec)
-        assert (z - z64).abs().max().item() < tol * z64.abs().max().item()
+        for tr in (False, True):
+            z64 = L.lrcc_ladder_dev(ctx, x, transpose=tr)
+            z = L.lrcc_ladder_dev(ctx, x, transpose=tr, prec=prec)
+            assert (z - z64).abs().max().item() < tol * z64.abs().max().item()
 
 
 @pytest.mark.parametrize("prec", [1, 2])
