@@ -117,6 +117,21 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
         else if (ia && ib) gk.push_back(c);
         else throw LrccError(LRCC_EINVAL, "label in one operand only: " + spec);
     }
+    if (gk.empty()) {
+        // no contracted label: a broadcast product written straight into C
+        Tensor Av, Bv;
+        Av.nd = Bv.nd = C.nd;
+        Av.p = A0.p;
+        Bv.p = B0.p;
+        for (int k = 0; k < C.nd; ++k) {
+            int pa = pos(sp.a, sp.c[k]), pb = pos(sp.b, sp.c[k]);
+            Av.d[k] = Bv.d[k] = C.d[k];
+            Av.s[k] = pa >= 0 ? A0.s[pa] : 0;
+            Bv.s[k] = pb >= 0 ? B0.s[pb] : 0;
+        }
+        outer_axpby(D, alpha, Av, cA, Bv, cB, beta, C);
+        return;
+    }
     Tensor A = A0, B = B0;
     std::string la = sp.a, lb = sp.b;
     bool ca = cA, cb = cB;

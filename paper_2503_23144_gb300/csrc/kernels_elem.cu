@@ -219,6 +219,95 @@ static ShapeStrides simplify(const Tensor& x, const Tensor& y) {
     return ss;
 }
 
+// Tiled transpose-axpby for permutations whose innermost dimensions differ:
+// a 32x32 tile over (dim kx with x-stride 1, dim ky with y-stride 1) is read
+// coalesced along kx into shared memory and written coalesced along ky.
+// The remaining dimensions are enumerated by blockIdx.y (batch).
+struct TStr {
+    int nb;                 // batch dims
+    int64_t bd[MAXD];
+    int64_t bsx[MAXD], bsy[MAXD];
+    int64_t nx, ny;         // extents of the x-inner and y-inner dims
+    int64_t sxy, syx;       // x stride of the y-inner dim, y stride of the x-inner dim
+    int64_t nbatch;
+};
+
+template <bool BETA0>
+__global__ void k_transpose(TStr t, cplx alpha, const cplx* __restrict__ x, int conjx, cplx beta,
+                            cplx* __restrict__ y) {
+    __shared__ cplx tile[32][33];
+    const int64_t tiles_x = (t.nx + 31) / 32;
+    for (int64_t bb = blockIdx.y; bb < t.nbatch; bb += gridDim.y) {
+        int64_t r = bb, ox = 0, oy = 0;
+        for (int k = t.nb - 1; k >= 0; --k) {
+            int64_t c = r % t.bd[k];
+            r /= t.bd[k];
+            ox += c * t.bsx[k];
+            oy += c * t.bsy[k];
+        }
+        const int64_t tx0 = (blockIdx.x % tiles_x) * 32, ty0 = (blockIdx.x / tiles_x) * 32;
+        // read: threadIdx.x runs along the x-inner dim
+        for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+            int64_t ix = tx0 + threadIdx.x, iy = ty0 + j;
+            if (ix < t.nx && iy < t.ny) {
+                cplx v = x[ox + ix + iy * t.sxy];
+                if (conjx) v.y = -v.y;
+                tile[j][threadIdx.x] = v;
+            }
+        }
+        __syncthreads();
+        // write: threadIdx.x runs along the y-inner dim
+        for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+            int64_t iy = ty0 + threadIdx.x, ix = tx0 + j;
+            if (ix < t.nx && iy < t.ny) {
+                cplx v = tile[threadIdx.x][j];
+                cplx o = make_double2(alpha.x * v.x - alpha.y * v.y, alpha.x * v.y + alpha.y * v.x);
+                cplx* yp = y + oy + iy + ix * t.syx;
+                if (!BETA0) {
+                    cplx w = *yp;
+                    o.x += beta.x * w.x - beta.y * w.y;
+                    o.y += beta.x * w.y + beta.y * w.x;
+                }
+                *yp = o;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+static bool try_transpose(Dev& D, cplx alpha, const ShapeStrides& ss, const cplx* x, bool conjx, cplx beta, cplx* y) {
+    int kx = -1, ky = -1;
+    for (int k = 0; k < ss.nd; ++k) {
+        if (ss.sx[k] == 1) kx = k;
+        if (ss.sy[k] == 1) ky = k;
+    }
+    if (kx < 0 || ky < 0 || kx == ky || ss.d[kx] < 8 || ss.d[ky] < 8) return false;
+    TStr t;
+    t.nb = 0;
+    t.nbatch = 1;
+    for (int k = 0; k < ss.nd; ++k) {
+        if (k == kx || k == ky) continue;
+        t.bd[t.nb] = ss.d[k];
+        t.bsx[t.nb] = ss.sx[k];
+        t.bsy[t.nb] = ss.sy[k];
+        t.nbatch *= ss.d[k];
+        t.nb++;
+    }
+    t.nx = ss.d[kx];
+    t.ny = ss.d[ky];
+    t.sxy = ss.sx[ky];
+    t.syx = ss.sy[kx];
+    int64_t tiles = ((t.nx + 31) / 32) * ((t.ny + 31) / 32);
+    if (tiles > INT32_MAX) return false;
+    dim3 block(32, 8);
+    dim3 grid((unsigned)tiles, (unsigned)std::min<int64_t>(t.nbatch, 65535));
+    bool beta0 = beta.x == 0.0 && beta.y == 0.0;
+    if (beta0) k_transpose<true><<<grid, block, 0, D.st>>>(t, alpha, x, conjx, beta, y);
+    else k_transpose<false><<<grid, block, 0, D.st>>>(t, alpha, x, conjx, beta, y);
+    LAUNCH_CHECK(D);
+    return true;
+}
+
 void axpby(Dev& D, cplx alpha, const Tensor& x, bool conjx, cplx beta, Tensor& y) {
     if (x.nd != y.nd) throw LrccError(LRCC_EINVAL, "axpby rank mismatch");
     for (int k = 0; k < y.nd; ++k)
@@ -231,6 +320,8 @@ void axpby(Dev& D, cplx alpha, const Tensor& x, bool conjx, cplx beta, Tensor& y
     if (ss.nd == 1 && ss.sx[0] == 1 && ss.sy[0] == 1) {
         if (beta0) k_axpby_contig<true><<<g, th, 0, D.st>>>(n, alpha, x.p, conjx, beta, y.p);
         else k_axpby_contig<false><<<g, th, 0, D.st>>>(n, alpha, x.p, conjx, beta, y.p);
+    } else if (try_transpose(D, alpha, ss, x.p, conjx, beta, y.p)) {
+        return;
     } else {
         if (beta0) k_axpby<true><<<g, th, 0, D.st>>>(ss, n, alpha, x.p, conjx, beta, y.p);
         else k_axpby<false><<<g, th, 0, D.st>>>(ss, n, alpha, x.p, conjx, beta, y.p);
@@ -313,4 +404,134 @@ double max_abs(Dev& D, const Tensor& y) {
     CK(cudaMemcpyAsync(&h, dv, sizeof(double), cudaMemcpyDeviceToHost, D.st));
     CK(cudaStreamSynchronize(D.st));
     return h;
+}
+
+// ---------------------------------------------------------------------------
+// broadcast product: C = alpha * op(A) * op(B) + beta * C elementwise over C's
+// index space (an einsum without contracted labels), offsets from strides
+// ---------------------------------------------------------------------------
+struct Str3 {
+    int nd;
+    int64_t d[MAXD];
+    int64_t sa[MAXD], sb[MAXD], sc[MAXD];
+};
+
+template <bool BETA0>
+__global__ void k_outer(Str3 s, int64_t n, cplx alpha, const cplx* __restrict__ a, int ca, const cplx* __restrict__ b,
+                        int cb, cplx beta, cplx* __restrict__ c) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = idx, oa = 0, ob = 0, oc = 0;
+        for (int k = s.nd - 1; k >= 0; --k) {
+            int64_t q = r % s.d[k];
+            r /= s.d[k];
+            oa += q * s.sa[k];
+            ob += q * s.sb[k];
+            oc += q * s.sc[k];
+        }
+        cplx u = a[oa], v = b[ob];
+        if (ca) u.y = -u.y;
+        if (cb) v.y = -v.y;
+        cplx p = cmul(alpha, cmul(u, v));
+        if (!BETA0) {
+            cplx w = cmul(beta, c[oc]);
+            p.x += w.x;
+            p.y += w.y;
+        }
+        c[oc] = p;
+    }
+}
+
+// A, B given as views over C's dimensions (stride 0 where a label is absent)
+void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, bool cb, cplx beta, Tensor& C) {
+    Str3 s;
+    s.nd = 0;
+    for (int k = 0; k < C.nd; ++k) {
+        if (C.d[k] == 1) continue;
+        if (s.nd > 0) {
+            int j = s.nd - 1;
+            if (s.sa[j] == A.s[k] * C.d[k] && s.sb[j] == B.s[k] * C.d[k] && s.sc[j] == C.s[k] * C.d[k]) {
+                s.d[j] *= C.d[k];
+                s.sa[j] = A.s[k];
+                s.sb[j] = B.s[k];
+                s.sc[j] = C.s[k];
+                continue;
+            }
+        }
+        s.d[s.nd] = C.d[k];
+        s.sa[s.nd] = A.s[k];
+        s.sb[s.nd] = B.s[k];
+        s.sc[s.nd] = C.s[k];
+        s.nd++;
+    }
+    if (s.nd == 0) {
+        s.nd = 1;
+        s.d[0] = 1;
+        s.sa[0] = s.sb[0] = s.sc[0] = 0;
+    }
+    int64_t n = C.numel();
+    if (n == 0) return;
+    bool beta0 = beta.x == 0.0 && beta.y == 0.0;
+    int th = 256, g = grid_for(D, n, th);
+    if (beta0) k_outer<true><<<g, th, 0, D.st>>>(s, n, alpha, A.p, ca, B.p, cb, beta, C.p);
+    else k_outer<false><<<g, th, 0, D.st>>>(s, n, alpha, A.p, ca, B.p, cb, beta, C.p);
+    LAUNCH_CHECK(D);
+}
+
+// ---------------------------------------------------------------------------
+// antisymmetrisers on contiguous [nb][O][O][V][V]:
+//   mode 1: x_ijab - x_jiab,  mode 2: x_ijab - x_ijba,  mode 3: both (4 terms)
+// y = alpha * P x + beta * y.  Each P is its own transpose.
+// ---------------------------------------------------------------------------
+template <bool BETA0>
+__global__ void k_asym(int mode, int64_t n, int64_t O, int64_t V, cplx alpha, const cplx* __restrict__ x, cplx beta,
+                       cplx* __restrict__ y) {
+    const int64_t VV = V * V, OVV = O * VV;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = idx % V, t = idx / V, a = t % V;
+        t /= V;
+        int64_t j = t % O;
+        t /= O;
+        int64_t i = t % O, r = t / O;
+        const cplx* xr = x + r * O * OVV;
+        cplx v = xr[i * OVV + j * VV + a * V + b];
+        if (mode & 1) {
+            cplx w = xr[j * OVV + i * VV + a * V + b];
+            v.x -= w.x;
+            v.y -= w.y;
+        }
+        if (mode & 2) {
+            cplx w = xr[i * OVV + j * VV + b * V + a];
+            v.x -= w.x;
+            v.y -= w.y;
+        }
+        if (mode == 3) {
+            cplx w = xr[j * OVV + i * VV + b * V + a];
+            v.x += w.x;
+            v.y += w.y;
+        }
+        v = cmul(alpha, v);
+        if (!BETA0) {
+            cplx w = cmul(beta, y[idx]);
+            v.x += w.x;
+            v.y += w.y;
+        }
+        y[idx] = v;
+    }
+}
+
+void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor& y) {
+    REQUIRE(mode >= 1 && mode <= 3, "asym: bad mode");
+    REQUIRE(x.contiguous() && y.contiguous() && x.numel() == y.numel() && x.nd >= 4 && y.nd >= 4,
+            "asym: contiguous [..][O][O][V][V] tensors expected");
+    int64_t O = x.d[x.nd - 4], V = x.d[x.nd - 1];
+    REQUIRE(x.d[x.nd - 3] == O && x.d[x.nd - 2] == V, "asym: [..][O][O][V][V] expected");
+    int64_t n = y.numel();
+    if (n == 0) return;
+    bool beta0 = beta.x == 0.0 && beta.y == 0.0;
+    int th = 256, g = grid_for(D, n, th);
+    if (beta0) k_asym<true><<<g, th, 0, D.st>>>(mode, n, O, V, alpha, x.p, beta, y.p);
+    else k_asym<false><<<g, th, 0, D.st>>>(mode, n, O, V, alpha, x.p, beta, y.p);
+    LAUNCH_CHECK(D);
 }

@@ -164,6 +164,12 @@ Tensor wrap(cplx* p, std::vector<int64_t> shape);
 // y = alpha * op(x) + beta * y over identical shapes; beta == 0 overwrites.
 void axpby(Dev& D, cplx alpha, const Tensor& x, bool conjx, cplx beta, Tensor& y);
 void fill(Dev& D, Tensor& y, cplx v);
+// C = alpha op(A) op(B) + beta C elementwise; A and B are views over C's dims
+// (stride 0 along dims they do not carry)
+void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, bool cb, cplx beta, Tensor& C);
+// y = alpha P x + beta y on contiguous [..][O][O][V][V]; P = P(ij) (mode 1),
+// P(ab) (mode 2) or P(ij)P(ab) (mode 3)
+void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor& y);
 // max |y| over all elements (host result; synchronises the stream)
 double max_abs(Dev& D, const Tensor& y);
 // per-leading-index max |y| into dev out[R] (double), no sync

@@ -65,7 +65,7 @@ std::vector<int64_t> Prog::out_shape(const Op& op) const {
     const Term& t = op.terms.at(0);
     const std::vector<int64_t>& A = shape0[t.a];
     std::vector<int64_t> sh;
-    if (t.kind == TK_LADDER) return A;
+    if (t.kind == TK_LADDER || t.kind == TK_ASYM) return A;
     if (t.kind == TK_PERM) {
         std::string lx = perm_in(t.spec), ly = rhs(t.spec);
         for (char c : ly) sh.push_back(A[lx.find(c)]);
@@ -118,6 +118,9 @@ void Prog::apply_term(Dev& D, const Term& t, cplx beta, Tensor& out, int prec) {
             std::string z = out_batched ? "Z" : "";
             perm_axpby(D, z + lx + "->" + z + ly, c, val[t.a], beta, out);
         }
+    } else if (t.kind == TK_ASYM) {
+        REQUIRE(RB == 0 || active[t.a], "asym term on a constant in a batched evaluation");
+        asym_axpby(D, asym_mode(t), c, val[t.a], beta, out);
     } else {
         int64_t R = (RB > 0 && active[t.a]) ? RB : 1;
         Tensor x = as5(val[t.a], R, O, V);
@@ -189,6 +192,8 @@ std::vector<Tensor> Prog::jvp(Dev& D, const std::vector<Tensor>& tin, const std:
                     ein(D, zp(t.a) + la + ",Z" + lb + "->Z" + lc, t.c, val[t.a], false, tan[t.b], false, beta(), out, prec);
             } else if (t.kind == TK_PERM) {
                 if (active[t.a]) perm_axpby(D, "Z" + perm_in(t.spec) + "->Z" + rhs(t.spec), t.c, tan[t.a], beta(), out);
+            } else if (t.kind == TK_ASYM) {
+                if (active[t.a]) asym_axpby(D, asym_mode(t), t.c, tan[t.a], beta(), out);
             } else {
                 if (active[t.a]) {
                     Tensor x = as5(tan[t.a], R, O, V), z = as5(out, R, O, V);
@@ -253,6 +258,9 @@ std::vector<Tensor> Prog::vjp(Dev& D, const std::vector<Tensor>& cot, const std:
                     acc(t.a, [&](Tensor& dst, cplx b) {
                         perm_axpby(D, "Z" + rhs(t.spec) + "->Z" + perm_in(t.spec), t.c, cb, b, dst);
                     });
+            } else if (t.kind == TK_ASYM) {
+                if (active[t.a])
+                    acc(t.a, [&](Tensor& dst, cplx b) { asym_axpby(D, asym_mode(t), t.c, cb, b, dst); });
             } else {
                 if (active[t.a])
                     acc(t.a, [&](Tensor& dst, cplx b) {
@@ -300,6 +308,8 @@ std::vector<Tensor> Prog::jvp_of_vjp(Dev& D, const std::vector<Tensor>& tin, con
                 if (active[t.b]) ein(D, la + ",Z" + lb + "->Z" + lc, t.c, val[t.a], false, tan[t.b], false, beta(), out, prec);
             } else if (t.kind == TK_PERM) {
                 if (active[t.a]) perm_axpby(D, "Z" + perm_in(t.spec) + "->Z" + rhs(t.spec), t.c, tan[t.a], beta(), out);
+            } else if (t.kind == TK_ASYM) {
+                if (active[t.a]) asym_axpby(D, asym_mode(t), t.c, tan[t.a], beta(), out);
             } else if (active[t.a]) {
                 Tensor x = as5(tan[t.a], R, O, V), z = as5(out, R, O, V);
                 ladder(D, *lad, x, t.c, beta(), z, false, prec);
@@ -368,6 +378,10 @@ std::vector<Tensor> Prog::jvp_of_vjp(Dev& D, const std::vector<Tensor>& tin, con
                             ein(D, "Z" + la + "," + lc + "->Z" + lb, t.c, tan[t.a], false, cb, false, b, dst, prec);
                         });
                 }
+            } else if (t.kind == TK_ASYM) {
+                if (!active[t.a]) continue;
+                if (cb.p) acc1(t.a, [&](Tensor& dst, cplx b) { asym_axpby(D, asym_mode(t), t.c, cb, b, dst); });
+                if (dcb.p) accR(t.a, [&](Tensor& dst, cplx b) { asym_axpby(D, asym_mode(t), t.c, dcb, b, dst); });
             } else if (t.kind == TK_PERM) {
                 if (!active[t.a]) continue;
                 std::string lx = perm_in(t.spec), ly = rhs(t.spec);
@@ -475,8 +489,7 @@ void build_ccsd(CCProg& cp, const Ham& H, LadderCtx* lad) {
     int Fmj = P.op({PERM(1, "mj->mj", Fmi), EIN(0.5, "je,me->mj", t1, Fme)});
     int Xa = P.op({EIN(1, "ijae,be->ijab", t2, Fbe)});
     int Xb = P.op({EIN(1, "imab,mj->ijab", t2, Fmj)});
-    std::vector<Term> r2 = {PERM(1, "ijab->ijab", Xa), PERM(-1, "ijab->ijba", Xa), PERM(-1, "ijab->ijab", Xb),
-                            PERM(1, "ijab->jiab", Xb)};
+    std::vector<Term> r2 = {ASYM(1, Xa, 2), ASYM(-1, Xb, 1)};
     if (w) {
         r2.push_back(PERM(1, "abij->ijab", vvoo));
         int Xw = P.op({EIN(1, "je,mnie->mnij", t1, ooov)});
@@ -487,24 +500,18 @@ void build_ccsd(CCProg& cp, const Ham& H, LadderCtx* lad) {
         r2.push_back(LADDER(1, tau));
         int Q = P.op({EIN(1, "amef,ijef->amij", vovv, tau)});
         int S = P.op({EIN(1, "amij,mb->ijab", Q, t1)});
-        r2.push_back(PERM(-0.5, "ijab->ijab", S));
-        r2.push_back(PERM(0.5, "ijab->ijba", S));
+        r2.push_back(ASYM(-0.5, S, 2));
         int Zt = P.op({PERM(0.5, "jnfb->jnfb", t2), EIN(1, "jf,nb->jnfb", t1, t1)});
         int Wmbej = P.op({PERM(1, "mbej->mbej", ovvo), EIN(1, "jf,mbef->mbej", t1, ovvv),
                           EIN(-1, "nb,mnej->mbej", t1, oovo), EIN(-1, "jnfb,mnef->mbej", Zt, oovv)});
         int ring1 = P.op({EIN(1, "imae,mbej->ijab", t2, Wmbej)});
         int tmp = P.op({EIN(1, "ie,mbej->mbij", t1, ovvo)});
         int ring = P.op({PERM(1, "ijab->ijab", ring1), EIN(-1, "ma,mbij->ijab", t1, tmp)});
-        r2.push_back(PERM(1, "ijab->ijab", ring));
-        r2.push_back(PERM(-1, "ijab->jiab", ring));
-        r2.push_back(PERM(-1, "ijab->ijba", ring));
-        r2.push_back(PERM(1, "ijab->jiba", ring));
+        r2.push_back(ASYM(1, ring, 3));
         int t3 = P.op({EIN(1, "ie,abej->ijab", t1, vvvo)});
-        r2.push_back(PERM(1, "ijab->ijab", t3));
-        r2.push_back(PERM(-1, "ijab->jiab", t3));
+        r2.push_back(ASYM(1, t3, 1));
         int t4 = P.op({EIN(1, "ma,mbij->ijab", t1, ovoo)});
-        r2.push_back(PERM(-1, "ijab->ijab", t4));
-        r2.push_back(PERM(1, "ijab->ijba", t4));
+        r2.push_back(ASYM(-1, t4, 2));
     }
     cp.R2 = P.op(r2);
 

@@ -4,7 +4,7 @@
 #pragma once
 #include "lrcc_internal.h"
 
-enum TermKind { TK_EIN = 0, TK_PERM = 1, TK_LADDER = 2 };
+enum TermKind { TK_EIN = 0, TK_PERM = 1, TK_LADDER = 2, TK_ASYM = 3 };
 
 struct Term {
     TermKind kind;
@@ -16,6 +16,10 @@ struct Term {
 inline Term EIN(double c, const char* spec, int a, int b) { return Term{TK_EIN, mkc(c), spec, a, b}; }
 inline Term PERM(double c, const char* spec, int a) { return Term{TK_PERM, mkc(c), spec, a, -1}; }
 inline Term LADDER(double c, int a) { return Term{TK_LADDER, mkc(c), "", a, -1}; }
+// antisymmetriser of an [O][O][V][V] slot: mode 1 P(ij), 2 P(ab), 3 P(ij)P(ab)
+// (the operand index b carries the mode; it is not a slot)
+inline Term ASYM(double c, int a, int mode) { return Term{TK_ASYM, mkc(c), "", a, -1 - mode}; }
+inline int asym_mode(const Term& t) { return -1 - t.b; }
 
 struct Op {
     int out;

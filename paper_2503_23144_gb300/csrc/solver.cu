@@ -224,10 +224,7 @@ Amp amp_copy(Dev& D, const Amp& x) {
 // y = x - P_ij x - P_ab x + P_ij P_ab x on [R][O][O][V][V]
 Tensor antisym4(Dev& D, const Tensor& x) {
     Tensor y = empty(D, x.shape());
-    perm_axpby(D, "Zijab->Zijab", mkc(1.0), x, mkc(0.0), y);
-    perm_axpby(D, "Zijab->Zjiab", mkc(-1.0), x, mkc(1.0), y);
-    perm_axpby(D, "Zijab->Zijba", mkc(-1.0), x, mkc(1.0), y);
-    perm_axpby(D, "Zijab->Zjiba", mkc(1.0), x, mkc(1.0), y);
+    asym_axpby(D, 3, mkc(1.0), x, mkc(0.0), y);
     return y;
 }
 
