@@ -39,6 +39,25 @@ def nominal_flops(O, V, L, R):
     return 8.0 * (R * (po * pv * pv + O ** 3 * V ** 3) + pv * pv * L)
 
 
+def recorded_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
+    when the kernel's source has changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "tc_gemm_traffic_c2.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("#") or "=" not in line:
+            continue
+        kv = dict(x.split("=", 1) for x in line.split())
+        if kv.get("kernel") != kernel:
+            continue
+        src = os.path.join(ROOT, kv["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return float(kv["bytes_per_launch"]) if sha == kv.get("sha256_16") else None
+    return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -303,8 +322,10 @@ def main():
         else:
             peak, unit, bound = 1.25, "TFLOP/s", "alu"              # FP64 nominal (FMA pipes)
             note = "GB300 FP64 nominal 1.25 TFLOP/s"
+        traffic = recorded_traffic(name) if args.workload == "c2" else None
         roof = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "launches": st["count"],
+                "frac": achieved / peak, "traffic": traffic, "launches": st["count"],
+                "algorithmic_bytes_per_launch": st["bytes"] / max(st["count"], 1),
                 "share_of_step": st["ms"] / total, "peak_note": note}
 
     line = {
