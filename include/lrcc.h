@@ -61,10 +61,13 @@ typedef struct {
     int diis_size;         /* Pulay subspace per right-hand side (default 8)      */
     int rhs_chunk;         /* right-hand sides per batched solve (default 12)     */
     lrcc_precision prec;   /* contraction precision of the response solves        */
-    double inner_tol;      /* mixed mode: relative residual drop per inner solve  */
+    double inner_tol;      /* mixed mode: residual reduction asked of the tensor-core
+                              iterations, relative (default 1e-5)                  */
     int plus_omega;        /* FNS++ denominator Dbar + omega (Eq. 46 as printed)
                               instead of Dbar - omega (diagonal of Eq. 29)        */
     int slab_rows;         /* ladder: (a<b) rows per assembled <ab||ef> slab; 0 = auto */
+    int pm_omega;          /* 1: response function of Eq. 36 (solves X(+w) and X(-w),
+                              no Y); 0 (default): Eq. 35 (X(w) and Y(w))            */
 } lrcc_options;
 
 /* Fill *opt with the defaults above. */
@@ -126,6 +129,10 @@ lrcc_status lrcc_fns_truncate(lrcc_ctx* ctx, int by_count, double value, double 
  * (Eq. 29-31) and Y^B from Y (A + omega) = -(eta + F X) (Eq. 32-34); then
  * g_AB = Y^B . xi^A + eta^A . X^B and alpha_AB = -(g_AB + conj g_BA)/2.
  * Right-hand sides (component, omega) are batched rhs_chunk at a time.
+ * With opt.pm_omega = 1 the Eq. 36 form is used instead: X(+w) and X(-w) for
+ * every component (one frequency per batch), and
+ * <<A;B>>_w = 1/2 [G_AB(w) + conj G_AB(-w)],
+ * G_AB(w) = eta^A.X^B(w) + eta^B.X^A(-w) + X^A(-w).F.X^B(w).
  *   omegas [n_w]                 host, real frequencies (Hartree).
  *   comps  [n_c]                 host, component indices into mu (0..ncomp-1).
  *   alpha  [n_w][n_c][n_c] cplx  out, host, Re = polarisability.

@@ -383,6 +383,41 @@ def polarizability(system, comps, omegas, tol=1e-11, ground=None, return_parts=F
     return alpha
 
 
+def polarizability_pm(system, comps, omegas, tol=1e-11, ground=None):
+    """alpha_AB(omega) = -<<A;B>>_omega from Eq. 36: the +-omega form, which
+    solves X(+omega) and X(-omega) instead of Y.  With P(A(-w), B(w)) applied,
+    G_AB(w) = eta^A.X^B(w) + eta^B.X^A(-w) + X^A(-w).F.X^B(w), and
+    C^{+-w} gives <<A;B>>_w = 1/2 [G_AB(w) + conj G_AB(-w)].  F is symmetric, so
+    X^A(w).F.X^B(-w) = (F X^A(w)).X^B(-w).  Returns [n_w, n_c, n_c]."""
+    model = build(system)
+    if ground is None:
+        t, E, _ = solve_ccsd(model)
+        lam, _ = solve_lambda(model, t)
+    else:
+        t, E, lam = ground
+    comps = list(comps)
+    xi, eta = {}, {}
+    for A in comps:
+        mA = dipole_model(system, A)
+        xi[A] = mA.R(t)
+        eta[A] = mA.lagrangian_grad(t, lam)
+    nc = len(comps)
+    out = np.zeros((len(omegas), nc, nc), dtype=np.complex128)
+    dot = lambda u, v: complex(torch.sum(u * v))
+    for wi, w in enumerate(omegas):
+        Xp = {B: solve_x(model, t, xi[B], w, tol)[0] for B in comps}
+        Xm = {B: solve_x(model, t, xi[B], -w, tol)[0] for B in comps}
+        FXp = {B: model.FX(t, lam, Xp[B]) for B in comps}
+        Gp = np.zeros((nc, nc), dtype=np.complex128)
+        Gm = np.zeros((nc, nc), dtype=np.complex128)
+        for a, A in enumerate(comps):
+            for b, B in enumerate(comps):
+                Gp[a, b] = dot(eta[A], Xp[B]) + dot(eta[B], Xm[A]) + dot(Xm[A], FXp[B])
+                Gm[a, b] = dot(eta[A], Xm[B]) + dot(eta[B], Xp[A]) + dot(FXp[A], Xm[B])
+        out[wi] = -0.5 * (Gp + Gm.conj())
+    return out
+
+
 def field_energy(system, comp, F, tol=1e-13):
     """CCSD correlation energy with f -> f + F mu_A (orbital-unrelaxed field)."""
     f = fock_of(system) + F * np.asarray(system["mu"][comp])

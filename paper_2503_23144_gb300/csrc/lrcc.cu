@@ -300,6 +300,22 @@ void response_solve(lrcc_ctx* c, Amp& z, const Amp& b, const std::vector<double>
     }
     const int prec = c->opt.prec;
     std::vector<double> rn;
+    // phase 1: the whole solve on tensor-core products, down to their accuracy floor
+    {
+        std::vector<double> bn;
+        max_abs_amp(D, b, bn);
+        double bmax = *std::max_element(bn.begin(), bn.end());
+        auto resd = [&](const Amp& x) {
+            Amp s = apply(x, prec);
+            nmix++;
+            Amp q = amp_empty(D, R, O, V);
+            combine(D, s, x, shift_dev, &b, q);
+            return q;
+        };
+        solve_loop(c, z, resd, shift, std::max(c->opt.inner_tol * bmax, 0.5 * c->opt.x_tol),
+                   std::min(c->opt.max_iter, 60), nullptr, false);
+    }
+    // phase 2: FP64 residual, tensor-core correction (iterative refinement)
     for (int outer = 0; outer < 30; ++outer) {
         Amp r = res64(z);
         max_abs_amp(D, r, rn);
@@ -318,12 +334,76 @@ void response_solve(lrcc_ctx* c, Amp& z, const Amp& b, const std::vector<double>
             combine(D, s, x, shift_dev, &r, q);
             return q;
         };
-        double tol = std::max(c->opt.inner_tol * m, 0.5 * c->opt.x_tol);
+        // aim the correction at the final tolerance, within the products' accuracy
+        double tol = std::max(0.3 * c->opt.x_tol, c->opt.inner_tol * m);
         solve_loop(c, d, resm, shift, tol, std::min(c->opt.max_iter, 60), nullptr, false);
         amp_axpby(D, mkc(1.0), d, mkc(1.0), z);
     }
     final_res = rn;
     throw LrccError(LRCC_ENOCONV, "iterative refinement did not converge");
+}
+
+// Eq. 36: per frequency, X(+w) and X(-w) for all components in one batch,
+// F X(+w), and the Gram matrices of the unique-amplitude dots.
+void solve_pm_omega(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int n_c,
+                    const std::vector<Amp>& xi, const std::vector<Amp>& eta, double* alpha, double* err_est) {
+    Dev& D = c->D;
+    int O = c->O, V = c->V;
+    Amp etaS = amp_empty(D, n_c, O, V);
+    for (int a = 0; a < n_c; ++a) {
+        Tensor e1 = etaS.t1.index(a), e2 = etaS.t2.index(a);
+        axpby(D, mkc(1.0), eta[comps[a]].t1.index(0), false, mkc(0.0), e1);
+        axpby(D, mkc(1.0), eta[comps[a]].t2.index(0), false, mkc(0.0), e2);
+    }
+    for (int w = 0; w < n_w; ++w) {
+        const int64_t R = 2 * n_c;
+        Amp xiR = amp_empty(D, R, O, V);
+        std::vector<double> sh(R);
+        for (int64_t r = 0; r < R; ++r) {
+            int a = (int)(r % n_c);
+            Tensor a1 = xiR.t1.index(r), a2 = xiR.t2.index(r);
+            axpby(D, mkc(1.0), xi[comps[a]].t1.index(0), false, mkc(0.0), a1);
+            axpby(D, mkc(1.0), xi[comps[a]].t2.index(0), false, mkc(0.0), a2);
+            sh[r] = r < n_c ? -omegas[w] : omegas[w];   // (A - w') X = -xi, w' = +w then -w
+        }
+        std::shared_ptr<DevBuf> hs;
+        double* shd = dev_doubles(D, sh, hs);
+        Amp X = amp_empty(D, R, O, V);
+        std::vector<double> resX;
+        {
+            Timer tm(D);
+            auto apply = [&](const Amp& x, int p) { return sigma(D, *c->cc, x, p); };
+            response_solve(c, X, xiR, sh, shd, apply, resX, c->n_sigma64, c->n_sigma_mixed);
+            c->phase_ms[3] += tm.stop();
+        }
+        Amp Xp = amp_rows(X, 0, n_c), Xm = amp_rows(X, n_c, n_c);
+        Amp FXp;
+        {
+            Timer tm(D);
+            Amp Xpc = amp_copy(D, Xp);
+            FXp = fx_product(c, Xpc);
+            c->phase_ms[4] += tm.stop();
+        }
+        Timer tm(D);
+        Tensor g[6] = {amp_gram(D, etaS, Xp), amp_gram(D, Xm, etaS), amp_gram(D, Xm, FXp),
+                       amp_gram(D, etaS, Xm), amp_gram(D, Xp, etaS), amp_gram(D, FXp, Xm)};
+        std::vector<cplx> h(6 * n_c * n_c);
+        for (int q = 0; q < 6; ++q)
+            CK(cudaMemcpyAsync(h.data() + q * n_c * n_c, g[q].p, sizeof(cplx) * n_c * n_c, cudaMemcpyDeviceToHost, D.st));
+        CK(cudaStreamSynchronize(D.st));
+        c->phase_ms[6] += tm.stop();
+        for (int a = 0; a < n_c; ++a)
+            for (int b = 0; b < n_c; ++b) {
+                auto at = [&](int q) { return h[q * n_c * n_c + a * n_c + b]; };
+                cplx gp = mkc(at(0).x + at(1).x + at(2).x, at(0).y + at(1).y + at(2).y);   // G_AB(+w)
+                cplx gm = mkc(at(3).x + at(4).x + at(5).x, at(3).y + at(4).y + at(5).y);   // G_AB(-w)
+                size_t o = ((size_t)w * n_c + a) * n_c + b;
+                alpha[2 * o] = -0.5 * (gp.x + gm.x);
+                alpha[2 * o + 1] = -0.5 * (gp.y - gm.y);
+            }
+        if (err_est)
+            for (int a = 0; a < n_c; ++a) err_est[(size_t)w * n_c + a] = std::max(resX[a], resX[n_c + a]);
+    }
 }
 
 void do_solve(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int n_c, double* alpha,
@@ -345,6 +425,10 @@ void do_solve(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int 
             eta[k] = vjp_unique(D, *c->ccmu[k], c->Lam, 1.0, LRCC_FP64);
         }
         c->phase_ms[2] += tm.stop();
+    }
+    if (c->opt.pm_omega) {
+        solve_pm_omega(c, omegas, n_w, comps, n_c, xi, eta, alpha, err_est);
+        return;
     }
     // right-hand sides (omega, component), rhs_chunk at a time
     struct Rhs { int w, comp_idx; };
@@ -473,9 +557,10 @@ void lrcc_default_options(lrcc_options* o) {
     o->diis_size = 8;
     o->rhs_chunk = 12;
     o->prec = LRCC_FP64;
-    o->inner_tol = 1e-3;
+    o->inner_tol = 1e-5;
     o->plus_omega = 0;
     o->slab_rows = 0;
+    o->pm_omega = 0;
 }
 
 const char* lrcc_last_error(const lrcc_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }

@@ -210,6 +210,16 @@ Tensor amp_dot_fixed(Dev& D, const Amp& a, const Amp& b1) {
     return out;
 }
 
+// G[p][q] = sum over unique amplitudes of U_p W_q (unconjugated), U [P], W [Q]
+Tensor amp_gram(Dev& D, const Amp& U, const Amp& W) {
+    Tensor G = empty(D, {U.t1.d[0], W.t1.d[0]});
+    ein(D, "Pia,Qia->PQ", mkc(1.0), U.t1, false, W.t1, false, mkc(0.0), G);
+    ein(D, "Pijab,Qijab->PQ", mkc(0.25), U.t2, false, W.t2, false, mkc(1.0), G);
+    return G;
+}
+
+Amp amp_rows(const Amp& a, int64_t r0, int64_t n) { return Amp{a.t1.slice(0, r0, n), a.t2.slice(0, r0, n)}; }
+
 void amp_axpby(Dev& D, cplx a, const Amp& x, cplx b, Amp& y) {
     axpby(D, a, x.t1, false, b, y.t1);
     axpby(D, a, x.t2, false, b, y.t2);

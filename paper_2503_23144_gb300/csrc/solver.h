@@ -20,6 +20,10 @@ void combine(Dev& D, const Amp& s, const Amp& x, const double* coef_dev, const A
 // per-RHS unique-amplitude dot: sum_ia op(a)b + 1/4 sum_ijab op(a)b -> [R]
 Tensor amp_dot(Dev& D, const Amp& a, bool conj_a, const Amp& b);
 Tensor amp_dot_fixed(Dev& D, const Amp& a, const Amp& b1);
+// Gram matrix of unconjugated unique-amplitude dots between the rows of U and W
+Tensor amp_gram(Dev& D, const Amp& U, const Amp& W);
+// rows [r0, r0+n) of a batched amplitude set (a view)
+Amp amp_rows(const Amp& a, int64_t r0, int64_t n);
 // 4-fold antisymmetriser over the (i,j) and (a,b) pairs
 Tensor antisym4(Dev& D, const Tensor& x);
 void max_abs_amp(Dev& D, const Amp& r, std::vector<double>& out);

@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "LRCC_OK", 1: "LRCC_EINVAL", 2: "LRCC_ENOMEM", 3: "LRCC_ENOCO
 class lrcc_options(ctypes.Structure):
     _fields_ = [("r_tol", ctypes.c_double), ("x_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_size", ctypes.c_int), ("rhs_chunk", ctypes.c_int), ("prec", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("plus_omega", ctypes.c_int), ("slab_rows", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("plus_omega", ctypes.c_int), ("slab_rows", ctypes.c_int),
+                ("pm_omega", ctypes.c_int)]
 
 
 class LrccError(RuntimeError):

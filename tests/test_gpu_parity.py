@@ -219,3 +219,22 @@ def test_amplitude_readback(L, small):
     lu = _unique(L, lay, lam[None])[0]
     gE = model.lagrangian_grad(tu, torch.zeros_like(tu))
     assert float((model.vjp(tu, lu) + gE).abs().max()) < 1e-9
+
+
+def test_pm_omega_form_parity_and_two_electron_sos(L):
+    """Eq. 36 option (X(+w), X(-w), no Y) against the oracle, and exact for
+    two electrons."""
+    s = synth.make_system(4, 15, 20, seed=31)
+    oms = [0.0, 0.045]
+    ref = ccsd.polarizability_pm(s, (0, 1, 2), oms, tol=1e-11)
+    ctx = _ctx(L, s, x_tol=1e-10, pm_omega=1)
+    L.lrcc_ccsd_ground(ctx)
+    a, _ = L.lrcc_solve(ctx, oms, [0, 1, 2])
+    assert np.abs(a - ref).max() < 1e-9 * np.abs(ref).max()
+    cfg = synth.CONFIGS["c1b"]
+    s2 = synth.make_system(cfg["O"], cfg["V"], cfg["L"], cfg["seed"])
+    c2 = _ctx(L, s2, r_tol=1e-12, x_tol=1e-11, pm_omega=1, prec=2)
+    L.lrcc_ccsd_ground(c2)
+    a2, _ = L.lrcc_solve(c2, list(cfg["omegas"]), [0, 1, 2])
+    sos, _, _ = fci.sos_polarizability(ccsd.fock_of(s2), s2["B"], s2["mu"], s2["O"], (0, 1, 2), list(cfg["omegas"]))
+    assert np.abs(a2 - sos).max() < 1e-9 * np.abs(sos).max()

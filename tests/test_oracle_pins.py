@@ -103,6 +103,29 @@ def test_two_electron_ccsd_equals_fci_and_sos():
     assert np.abs(a_lr - a_sos).max() < 1e-9 * np.abs(a_sos).max()
 
 
+def test_pm_omega_form_equals_sos_for_two_electrons():
+    """Eq. 36 (X(+w), X(-w), no Y) is exact for 2 electrons as well, and agrees
+    with the Eq. 35 form there."""
+    cfg = synth.CONFIGS["c1b"]
+    s = synth.make_system(cfg["O"], cfg["V"], cfg["L"], cfg["seed"])
+    oms = [0.0, 0.05]
+    a36 = ccsd.polarizability_pm(s, (0, 1, 2), oms)
+    sos, _, _ = fci.sos_polarizability(ccsd.fock_of(s), s["B"], s["mu"], s["O"], (0, 1, 2), oms)
+    assert np.abs(a36 - sos).max() < 1e-9 * np.abs(sos).max()
+
+
+def test_pm_omega_form_close_to_eq35_for_more_electrons():
+    """For more than two electrons the two forms are different approximations;
+    at omega = 0 both equal d^2E/dF^2 (the same number), at omega != 0 they
+    differ only slightly."""
+    s = synth.make_system(3, 7, 10, seed=14)
+    a35 = ccsd.polarizability(s, (0, 2), [0.0, 0.05])
+    a36 = ccsd.polarizability_pm(s, (0, 2), [0.0, 0.05])
+    scale = np.abs(a35).max()
+    assert np.abs(a36[0] - a35[0]).max() < 1e-9 * scale
+    assert np.abs(a36[1] - a35[1]).max() < 1e-2 * scale
+
+
 def test_noninteracting_response_closed_form():
     """Without two-electron terms T = 0 and alpha is the independent-particle
     sum over (i, a): A_ia B_ai/(d - w) + B_ia A_ai/(d + w), d = e_a - e_i.
