@@ -238,9 +238,11 @@ def main():
     x_dev = torch.as_tensor(x_host).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    # the maps lrcc_solve applies: linearised at the converged T (t = None reuses
+    # the primal values the context keeps from lrcc_ccsd_ground)
     def step():
-        a = L.lrcc_residual_dev(ctx, L.LRCC_RES_SIGMA, t_dev, x_dev, prec=prec)
-        b = L.lrcc_residual_dev(ctx, L.LRCC_RES_VJP, t_dev, x_dev, prec=prec)
+        a = L.lrcc_residual_dev(ctx, L.LRCC_RES_SIGMA, None, x_dev, prec=prec)
+        b = L.lrcc_residual_dev(ctx, L.LRCC_RES_VJP, None, x_dev, prec=prec)
         return a, b
 
     for _ in range(max(3, args.warmup)):
@@ -281,11 +283,11 @@ def main():
     e2e_t = []
     for _ in range(2):
         t0 = time.perf_counter()
-        L.lrcc_residual(ctx, L.LRCC_RES_SIGMA, t_host, x_host, prec=prec)
-        L.lrcc_residual(ctx, L.LRCC_RES_VJP, t_host, x_host, prec=prec)
+        L.lrcc_residual(ctx, L.LRCC_RES_SIGMA, None, x_host, prec=prec)
+        L.lrcc_residual(ctx, L.LRCC_RES_VJP, None, x_host, prec=prec)
         e2e_t.append(time.perf_counter() - t0)
     e2e = F_step / min(e2e_t) / 1e12 * world
-    h2d = 2 * (x_host.nbytes + t_host.nbytes)
+    h2d = 2 * x_host.nbytes
     d2h = 2 * x_host.nbytes
     clk = clocks.stop()
 

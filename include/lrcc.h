@@ -164,7 +164,10 @@ typedef enum {
  *            are first projected onto their antisymmetric part (a no-op for
  *            antisymmetric inputs), so every kind is defined for any array.
  *   t        host [O*V + O*O*V*V] complex: the amplitudes T at which
- *            SIGMA / VJP are linearised (ignored for T, ENERGY, XI).
+ *            SIGMA / VJP are linearised, or NULL to linearise at the
+ *            converged ground state of lrcc_ccsd_ground (its primal values are
+ *            reused, as in lrcc_solve; LRCC_ESTATE before the ground state).
+ *            Required for XI; ignored for T and ENERGY.
  *   in       host [R][O*V + O*O*V*V] complex.
  *   R        number of right-hand sides (>= 1).
  *   comp     dipole component for XI.

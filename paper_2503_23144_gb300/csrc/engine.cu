@@ -197,8 +197,9 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
     double flops = 8.0 * double(g.M) * double(g.N) * double(g.K) * double(g.batch);
     // mixed mode: every contraction with real work goes to the tensor cores
     // (the O-sized contractions too: FP64 on this part is 1.25 TFLOP/s)
-    bool tc = prec != LRCC_FP64 && gemm_tc_available() && flops >= 2e8;
+    bool tc = prec != LRCC_FP64 && gemm_tc_available() && flops >= 5e7 && g.K >= 48;
     if (tc) gemm_tc(D, g, prec);
+    else if (prec != LRCC_FP64) gemm_f32c(D, g);
     else gemm_f64(D, g);
     if (!c_ok) perm_axpby(D, lc + "->" + sp.c, alpha, Ct, beta, C);
 }

@@ -20,6 +20,28 @@ __device__ __forceinline__ void cfma(cplx& c, cplx a, cplx b) {
     c.y = fma(a.x, b.y, c.y);
     c.y = fma(a.y, b.x, c.y);
 }
+__device__ __forceinline__ void cfma(float2& c, float2 a, float2 b) {
+    c.x = fmaf(a.x, b.x, c.x);
+    c.x = fmaf(-a.y, b.y, c.x);
+    c.y = fmaf(a.x, b.y, c.y);
+    c.y = fmaf(a.y, b.x, c.y);
+}
+
+// compute-type traits: FP64 (the FP64 path) or FP32 (the inner products of
+// the mixed path, for contractions too small or too thin for the tensor cores)
+template <typename T> struct CT;
+template <> struct CT<double> {
+    typedef cplx C;
+    __device__ static C cvt(cplx v) { return v; }
+    __device__ static cplx back(C v) { return v; }
+    __device__ static C zero() { return make_double2(0.0, 0.0); }
+};
+template <> struct CT<float> {
+    typedef float2 C;
+    __device__ static C cvt(cplx v) { return make_float2((float)v.x, (float)v.y); }
+    __device__ static cplx back(C v) { return make_double2((double)v.x, (double)v.y); }
+    __device__ static C zero() { return make_float2(0.f, 0.f); }
+};
 
 struct GemmK {
     int64_t M, N, K;
@@ -37,9 +59,11 @@ struct GemmK {
     int a_kfast, b_nfast;
 };
 
+template <typename T>
 __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
-    __shared__ cplx As[2][BK][BM];
-    __shared__ cplx Bs[2][BK][BN];
+    typedef typename CT<T>::C cT;
+    __shared__ cT As[2][BK][BM];
+    __shared__ cT Bs[2][BK][BN];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int64_t tiles_n = (g.N + BN - 1) / BN;
@@ -51,13 +75,13 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
     const cplx* A = g.A + b * g.sAb;
     const cplx* B = g.B + b * g.sBb;
 
-    cplx acc[4][4];
+    cT acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+        for (int j = 0; j < 4; ++j) acc[i][j] = CT<T>::zero();
 
-    cplx ra[2], rb[2];
+    cT ra[2], rb[2];
     auto load = [&](int64_t k0) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -68,7 +92,7 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
             cplx v = make_double2(0.0, 0.0);
             if (m < g.M && k < kend) v = A[m * g.sAm + k * g.sAk];
             if (g.cA) v.y = -v.y;
-            ra[r] = v;
+            ra[r] = CT<T>::cvt(v);
             int nn;
             if (g.b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
             int64_t n = n0 + nn;
@@ -76,7 +100,7 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
             cplx w = make_double2(0.0, 0.0);
             if (n < g.N && k < kend) w = B[k * g.sBk + n * g.sBn];
             if (g.cB) w.y = -w.y;
-            rb[r] = w;
+            rb[r] = CT<T>::cvt(w);
         }
     };
     auto store = [&](int buf) {
@@ -102,7 +126,7 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
         if (more) load(k0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            cplx a[4], bb[4];
+            cT a[4], bb[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
@@ -126,7 +150,7 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
         for (int j = 0; j < 4; ++j) {
             int64_t n = n0 + tx + 16 * j;
             if (n >= g.N) continue;
-            cplx v = acc[i][j];
+            cplx v = CT<T>::back(acc[i][j]);
             cplx r = make_double2(g.alpha.x * v.x - g.alpha.y * v.y, g.alpha.x * v.y + g.alpha.y * v.x);
             cplx* c = C + m * g.sCm + n * g.sCn;
             if (g.atomic) {
@@ -150,18 +174,19 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
 // would waste most of the FMA work.
 constexpr int SK_KC = 32, SK_TH = 128;
 
-template <int NMAX>
+template <int NMAX, typename T>
 __global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
-    __shared__ cplx Bs[SK_KC][NMAX];
+    typedef typename CT<T>::C cT;
+    __shared__ cT Bs[SK_KC][NMAX];
     const int64_t m = blockIdx.x * (int64_t)SK_TH + threadIdx.x;
     const int64_t b = blockIdx.y;
     const cplx* A = g.A + b * g.sAb;
     const cplx* B = g.B + b * g.sBb;
     const int N = (int)g.N;
     const int64_t kbeg = blockIdx.z * g.kper, kend = min(g.K, kbeg + g.kper);
-    cplx acc[NMAX];
+    cT acc[NMAX];
 #pragma unroll
-    for (int n = 0; n < NMAX; ++n) acc[n] = make_double2(0.0, 0.0);
+    for (int n = 0; n < NMAX; ++n) acc[n] = CT<T>::zero();
     for (int64_t k0 = kbeg; k0 < kend; k0 += SK_KC) {
         int kc = (int)min((int64_t)SK_KC, kend - k0);
         for (int e = threadIdx.x; e < SK_KC * NMAX; e += SK_TH) {
@@ -170,13 +195,14 @@ __global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
             cplx w = make_double2(0.0, 0.0);
             if (kk < kc && nn < N) w = B[(k0 + kk) * g.sBk + nn * g.sBn];
             if (g.cB) w.y = -w.y;
-            Bs[kk][nn] = w;
+            Bs[kk][nn] = CT<T>::cvt(w);
         }
         __syncthreads();
         if (m < g.M) {
             for (int kk = 0; kk < kc; ++kk) {
-                cplx a = A[m * g.sAm + (k0 + kk) * g.sAk];
-                if (g.cA) a.y = -a.y;
+                cplx a0 = A[m * g.sAm + (k0 + kk) * g.sAk];
+                if (g.cA) a0.y = -a0.y;
+                cT a = CT<T>::cvt(a0);
 #pragma unroll
                 for (int n = 0; n < NMAX; ++n) cfma(acc[n], a, Bs[kk][n]);
             }
@@ -188,7 +214,7 @@ __global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
 #pragma unroll
     for (int n = 0; n < NMAX; ++n) {
         if (n >= N) break;
-        cplx v = acc[n];
+        cplx v = CT<T>::back(acc[n]);
         cplx r = make_double2(g.alpha.x * v.x - g.alpha.y * v.y, g.alpha.x * v.y + g.alpha.y * v.x);
         cplx* c = C + m * g.sCm + n * g.sCn;
         if (g.atomic) {
@@ -276,7 +302,15 @@ void gemm_prescale(Dev& D, const GemmArgs& g) {
     LAUNCH_CHECK(D);
 }
 
-void gemm_f64(Dev& D, const GemmArgs& g) {
+template <typename T>
+static void gemm_simt(Dev& D, const GemmArgs& g);
+
+void gemm_f64(Dev& D, const GemmArgs& g) { gemm_simt<double>(D, g); }
+void gemm_f32c(Dev& D, const GemmArgs& g) { gemm_simt<float>(D, g); }
+
+template <typename T>
+static void gemm_simt(Dev& D, const GemmArgs& g) {
+    const char* kname = sizeof(T) == 8 ? "gemm_f64" : "gemm_f32";
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
     if (g.K <= 0) {
         prescale(D, g);
@@ -294,7 +328,7 @@ void gemm_f64(Dev& D, const GemmArgs& g) {
         return;
     }
     // skinny shapes: one of M, N at most 32 (swap roles so that N is the small one)
-    if (std::min(g.M, g.N) <= 32 && (std::max(g.M, g.N) >= 256 || g.K >= 4096)) {
+    if (std::min(g.M, g.N) <= 32) {
         GemmK k{};
         bool swap = g.M < g.N;
         k.M = swap ? g.N : g.M;
@@ -312,27 +346,28 @@ void gemm_f64(Dev& D, const GemmArgs& g) {
         k.alpha = g.alpha;
         k.beta = g.beta;
         k.b_nfast = (k.sBn == 1) || (k.sBk != 1 && std::llabs(k.sBn) < std::llabs(k.sBk));
-        // split K until there are about 4 CTAs per SM
+        // split K until there are about 4 CTAs per SM: FP64 on this part is
+        // ~8 GFLOP/s per SM, so work left on a few SMs dominates everything
         int64_t blocks = ((k.M + SK_TH - 1) / SK_TH) * g.batch;
         int64_t sp = std::max<int64_t>(1, std::min<int64_t>((4 * (int64_t)D.sm_count + blocks - 1) / blocks,
-                                                            (g.K + 4 * SK_KC - 1) / (4 * SK_KC)));
+                                                            (g.K + 7) / 8));
         sp = std::min<int64_t>(sp, 1024);
         k.kper = (g.K + sp - 1) / sp;
-        k.kper = (k.kper + SK_KC - 1) / SK_KC * SK_KC;
+        k.kper = (k.kper + 7) / 8 * 8;
         sp = (g.K + k.kper - 1) / k.kper;
         k.atomic = sp > 1;
         if (k.atomic) prescale(D, g);
         dim3 grid((unsigned)((k.M + SK_TH - 1) / SK_TH), (unsigned)g.batch, (unsigned)sp);
-        KTimer kt(D, "gemm_f64", 8.0 * g.M * g.N * g.K * g.batch, 16.0 * (g.M * g.K + g.K * g.N + g.M * g.N) * g.batch,
+        KTimer kt(D, kname, 8.0 * g.M * g.N * g.K * g.batch, 16.0 * (g.M * g.K + g.K * g.N + g.M * g.N) * g.batch,
                   g.M, g.N, g.K, g.batch);
-        if (k.N <= 1) k_gemm_skinny<1><<<grid, SK_TH, 0, D.st>>>(k);
-        else if (k.N <= 2) k_gemm_skinny<2><<<grid, SK_TH, 0, D.st>>>(k);
-        else if (k.N <= 4) k_gemm_skinny<4><<<grid, SK_TH, 0, D.st>>>(k);
-        else if (k.N <= 8) k_gemm_skinny<8><<<grid, SK_TH, 0, D.st>>>(k);
-        else if (k.N <= 12) k_gemm_skinny<12><<<grid, SK_TH, 0, D.st>>>(k);
-        else if (k.N <= 16) k_gemm_skinny<16><<<grid, SK_TH, 0, D.st>>>(k);
-        else if (k.N <= 24) k_gemm_skinny<24><<<grid, SK_TH, 0, D.st>>>(k);
-        else k_gemm_skinny<32><<<grid, SK_TH, 0, D.st>>>(k);
+        if (k.N <= 1) k_gemm_skinny<1, T><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 2) k_gemm_skinny<2, T><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 4) k_gemm_skinny<4, T><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 8) k_gemm_skinny<8, T><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 12) k_gemm_skinny<12, T><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 16) k_gemm_skinny<16, T><<<grid, SK_TH, 0, D.st>>>(k);
+        else if (k.N <= 24) k_gemm_skinny<24, T><<<grid, SK_TH, 0, D.st>>>(k);
+        else k_gemm_skinny<32, T><<<grid, SK_TH, 0, D.st>>>(k);
         LAUNCH_CHECK(D);
         return;
     }
@@ -341,9 +376,9 @@ void gemm_f64(Dev& D, const GemmArgs& g) {
     int64_t ctas = tiles * g.batch;
     int64_t splits = 1;
     int64_t target = 2 * (int64_t)D.sm_count;
-    if (ctas < target && g.K >= 4 * BK * 8) {
-        splits = std::min<int64_t>((target + ctas - 1) / ctas, g.K / (BK * 16));
-        splits = std::max<int64_t>(1, std::min<int64_t>(splits, 64));
+    if (ctas < target && g.K >= 2 * BK) {
+        splits = std::min<int64_t>((target + ctas - 1) / ctas, g.K / BK);
+        splits = std::max<int64_t>(1, std::min<int64_t>(splits, 512));
     }
     GemmK k;
     k.M = g.M; k.N = g.N; k.K = g.K;
@@ -359,8 +394,8 @@ void gemm_f64(Dev& D, const GemmArgs& g) {
     k.b_nfast = (g.sBn == 1) || (g.sBk != 1 && std::llabs(g.sBn) < std::llabs(g.sBk));
     if (k.atomic) prescale(D, g);
     dim3 grid((unsigned)tiles, (unsigned)g.batch, (unsigned)splits);
-    KTimer kt(D, "gemm_f64", 8.0 * g.M * g.N * g.K * g.batch, 16.0 * (g.M * g.K + g.K * g.N + g.M * g.N) * g.batch,
+    KTimer kt(D, kname, 8.0 * g.M * g.N * g.K * g.batch, 16.0 * (g.M * g.K + g.K * g.N + g.M * g.N) * g.batch,
               g.M, g.N, g.K, g.batch);
-    k_gemm<<<grid, TH, 0, D.st>>>(k);
+    k_gemm<T><<<grid, TH, 0, D.st>>>(k);
     LAUNCH_CHECK(D);
 }

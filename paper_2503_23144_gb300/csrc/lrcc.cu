@@ -713,8 +713,24 @@ static lrcc_status residual_impl(lrcc_ctx* c, int kind, const double* t, const d
     Amp X = to_amp(inb, R);
     Amp res;
     std::vector<cplx> energies;
-    if (kind == LRCC_RES_SIGMA || kind == LRCC_RES_VJP || kind == LRCC_RES_VJP_FULL || kind == LRCC_RES_XI) {
-        REQUIRE(t, "t is required for SIGMA, VJP and XI");
+    if ((kind == LRCC_RES_SIGMA || kind == LRCC_RES_VJP || kind == LRCC_RES_VJP_FULL) && !t) {
+        // linearised at the converged ground state: the primal values cached in
+        // the solver's program are reused (exactly the maps lrcc_solve applies)
+        if (!c->ground) throw LrccError(LRCC_ESTATE, "t == NULL needs lrcc_ccsd_ground first");
+        if (kind == LRCC_RES_SIGMA) {
+            res = sigma(D, *c->cc, X, prec);
+        } else if (kind == LRCC_RES_VJP) {
+            res = vjp_unique(D, *c->cc, X, 0.0, prec);
+        } else {
+            Amp Xs = amp_copy(D, X);
+            axpby(D, mkc(4.0), X.t2, false, mkc(0.0), Xs.t2);
+            res = vjp_unique(D, *c->cc, Xs, 0.0, prec);
+            Tensor q = empty(D, res.t2.shape());
+            axpby(D, mkc(0.25), res.t2, false, mkc(0.0), q);
+            res.t2 = q;
+        }
+    } else if (kind == LRCC_RES_SIGMA || kind == LRCC_RES_VJP || kind == LRCC_RES_VJP_FULL || kind == LRCC_RES_XI) {
+        REQUIRE(t, "t is required for XI");
         Tensor tb = device ? wrap((cplx*)t, {1, nt}) : dev_copy_c(D, t, {1, nt});
         Amp T = to_amp(tb, 1);
         if (kind == LRCC_RES_XI) {

@@ -191,6 +191,9 @@ struct GemmArgs {
     cplx alpha, beta;
 };
 void gemm_f64(Dev& D, const GemmArgs& g);
+// same GEMM with FP32 arithmetic (FP64 in and out): inner products of the
+// mixed path that are too thin or too short in K for the tensor cores
+void gemm_f32c(Dev& D, const GemmArgs& g);
 // C *= beta on the GEMM's output view (before split-K accumulation)
 void gemm_prescale(Dev& D, const GemmArgs& g);
 

@@ -238,3 +238,18 @@ def test_pm_omega_form_parity_and_two_electron_sos(L):
     a2, _ = L.lrcc_solve(c2, list(cfg["omegas"]), [0, 1, 2])
     sos, _, _ = fci.sos_polarizability(ccsd.fock_of(s2), s2["B"], s2["mu"], s2["O"], (0, 1, 2), list(cfg["omegas"]))
     assert np.abs(a2 - sos).max() < 1e-9 * np.abs(sos).max()
+
+
+def test_residual_hook_at_converged_ground_state(L, small):
+    """t = NULL linearises at the converged T (cached primal): same maps as
+    passing that T explicitly."""
+    s, model, ctx = small
+    lay = model.lay
+    L.lrcc_ccsd_ground(ctx)
+    t = L.lrcc_get_amplitudes(ctx, 0)
+    xs = _rand(lay, 2, 5, 0.3)
+    xf = L.pack_amplitudes(*_flat(lay, xs))
+    for kind in (L.LRCC_RES_SIGMA, L.LRCC_RES_VJP):
+        a = L.lrcc_residual(ctx, kind, None, xf)
+        b = L.lrcc_residual(ctx, kind, t, xf)
+        assert np.abs(a - b).max() < 1e-13 * np.abs(b).max()
