@@ -124,6 +124,16 @@ lrcc_status lrcc_fns_truncate(lrcc_ctx* ctx, int by_count, double value, double 
                               int* v_kept, double* occ_out);
 
 /*
+ * lrcc_mp2_correction -- MP2 energies of the last lrcc_fns_truncate (Eq. 51):
+ * e_full: 1/4 sum <ij||ab> t_ij^ab with MP2 doubles in the full virtual space,
+ * e_trunc: the same in the truncated semicanonical space,
+ * delta = e_full - e_trunc, the correction added to the truncated CCSD
+ * correlation energy (Eq. 52).  Complex pairs (Re, Im); any pointer may be
+ * NULL.  LRCC_ESTATE if no truncation was made on this context.
+ */
+lrcc_status lrcc_mp2_correction(const lrcc_ctx* ctx, double e_full[2], double e_trunc[2], double delta[2]);
+
+/*
  * lrcc_solve -- polarisabilities alpha_AB(omega) = -<<A;B>>_omega (Eq. 35):
  * for every omega and every component B in comps, X^B from (A - omega) X = -xi
  * (Eq. 29-31) and Y^B from Y (A + omega) = -(eta + F X) (Eq. 32-34); then

@@ -148,11 +148,14 @@ void fns_truncate_impl(lrcc_ctx* c, int by_count, double value, double omega, in
         DevDoubles z0 = dev_doubles(D, zero);
         precond(D, nullptr, r, t, deo.p, dev.p, z0.p);
     }
-    // 2. Hbar diagonals
+    // 2. Hbar diagonals (and the full-space MP2 energy 1/4 sum <ij||ab> t_ij^ab, Eq. 51)
     DevDoubles Hii = dev_doubles(D, eo), Haa = dev_doubles(D, ev);
+    cplx e_full = mkc(0.0);
     {
         Tensor oovv = anti_block(D, B, 0, O, 0, O, O, V, O, V);
         Tensor t2 = t.t2.index(0);
+        Tensor ef = ein_new(D, "ijab,ijab->", mkc(0.25), oovv, false, t2, false);
+        CK(cudaMemcpyAsync(&e_full, ef.p, sizeof(cplx), cudaMemcpyDeviceToHost, D.st));
         Tensor si = ein_new(D, "inef,inef->i", mkc(1.0), t2, false, oovv, false);
         Tensor sa = ein_new(D, "mnfa,mnfa->a", mkc(1.0), t2, false, oovv, false);
         k_real_axpy<<<grid_n(D, O), 256, 0, D.st>>>(O, deo.p, 0.5, si.p, Hii.p);
@@ -236,7 +239,27 @@ void fns_truncate_impl(lrcc_ctx* c, int by_count, double value, double omega, in
     };
     Tensor Bn = rotate(B);
     Tensor mun = rotate(c->mu);
+    // MP2 energy in the truncated semicanonical basis (Eq. 51)
+    cplx e_trunc = mkc(0.0);
+    {
+        std::vector<double> etv(et.begin(), et.end());
+        DevDoubles det = dev_doubles(D, etv);
+        Tensor vvoo = anti_block(D, Bn, O, Vk, O, Vk, 0, O, 0, O);
+        Tensor oovv = anti_block(D, Bn, 0, O, 0, O, O, Vk, O, Vk);
+        Amp r = amp_zeros(D, 1, O, Vk), tt = amp_zeros(D, 1, O, Vk);
+        Tensor r2 = r.t2.index(0);
+        perm_axpby(D, "abij->ijab", mkc(1.0), vvoo, mkc(0.0), r2);
+        std::vector<double> zero(1, 0.0);
+        DevDoubles z0 = dev_doubles(D, zero);
+        precond(D, nullptr, r, tt, deo.p, det.p, z0.p);
+        Tensor tt2 = tt.t2.index(0);
+        Tensor e = ein_new(D, "ijab,ijab->", mkc(0.25), oovv, false, tt2, false);
+        CK(cudaMemcpyAsync(&e_trunc, e.p, sizeof(cplx), cudaMemcpyDeviceToHost, D.st));
+    }
     CK(cudaStreamSynchronize(D.st));
+    c->e_mp2_full = e_full;
+    c->e_mp2_trunc = e_trunc;
+    c->truncated = true;
     // 8. replace the virtual space
     c->B = Bn;
     c->mu = mun;
@@ -273,4 +296,16 @@ extern "C" lrcc_status lrcc_fns_truncate(lrcc_ctx* c, int by_count, double value
         c->err = e.what();
         return LRCC_ECUDA;
     }
+}
+
+extern "C" lrcc_status lrcc_mp2_correction(const lrcc_ctx* c, double e_full[2], double e_trunc[2], double delta[2]) {
+    if (!c) return LRCC_EINVAL;
+    if (!c->truncated) return LRCC_ESTATE;
+    if (e_full) { e_full[0] = c->e_mp2_full.x; e_full[1] = c->e_mp2_full.y; }
+    if (e_trunc) { e_trunc[0] = c->e_mp2_trunc.x; e_trunc[1] = c->e_mp2_trunc.y; }
+    if (delta) {
+        delta[0] = c->e_mp2_full.x - c->e_mp2_trunc.x;
+        delta[1] = c->e_mp2_full.y - c->e_mp2_trunc.y;
+    }
+    return LRCC_OK;
 }

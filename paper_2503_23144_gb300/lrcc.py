@@ -62,6 +62,7 @@ SIGNATURES = [
     ("lrcc_profile", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lrcc_profile_dump", ctypes.c_int, [_vp, ctypes.c_char_p]),
     ("lrcc_get_amplitudes", ctypes.c_int, [_vp, ctypes.c_int, _dp]),
+    ("lrcc_mp2_correction", ctypes.c_int, [_vp, _dp, _dp, _dp]),
     ("lrcc_ladder_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                            ctypes.c_int, _vp]),
     ("lrcc_solve_counts", ctypes.c_int, [_vp, _ip, _ip]),
@@ -160,6 +161,13 @@ def lrcc_fns_truncate(ctx: Context, by_count: bool, value: float, omega: float =
                                           _cd(occ)))
     ctx.V = vk.value
     return vk.value, occ
+
+
+def lrcc_mp2_correction(ctx: Context):
+    """(E_MP2 full, E_MP2 truncated, Delta = full - truncated), complex (Eq. 51)."""
+    a, b, d = np.zeros(2), np.zeros(2), np.zeros(2)
+    ctx.check(library().lrcc_mp2_correction(ctx.h, _cd(a), _cd(b), _cd(d)))
+    return complex(*a), complex(*b), complex(*d)
 
 
 def pack_amplitudes(t1, t2) -> np.ndarray:

@@ -30,8 +30,17 @@ def test_fnspp_truncated_alpha_and_occupations(L):
     new, occ_ref, _ = fns.truncate(s, True, keep)
     a_ref = ccsd.polarizability(new, (0, 1, 2), oms, tol=1e-11)
     ctx = _ctx(L, s, x_tol=1e-10)
+    with pytest.raises(L.LrccError):
+        L.lrcc_mp2_correction(ctx)
     vk, occ = L.lrcc_fns_truncate(ctx, True, keep)
     assert vk == keep
+    # MP2 correction of Eq. 51 against the oracle's MP2 energies in both bases
+    ef, et, de = L.lrcc_mp2_correction(ctx)
+    ef_ref = fns.mp2_energy(s["eps"], s["B"], 4)
+    et_ref = fns.mp2_energy(new["eps"], new["B"], 4)
+    assert abs(ef - ef_ref) < 1e-12 * abs(ef_ref)
+    assert abs(et - et_ref) < 1e-12 * abs(ef_ref)
+    assert abs(de - (ef_ref - et_ref)) < 1e-12 * abs(ef_ref)
     assert np.abs(occ - occ_ref).max() < 1e-12 * occ_ref.max()
     L.lrcc_ccsd_ground(ctx)
     a, _ = L.lrcc_solve(ctx, oms, [0, 1, 2])
@@ -60,3 +69,19 @@ def test_fnspp_untruncated_reproduces_full_alpha(L):
     L.lrcc_ccsd_ground(c_tr)
     a_tr, _ = L.lrcc_solve(c_tr, oms, [0, 1, 2])
     assert np.abs(a_tr - a_full).max() < 1e-10 * np.abs(a_full).max()
+
+
+def test_fnspp_config3_recipe_reduced_size(L):
+    """The FNS++ workload's recipe (O=16, seed 2, static, 3 components) at a
+    virtual space the oracle handles: V=100 -> 30, mixed-precision solve."""
+    s = synth.make_system(16, 100, 400, seed=2)
+    keep = 30
+    new, occ_ref, _ = fns.truncate(s, True, keep)
+    a_ref = ccsd.polarizability(new, (0, 1, 2), [0.0], tol=1e-10)
+    ctx = _ctx(L, s, prec=2)
+    vk, occ = L.lrcc_fns_truncate(ctx, True, keep)
+    assert vk == keep
+    assert np.abs(occ - occ_ref).max() < 1e-11 * occ_ref.max()
+    L.lrcc_ccsd_ground(ctx)
+    a, _ = L.lrcc_solve(ctx, [0.0], [0, 1, 2])
+    assert np.abs(a - a_ref).max() < 1e-6 * np.abs(a_ref).max()
