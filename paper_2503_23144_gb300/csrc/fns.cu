@@ -27,24 +27,24 @@ int grid_n(Dev& D, int64_t n) {
 
 // out[p] = base[p] + scale * Re(in[p])
 __global__ void k_real_axpy(int64_t n, const double* base, double scale, const cplx* in, double* out) {
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p < n) out[p] = base[p] + scale * in[p].x;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        out[p] = base[p] + scale * in[p].x;
 }
 
 // dst[p][j] = src[p][idx[j]]
 __global__ void k_gather_cols(int64_t n, int64_t m, const cplx* src, const int* idx, cplx* dst) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n * m) return;
-    int64_t p = e / m, j = e % m;
-    dst[e] = src[p * n + idx[j]];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * m; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = e / m, j = e % m;
+        dst[e] = src[p * n + idx[j]];
+    }
 }
 
 // diag(v) as a complex matrix
 __global__ void k_diag(int64_t n, const double* v, cplx* out) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n * n) return;
-    int64_t p = e / n, q = e % n;
-    out[e] = make_double2(p == q ? v[p] : 0.0, 0.0);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = e / n, q = e % n;
+        out[e] = make_double2(p == q ? v[p] : 0.0, 0.0);
+    }
 }
 
 struct DevDoubles {

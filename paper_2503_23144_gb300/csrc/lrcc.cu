@@ -4,6 +4,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
+#include <cstdlib>
+#include <limits>
 #include <string>
 
 #include "ctx.h"
@@ -170,6 +173,9 @@ double* dev_doubles(Dev& D, const std::vector<double>& v, std::shared_ptr<DevBuf
 
 // generic preconditioned DIIS loop on R right-hand sides:
 //   r = resid(x);  x <- extrapolate(x - r/(D + shift))
+// kernels with bounded waits raise a device error word instead of hanging
+void check_device_error(Dev& D);
+
 template <class F>
 int solve_loop(lrcc_ctx* c, Amp& x, F&& resid, const std::vector<double>& shift, double tol, int max_iter,
                std::vector<double>* final_res = nullptr, bool throw_on_max = true) {
@@ -179,14 +185,40 @@ int solve_loop(lrcc_ctx* c, Amp& x, F&& resid, const std::vector<double>& shift,
     double* sh = dev_doubles(D, shift, hold);
     Diis diis(D, (int)R, c->opt.diis_size);
     std::vector<double> rn;
+    // non-throwing mode (tensor-core phases): stop at the products' noise floor
+    // -- no improvement in 8 iterations or growth past 10x the best residual --
+    // and return the best iterate seen
+    double best = std::numeric_limits<double>::infinity();
+    int since_best = 0;
+    Amp best_x;
     for (int it = 0; it < max_iter; ++it) {
         Amp r = resid(x);
         max_abs_amp(D, r, rn);
         double m = *std::max_element(rn.begin(), rn.end());
-        if (!std::isfinite(m) || m > 1e250) throw LrccError(LRCC_ENOCONV, "residual is not finite");
+        if (getenv("LRCC_VERBOSE"))
+            fprintf(stderr, "  iter %3d  R=%lld  max|r| = %.3e%s\n", it, (long long)R, m, throw_on_max ? "" : "  (tc)");
+        if (!std::isfinite(m) || m > 1e250) {
+            check_device_error(D);
+            if (!throw_on_max && best_x.t1.p) {
+                x = best_x;
+                return it;
+            }
+            throw LrccError(LRCC_ENOCONV, "residual is not finite");
+        }
         if (m < tol) {
             if (final_res) *final_res = rn;
             return it;
+        }
+        if (!throw_on_max) {
+            if (m < best) {
+                best = m;
+                since_best = 0;
+                best_x = amp_copy(D, x);
+            } else if (++since_best >= 8 || m > 10.0 * best) {
+                x = best_x;
+                if (final_res) *final_res = rn;
+                return it;
+            }
         }
         Amp xn = amp_empty(D, R, c->O, c->V);
         precond(D, &x, r, xn, c->eo, c->ev, sh);
@@ -196,7 +228,10 @@ int solve_loop(lrcc_ctx* c, Amp& x, F&& resid, const std::vector<double>& shift,
         x = diis.push_extrapolate(D, xn, e);
     }
     if (final_res) *final_res = rn;
-    if (!throw_on_max) return max_iter;
+    if (!throw_on_max) {
+        if (best_x.t1.p) x = best_x;
+        return max_iter;
+    }
     throw LrccError(LRCC_ENOCONV, "no convergence after " + std::to_string(max_iter) + " iterations (max|r| = " +
                                       std::to_string(rn.empty() ? -1.0 : *std::max_element(rn.begin(), rn.end())) + ")");
 }

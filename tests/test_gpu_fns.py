@@ -85,3 +85,19 @@ def test_fnspp_config3_recipe_reduced_size(L):
     L.lrcc_ccsd_ground(ctx)
     a, _ = L.lrcc_solve(ctx, [0.0], [0, 1, 2])
     assert np.abs(a - a_ref).max() < 1e-6 * np.abs(a_ref).max()
+
+
+def test_fnspp_large_virtual_space_v800(L):
+    """V = 800 (V^2 beyond one wave of the element-wise kernels' capped grids):
+    occupations and the truncated alpha against the oracle."""
+    s = synth.make_system(3, 800, 6, seed=8)
+    keep = 16
+    new, occ_ref, _ = fns.truncate(s, True, keep)
+    a_ref = ccsd.polarizability(new, (0, 2), [0.0], tol=1e-11)
+    ctx = _ctx(L, s, x_tol=1e-10)
+    vk, occ = L.lrcc_fns_truncate(ctx, True, keep)
+    assert vk == keep
+    assert np.abs(occ - occ_ref).max() < 1e-11 * occ_ref.max()
+    L.lrcc_ccsd_ground(ctx)
+    a, _ = L.lrcc_solve(ctx, [0.0], [0, 2])
+    assert np.abs(a - a_ref).max() < 1e-9 * np.abs(a_ref).max()
