@@ -65,7 +65,9 @@ typedef struct {
                               iterations, relative (default 1e-5)                  */
     int plus_omega;        /* FNS++ denominator Dbar + omega (Eq. 46 as printed)
                               instead of Dbar - omega (diagonal of Eq. 29)        */
-    int slab_rows;         /* ladder: (a<b) rows per assembled <ab||ef> slab; 0 = auto */
+    int slab_rows;         /* ladder: > 0 never caches <ab||ef>; it is assembled per call in
+                              slabs of at most this many (a<b) rows.  0 = automatic: cached
+                              when it fits in a third of free memory, else slabs sized to it */
     int pm_omega;          /* 1: response function of Eq. 36 (solves X(+w) and X(-w),
                               no Y); 0 (default): Eq. 35 (X(w) and Y(w))            */
 } lrcc_options;
@@ -208,6 +210,27 @@ lrcc_status lrcc_residual_dev(lrcc_ctx* ctx, int kind, const double* t_dev, cons
  */
 lrcc_status lrcc_ladder_dev(lrcc_ctx* ctx, const double* x_dev, double* z_dev, int R,
                             int transpose, int prec, void* stream);
+
+/*
+ * lrcc_ladder_packed_dev -- the particle-particle ladder on packed (unique-pair)
+ * amplitudes, reading only the virtual-virtual block of B (the other integral
+ * blocks are not built, so it runs at virtual spaces where they would not fit):
+ *   Zt[n][ab] = sum_{e<f} <ab||ef> Xt[n][ef]   (= 1/2 sum_ef <ab||ef> X_ij^ef,
+ *   the ladder term of Eq. 30 for X antisymmetric in (e,f)),
+ *   <ab||ef> = <ab|ef> - <ab|fe>,  <ab|ef> = sum_L B^L_ae B^L_bf.
+ *   xt_dev  [ncol][P_V] complex, device: one row per column n (e.g. n = r P_O + ij
+ *           for R right-hand sides and the pairs i<j); pairs e<f in row-major
+ *           order of the strict upper triangle.  Not modified.
+ *   zt_dev  [ncol][P_V] complex, device, overwritten; must not overlap xt_dev.
+ *   transpose  1: <ef||ab> = conj <ab||ef>, the holomorphic transpose.
+ *   prec    LRCC_FP64, LRCC_MIXED_TF32 or LRCC_MIXED_BF16X3.
+ * The context caches <ab||ef> (FP64 or embedded) when it fits in a third of the
+ * free device memory; otherwise every call assembles it in slabs from B (an
+ * embedded copy of B_vv is then kept for the mixed precisions).  LRCC_ENOMEM
+ * if the slab buffers do not fit.  Stream-ordered on `stream`; no sync.
+ */
+lrcc_status lrcc_ladder_packed_dev(lrcc_ctx* ctx, const double* xt_dev, double* zt_dev, int64_t ncol,
+                                   int transpose, int prec, void* stream);
 
 /*
  * lrcc_get_amplitudes -- copy the converged ground-state amplitudes to the host.

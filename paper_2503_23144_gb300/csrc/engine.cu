@@ -319,20 +319,207 @@ __global__ void k_unpack_z(const cplx* __restrict__ Zp, cplx* __restrict__ Z, in
     }
 }
 
+// packed layouts of the batched paths: Xt[n][ef], Zt[n][ab], n = r*PO + ij
+// Xt[n][ef] = 1/2 (X[r][i][j][e][f] - X[r][i][j][f][e]),  i<j, e<f
+__global__ void k_pack_xt(const cplx* __restrict__ X, cplx* __restrict__ Xt, int64_t R, int64_t O, int64_t V) {
+    int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
+    int64_t total = R * PO * PV;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ef = idx % PV, n = idx / PV;
+        int64_t r = n / PO, ij = n % PO;
+        int64_t e, f, i, j;
+        pair_decode(ef, V, e, f);
+        pair_decode(ij, O, i, j);
+        const cplx* x = X + ((r * O + i) * O + j) * V * V;
+        cplx u = x[e * V + f], w = x[f * V + e];
+        Xt[idx] = make_double2(0.5 * (u.x - w.x), 0.5 * (u.y - w.y));
+    }
+}
+
+// Z[r][i][j][a][b] = alpha * sign * Zt[r*PO + ij][ab] + beta * Z
+__global__ void k_unpack_zt(const cplx* __restrict__ Zt, cplx* __restrict__ Z, int64_t R, int64_t O, int64_t V,
+                            cplx alpha, cplx beta, int beta0) {
+    int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
+    int64_t total = R * O * O * V * V;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = idx % V, t = idx / V;
+        int64_t a = t % V;
+        t /= V;
+        int64_t j = t % O;
+        t /= O;
+        int64_t i = t % O, r = t / O;
+        cplx v = make_double2(0.0, 0.0);
+        if (i != j && a != b) {
+            double sg = 1.0;
+            int64_t ii = i, jj = j, aa = a, bb = b;
+            if (ii > jj) { int64_t q = ii; ii = jj; jj = q; sg = -sg; }
+            if (aa > bb) { int64_t q = aa; aa = bb; bb = q; sg = -sg; }
+            cplx z = Zt[(r * PO + pair_index(ii, jj, O)) * PV + pair_index(aa, bb, V)];
+            v = make_double2(sg * (alpha.x * z.x - alpha.y * z.y), sg * (alpha.x * z.y + alpha.y * z.x));
+        }
+        if (!beta0) {
+            cplx o = Z[idx];
+            v.x += beta.x * o.x - beta.y * o.y;
+            v.y += beta.x * o.y + beta.y * o.x;
+        }
+        Z[idx] = v;
+    }
+}
+
+// W[row][ef] = GT[(b-gb0)V + f][(a-a0)V + e] - GT[(b-gb0)V + e][(a-a0)V + f]  (e<f)
+// for the rows (a,b) = pair(prow0 + row) of one slab; GT = sum_L Bvv_bf Bvv_ae
+__global__ void k_antisym_gt(const cplx* __restrict__ GT, int64_t ldt, int64_t a0, int64_t gb0, int64_t prow0,
+                             int64_t nrows, int64_t V, cplx* __restrict__ W) {
+    int64_t PV = V * (V - 1) / 2;
+    int64_t total = nrows * PV;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row = idx / PV, ef = idx % PV;
+        int64_t a, b, e, f;
+        pair_decode(prow0 + row, V, a, b);
+        pair_decode(ef, V, e, f);
+        int64_t ra = (a - a0) * V, cb = (b - gb0) * V;
+        cplx g1 = GT[(cb + f) * ldt + ra + e];
+        cplx g2 = GT[(cb + e) * ldt + ra + f];
+        W[idx] = make_double2(g1.x - g2.x, g1.y - g2.y);
+    }
+}
+
 int grid_n(Dev& D, int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)D.sm_count * 16));
 }
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// <ab||ef> assembly in slabs.  A slab holds the rows (a,b), a in [a0, a1),
+// b in [max(a+1, b0), b1): consecutive rows of the pair order.  Its products
+// GT[(b,f)][(a,e)] = sum_L Bvv^L_bf Bvv^L_ae (b >= gb0) come from one GEMM
+// over L, then W_ab,ef = GT[(b,f)][(a,e)] - GT[(b,e)][(a,f)] for e < f.
+// ---------------------------------------------------------------------------
+struct Slab {
+    int64_t a0, a1, b0, b1, gb0, prow0, nrows;
+};
+
+// budget_el bounds the GT elements of one slab; row_cap > 0 forces single-a
+// slabs of at most row_cap rows
+static std::vector<Slab> plan_slabs(int64_t V, int64_t budget_el, int64_t row_cap) {
+    std::vector<Slab> out;
+    int64_t a0 = 0;
+    while (a0 < V - 1) {
+        const int64_t nb = V - a0 - 1;
+        if (row_cap <= 0 && V * V * nb <= budget_el) {
+            const int64_t na = std::max<int64_t>(1, budget_el / (V * V * nb));
+            const int64_t a1 = std::min<int64_t>(V - 1, a0 + na);
+            Slab sl{a0, a1, a0 + 1, V, a0 + 1, pair_index(a0, a0 + 1, V), 0};
+            sl.nrows = pair_index(a1 - 1, V - 1, V) + 1 - sl.prow0;
+            out.push_back(sl);
+            a0 = a1;
+        } else {
+            int64_t cb = row_cap > 0 ? row_cap : std::max<int64_t>(1, budget_el / (V * V));
+            if (row_cap <= 0 && cb >= 256) cb = cb / 128 * 128;  // whole 128-row M tiles
+            for (int64_t b0 = a0 + 1; b0 < V; b0 += cb) {
+                const int64_t b1 = std::min<int64_t>(V, b0 + cb);
+                out.push_back(Slab{a0, a0 + 1, b0, b1, b0, pair_index(a0, b0, V), b1 - b0});
+            }
+            a0 += 1;
+        }
+    }
+    return out;
+}
+
+static int64_t slab_budget_el(Dev& D) {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    double bytes = std::min(0.3 * double(fr + D.pool.cached), 24.0 * (1 << 30));
+    return std::max<int64_t>(1 << 20, (int64_t)(std::max(bytes, double(1 << 30)) / 16));
+}
+
+// embedded B operand of the slab GEMMs: n = (b,f), k = L (built once per precision)
+static void ensure_bcache(Dev& D, LadderCtx& LC, int prec) {
+    if (LC.bcache && LC.bcache_prec == prec) return;
+    LC.bcache.reset();
+    const int64_t L = LC.Bvv.d[0], V = LC.Bvv.d[1];
+    int64_t rows_e, pitch;
+    size_t bytes = tc_embed_bytes(prec, V * V, L, 1, rows_e, pitch, true);
+    void* p = D.pool.get(bytes);
+    LC.bcache.reset(new DevBuf{&D.pool, p, bytes});
+    tc_embed_b(D, prec, LC.Bvv.p, 0, V * V, 1, false, 1, L, V * V, pitch, p);
+    LC.bcache_prec = prec;
+    LC.b_pitch = pitch;
+}
+
+// Assemble the rows of slab sl: FP64 into W [nrows][PV] (prec == FP64; conj:
+// <ef||ab> = conj <ab||ef> rows), or embedded into Wemb [nrows][pitch_w].
+// A_cache keeps the embedded (a,e) rows between slabs of the same a range.
+struct SlabScratch {
+    int64_t a0 = -1, a1 = -1;
+    std::shared_ptr<DevBuf> aemb;
+    int64_t a_pitch = 0;
+    Tensor gt_buf;  // GT of the largest slab of the plan (allocated once)
+    cplx* gt = nullptr;
+    int64_t gt_el = 0;
+    SlabScratch(Dev& D, const std::vector<Slab>& plan, int64_t V) {
+        for (const Slab& sl : plan) gt_el = std::max(gt_el, (sl.a1 - sl.a0) * V * (sl.b1 - sl.gb0) * V);
+        gt_buf = empty(D, {std::max<int64_t>(gt_el, 1)});
+        gt = gt_buf.p;
+    }
+};
+
+static int64_t max_rows(const std::vector<Slab>& plan) {
+    int64_t m = 0;
+    for (const Slab& sl : plan) m = std::max(m, sl.nrows);
+    return m;
+}
+
+static void assemble_slab(Dev& D, LadderCtx& LC, const Slab& sl, int prec, bool conj, cplx* W, void* Wemb,
+                          int64_t pitch_w, SlabScratch& sc) {
+    const int64_t L = LC.Bvv.d[0], V = LC.Bvv.d[1];
+    const int64_t M = (sl.a1 - sl.a0) * V, N = (sl.b1 - sl.gb0) * V;
+    REQUIRE(sc.gt && M * N <= sc.gt_el, "ladder: slab product buffer too small");
+    Tensor GT = wrap(sc.gt, {N, M});
+    if (prec == LRCC_FP64) {
+        GemmArgs g;
+        g.M = M; g.N = N; g.K = L; g.batch = 1;
+        g.A = LC.Bvv.p + sl.a0 * V; g.sAb = 0; g.sAm = 1; g.sAk = V * V; g.cA = conj;
+        g.B = LC.Bvv.p + sl.gb0 * V; g.sBb = 0; g.sBk = V * V; g.sBn = 1; g.cB = conj;
+        g.C = GT.p; g.sCb = 0; g.sCm = 1; g.sCn = M;
+        g.alpha = mkc(1.0); g.beta = mkc(0.0);
+        gemm_f64(D, g);
+        k_antisym_gt<<<grid_n(D, sl.nrows * (V * (V - 1) / 2)), 256, 0, D.st>>>(GT.p, M, sl.a0, sl.gb0, sl.prow0,
+                                                                               sl.nrows, V, W);
+        LAUNCH_CHECK(D);
+        return;
+    }
+    ensure_bcache(D, LC, prec);
+    if (sc.a0 != sl.a0 || sc.a1 != sl.a1) {
+        int64_t rows_e, pitch;
+        size_t bytes = tc_embed_bytes(prec, M, L, 1, rows_e, pitch, false);
+        void* p = D.pool.get(bytes);
+        sc.aemb.reset(new DevBuf{&D.pool, p, bytes});
+        tc_embed_a(D, prec, LC.Bvv.p + sl.a0 * V, 0, 1, V * V, false, 1, M, L, pitch, p);
+        sc.a0 = sl.a0;
+        sc.a1 = sl.a1;
+        sc.a_pitch = pitch;
+    }
+    REQUIRE(sc.a_pitch == LC.b_pitch, "ladder: embedded K pitch mismatch");
+    const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
+    const char* pb = (const char*)LC.bcache->p + (size_t)(2 * sl.gb0 * V) * (size_t)(LC.b_pitch * es);
+    tc_gemm_embedded(D, prec, sc.aemb->p, pb, 1, M, N, L, LC.b_pitch, GT.p, 0, 1, M, mkc(1.0), mkc(0.0), false,
+                     8.0 * M * N * L);
+    tc_embed_antisym_slab(D, prec, GT.p, M, sl.a0, sl.gb0, sl.prow0, sl.nrows, V, pitch_w, Wemb);
+}
+
 // Build the embedded <ab||ef> matrix W' (rows a<b, K over e<f) once for a
 // mixed precision, if it fits in a third of the free device memory.
 static bool ensure_wcache(Dev& D, LadderCtx& LC, int64_t V, int prec) {
     if (LC.wcache && LC.wcache_prec == prec) return true;
-    if (LC.wcache_disabled) return false;
-    const int64_t PV = V * (V - 1) / 2, L = LC.Bvv.d[0];
-    int64_t Mp, Kp;
-    size_t bytes = tc_embed_bytes(prec, PV, PV, 1, Mp, Kp, false);
+    if (LC.wcache_disabled || LC.slab_rows > 0) return false;
+    const int64_t PV = V * (V - 1) / 2;
+    int64_t rows_e, pitch;
+    size_t bytes = tc_embed_bytes(prec, PV, PV, 1, rows_e, pitch, false);
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
     if ((double)bytes > 0.33 * double(fr + D.pool.cached)) {
@@ -342,64 +529,25 @@ static bool ensure_wcache(Dev& D, LadderCtx& LC, int64_t V, int prec) {
     LC.wcache.reset();
     void* p = D.pool.get(bytes);
     LC.wcache.reset(new DevBuf{&D.pool, p, bytes});
-    CK(cudaMemsetAsync(p, 0, bytes, D.st));
-    int64_t budget = LC.slab_rows > 0 ? LC.slab_rows : (int64_t(4) << 30) / 16;
-    int64_t na = std::max<int64_t>(1, budget / std::max<int64_t>(1, V * V * V));
-    for (int64_t a0 = 0; a0 < V - 1; a0 += na) {
-        int64_t a1 = std::min<int64_t>(V - 1, a0 + na);
-        int64_t nb = V - a0 - 1;
-        Tensor G = empty(D, {(a1 - a0) * V, nb * V});
-        GemmArgs g1;
-        g1.M = (a1 - a0) * V; g1.N = nb * V; g1.K = L; g1.batch = 1;
-        g1.A = LC.Bvv.p + a0 * V; g1.sAb = 0; g1.sAm = 1; g1.sAk = V * V; g1.cA = false;
-        g1.B = LC.Bvv.p + (a0 + 1) * V; g1.sBb = 0; g1.sBk = V * V; g1.sBn = 1; g1.cB = false;
-        g1.C = G.p; g1.sCb = 0; g1.sCm = nb * V; g1.sCn = 1;
-        g1.alpha = mkc(1.0); g1.beta = mkc(0.0);
-        gemm_tc(D, g1, prec);
-        int64_t row0 = a0 * (2 * V - a0 - 1) / 2, row1 = a1 * (2 * V - a1 - 1) / 2;
-        int64_t nrows = row1 - row0;
-        Tensor W = empty(D, {nrows, PV});
-        k_antisym_slab<<<grid_n(D, nrows * PV), 256, 0, D.st>>>(G.p, nb * V, W.p, a0, nrows, V);
-        LAUNCH_CHECK(D);
-        int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
-        tc_embed_a(D, prec, W.p, 0, PV, 1, false, 1, nrows, PV, Mp, Kp, (char*)p + (size_t)(row0 * Kp * es));
-    }
+    const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
+    ensure_bcache(D, LC, prec);  // before sizing the slabs on the memory left
+    const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), 0);
+    SlabScratch sc(D, plan, V);
+    for (const Slab& sl : plan)
+        assemble_slab(D, LC, sl, prec, false, nullptr, (char*)p + (size_t)(sl.prow0 * pitch * es), pitch, sc);
+    LC.bcache.reset();  // the cache replaces per-call assembly
+    LC.bcache_prec = -1;
     LC.wcache_prec = prec;
-    LC.w_Mp = Mp;
-    LC.w_Kp = Kp;
+    LC.w_pitch = pitch;
     return true;
-}
-
-// Z = alpha * 1/2 sum_ef <ab||ef> X + beta Z with the cached W';
-// transpose: conj(W' conj(Xp)) (B^T = conj B).
-static void ladder_cached(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose,
-                          int prec) {
-    int64_t R = X.d[0], O = X.d[1], V = X.d[3];
-    int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
-    Tensor Xp = empty(D, {PV, R * PO});
-    k_pack_x<<<grid_n(D, PV * R * PO), 256, 0, D.st>>>(X.p, Xp.p, R, O, V);
-    LAUNCH_CHECK(D);
-    int64_t Np2, Kp;
-    size_t bytesB = tc_embed_bytes(prec, R * PO, PV, 1, Np2, Kp, true);
-    REQUIRE(Kp == LC.w_Kp, "ladder cache: K padding mismatch");
-    void* pb = D.pool.get(bytesB);
-    std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
-    CK(cudaMemsetAsync(pb, 0, bytesB, D.st));
-    tc_embed_b(D, prec, Xp.p, 0, R * PO, 1, transpose, 1, PV, R * PO, Np2, Kp, pb);
-    Tensor Zp = empty(D, {PV, R * PO});
-    tc_gemm_embedded(D, prec, LC.wcache->p, pb, 1, PV, R * PO, LC.w_Mp, Np2, Kp, Zp.p, 0, R * PO, 1, mkc(1.0),
-                     mkc(0.0), transpose, 8.0 * PV * PV * R * PO);
-    bool beta0 = beta.x == 0.0 && beta.y == 0.0;
-    k_unpack_z<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zp.p, Z.p, R, O, V, alpha, beta, beta0);
-    LAUNCH_CHECK(D);
 }
 
 // FP64 <ab||ef> matrix W [P_V][P_V] (rows a<b, columns e<f), built once if it
 // fits in a third of the free device memory.
 static bool ensure_w64(Dev& D, LadderCtx& LC, int64_t V) {
     if (LC.w64.p) return true;
-    if (LC.w64_disabled) return false;
-    const int64_t PV = V * (V - 1) / 2, L = LC.Bvv.d[0];
+    if (LC.w64_disabled || LC.slab_rows > 0) return false;
+    const int64_t PV = V * (V - 1) / 2;
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
     if (16.0 * PV * PV > 0.33 * double(fr + D.pool.cached)) {
@@ -407,56 +555,70 @@ static bool ensure_w64(Dev& D, LadderCtx& LC, int64_t V) {
         return false;
     }
     Tensor W = empty(D, {PV, PV});
-    int64_t budget = LC.slab_rows > 0 ? LC.slab_rows : (int64_t(4) << 30) / 16;
-    int64_t na = std::max<int64_t>(1, budget / std::max<int64_t>(1, V * V * V));
-    for (int64_t a0 = 0; a0 < V - 1; a0 += na) {
-        int64_t a1 = std::min<int64_t>(V - 1, a0 + na);
-        int64_t nb = V - a0 - 1;
-        Tensor G = empty(D, {(a1 - a0) * V, nb * V});
-        GemmArgs g1;
-        g1.M = (a1 - a0) * V; g1.N = nb * V; g1.K = L; g1.batch = 1;
-        g1.A = LC.Bvv.p + a0 * V; g1.sAb = 0; g1.sAm = 1; g1.sAk = V * V; g1.cA = false;
-        g1.B = LC.Bvv.p + (a0 + 1) * V; g1.sBb = 0; g1.sBk = V * V; g1.sBn = 1; g1.cB = false;
-        g1.C = G.p; g1.sCb = 0; g1.sCm = nb * V; g1.sCn = 1;
-        g1.alpha = mkc(1.0); g1.beta = mkc(0.0);
-        gemm_f64(D, g1);
-        int64_t row0 = a0 * (2 * V - a0 - 1) / 2, row1 = a1 * (2 * V - a1 - 1) / 2;
-        k_antisym_slab<<<grid_n(D, (row1 - row0) * PV), 256, 0, D.st>>>(G.p, nb * V, W.p + row0 * PV, a0,
-                                                                         row1 - row0, V);
-        LAUNCH_CHECK(D);
-    }
+    const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), 0);
+    SlabScratch sc(D, plan, V);
+    for (const Slab& sl : plan) assemble_slab(D, LC, sl, LRCC_FP64, false, W.p + sl.prow0 * PV, nullptr, 0, sc);
     LC.w64 = W;
     return true;
 }
 
+void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol, bool transpose, int prec) {
+    const int64_t V = LC.Bvv.d[1], PV = V * (V - 1) / 2;
+    if (ncol <= 0 || PV <= 0) return;
+    if (prec == LRCC_FP64) {
+        GemmArgs g2;
+        g2.N = ncol; g2.batch = 1;
+        g2.B = Xt; g2.sBb = 0; g2.sBk = 1; g2.sBn = PV; g2.cB = false;
+        g2.sCb = 0; g2.sCm = 1; g2.sCn = PV;
+        g2.alpha = mkc(1.0); g2.beta = mkc(0.0);
+        if (ensure_w64(D, LC, V)) {
+            g2.M = PV; g2.K = PV;
+            g2.A = LC.w64.p; g2.sAb = 0; g2.sAm = PV; g2.sAk = 1; g2.cA = transpose;  // B^T = conj B: conj(W)
+            g2.C = Zt;
+            gemm_f64(D, g2);
+            return;
+        }
+        const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), LC.slab_rows);
+        SlabScratch sc(D, plan, V);
+        Tensor W = empty(D, {max_rows(plan), PV});
+        for (const Slab& sl : plan) {
+            assemble_slab(D, LC, sl, LRCC_FP64, transpose, W.p, nullptr, 0, sc);
+            g2.M = sl.nrows; g2.K = PV;
+            g2.A = W.p; g2.sAb = 0; g2.sAm = PV; g2.sAk = 1; g2.cA = false;
+            g2.C = Zt + sl.prow0;
+            gemm_f64(D, g2);
+        }
+        return;
+    }
+    // tensor cores: X' embedded once; the transpose map is conj(W' conj(X))
+    int64_t rows_e, pitch;
+    size_t bytesB = tc_embed_bytes(prec, ncol, PV, 1, rows_e, pitch, true);
+    void* pb = D.pool.get(bytesB);
+    std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
+    tc_embed_b(D, prec, Xt, 0, 1, PV, transpose, 1, PV, ncol, pitch, pb);
+    if (ensure_wcache(D, LC, V, prec)) {
+        REQUIRE(pitch == LC.w_pitch, "ladder cache: K pitch mismatch");
+        tc_gemm_embedded(D, prec, LC.wcache->p, pb, 1, PV, ncol, PV, pitch, Zt, 0, 1, PV, mkc(1.0), mkc(0.0),
+                         transpose, 8.0 * PV * PV * ncol);
+        return;
+    }
+    const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
+    ensure_bcache(D, LC, prec);
+    const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), LC.slab_rows);
+    SlabScratch sc(D, plan, V);
+    const size_t wb = (size_t)(max_rows(plan) * pitch * es);
+    void* pw = D.pool.get(wb);
+    std::shared_ptr<DevBuf> hw(new DevBuf{&D.pool, pw, wb});
+    for (const Slab& sl : plan) {
+        assemble_slab(D, LC, sl, prec, false, nullptr, pw, pitch, sc);
+        tc_gemm_embedded(D, prec, pw, pb, 1, sl.nrows, ncol, PV, pitch, Zt + sl.prow0, 0, 1, PV, mkc(1.0),
+                         mkc(0.0), transpose, 8.0 * sl.nrows * PV * ncol);
+    }
+}
+
 void ladder(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose, int prec) {
     REQUIRE(X.nd == 5 && Z.nd == 5 && X.contiguous() && Z.contiguous(), "ladder needs contiguous [R][O][O][V][V]");
-    if (prec == LRCC_FP64 && X.d[1] >= 2 && X.d[3] >= 2 && ensure_w64(D, LC, X.d[3])) {
-        int64_t R = X.d[0], O = X.d[1], V = X.d[3];
-        int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
-        Tensor Xp = empty(D, {PV, R * PO});
-        k_pack_x<<<grid_n(D, PV * R * PO), 256, 0, D.st>>>(X.p, Xp.p, R, O, V);
-        LAUNCH_CHECK(D);
-        Tensor Zp = empty(D, {PV, R * PO});
-        GemmArgs g2;
-        g2.M = PV; g2.N = R * PO; g2.K = PV; g2.batch = 1;
-        g2.A = LC.w64.p; g2.sAb = 0; g2.sAm = PV; g2.sAk = 1; g2.cA = transpose;  // B^T = conj B: conj(W)
-        g2.B = Xp.p; g2.sBb = 0; g2.sBk = R * PO; g2.sBn = 1; g2.cB = false;
-        g2.C = Zp.p; g2.sCb = 0; g2.sCm = R * PO; g2.sCn = 1;
-        g2.alpha = mkc(1.0); g2.beta = mkc(0.0);
-        gemm_f64(D, g2);
-        bool beta0 = beta.x == 0.0 && beta.y == 0.0;
-        k_unpack_z<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zp.p, Z.p, R, O, V, alpha, beta, beta0);
-        LAUNCH_CHECK(D);
-        return;
-    }
-    if (prec != LRCC_FP64 && gemm_tc_available() && X.d[1] >= 2 && X.d[3] >= 2 &&
-        ensure_wcache(D, LC, X.d[3], prec)) {
-        ladder_cached(D, LC, X, alpha, beta, Z, transpose, prec);
-        return;
-    }
     int64_t R = X.d[0], O = X.d[1], V = X.d[3];
-    int64_t L = LC.Bvv.d[0];
     REQUIRE(LC.Bvv.d[1] == V && LC.Bvv.d[2] == V, "ladder: Bvv shape");
     int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
     bool beta0 = beta.x == 0.0 && beta.y == 0.0;
@@ -465,40 +627,12 @@ void ladder(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tenso
         else axpby(D, mkc(0.0), Z, false, beta, Z);
         return;
     }
-    Tensor Xp = empty(D, {PV, R * PO});
-    k_pack_x<<<grid_n(D, PV * R * PO), 256, 0, D.st>>>(X.p, Xp.p, R, O, V);
+    Tensor Xt = empty(D, {R * PO, PV});
+    k_pack_xt<<<grid_n(D, R * PO * PV), 256, 0, D.st>>>(X.p, Xt.p, R, O, V);
     LAUNCH_CHECK(D);
-    Tensor Zp = empty(D, {PV, R * PO});
-    // slab height: G of na*V x (V-a0-1)*V complex kept under ~4 GiB
-    int64_t budget = LC.slab_rows > 0 ? LC.slab_rows : (int64_t(4) << 30) / 16;
-    int64_t na = std::max<int64_t>(1, budget / std::max<int64_t>(1, V * V * V));
-    for (int64_t a0 = 0; a0 < V - 1; a0 += na) {
-        int64_t a1 = std::min<int64_t>(V - 1, a0 + na);
-        int64_t nb = V - a0 - 1;  // b in [a0+1, V)
-        Tensor G = empty(D, {(a1 - a0) * V, nb * V});
-        GemmArgs g1;
-        g1.M = (a1 - a0) * V; g1.N = nb * V; g1.K = L; g1.batch = 1;
-        g1.A = LC.Bvv.p + a0 * V; g1.sAb = 0; g1.sAm = 1; g1.sAk = V * V; g1.cA = transpose;
-        g1.B = LC.Bvv.p + (a0 + 1) * V; g1.sBb = 0; g1.sBk = V * V; g1.sBn = 1; g1.cB = transpose;
-        g1.C = G.p; g1.sCb = 0; g1.sCm = nb * V; g1.sCn = 1;
-        g1.alpha = mkc(1.0); g1.beta = mkc(0.0);
-        if (prec != LRCC_FP64 && gemm_tc_available()) gemm_tc(D, g1, prec);
-        else gemm_f64(D, g1);
-        int64_t row0 = a0 * (2 * V - a0 - 1) / 2, row1 = a1 * (2 * V - a1 - 1) / 2;
-        int64_t nrows = row1 - row0;
-        Tensor W = empty(D, {nrows, PV});
-        k_antisym_slab<<<grid_n(D, nrows * PV), 256, 0, D.st>>>(G.p, nb * V, W.p, a0, nrows, V);
-        LAUNCH_CHECK(D);
-        GemmArgs g2;
-        g2.M = nrows; g2.N = R * PO; g2.K = PV; g2.batch = 1;
-        g2.A = W.p; g2.sAb = 0; g2.sAm = PV; g2.sAk = 1; g2.cA = false;
-        g2.B = Xp.p; g2.sBb = 0; g2.sBk = R * PO; g2.sBn = 1; g2.cB = false;
-        g2.C = Zp.p + row0 * R * PO; g2.sCb = 0; g2.sCm = R * PO; g2.sCn = 1;
-        g2.alpha = mkc(1.0); g2.beta = mkc(0.0);
-        if (prec != LRCC_FP64 && gemm_tc_available()) gemm_tc(D, g2, prec);
-        else gemm_f64(D, g2);
-    }
-    k_unpack_z<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zp.p, Z.p, R, O, V, alpha, beta, beta0);
+    Tensor Zt = empty(D, {R * PO, PV});
+    ladder_packed(D, LC, Xt.p, Zt.p, R * PO, transpose, prec);
+    k_unpack_zt<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zt.p, Z.p, R, O, V, alpha, beta, beta0);
     LAUNCH_CHECK(D);
 }
 

@@ -13,11 +13,15 @@
 // Accumulation is FP32 in TMEM; the epilogue scales by the complex alpha and
 // adds beta * C in FP64.
 //
-// CTA tile: 128 (M) x 256 (accumulator columns = 128 complex outputs), K stage
-// = 128 bytes of K per row, 4 stages (192 KB of shared memory), 128 threads:
-// thread 0 issues TMA, thread 32 issues MMAs, all four warps run the epilogue
-// (warp w owns TMEM lanes 32w..32w+31).  Every mbarrier wait is bounded; on
-// expiry the kernel raises the context's error word and returns.
+// Persistent kernel, one CTA of 192 threads per SM: warp 0 issues TMA into a
+// ring of shared-memory stages (128 bytes of K per row each), warp 1 issues
+// tcgen05.mma into one of two TMEM accumulators of 128 x BN FP32 columns
+// (BN = 32..256, picked per call from N), warps 2-5 drain the other
+// accumulator (warp w owns TMEM lanes 32 (w % 4) .. +31), so epilogues overlap
+// main loops.  Work units are (M tile, N tile, batch, K split); split units
+// add into C with FP64 atomics.  Every mbarrier wait is bounded; on expiry the
+// kernel raises the context's error word, drains its copies and MMAs, frees
+// TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -29,12 +33,10 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int BM = 128;
 constexpr int ROWB = 128;                 // bytes of K per row per stage
 constexpr int A_STAGE = BM * ROWB;        // 16 KB
-constexpr int B_STAGE = BN * ROWB;        // 32 KB
-constexpr int SMEM_BYTES = STAGES * (A_STAGE + B_STAGE) + 1024 + 256;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int smem_bytes(int bn, int stages) { return stages * (A_STAGE + bn * ROWB) + 1024 + 256; }
 constexpr uint32_t WAIT_LIMIT = 1u << 25;  // polls (with backoff) before giving up
 constexpr uint32_t WAIT_LIMIT_INJECT = 1u << 14;
 
@@ -137,36 +139,81 @@ struct Epi {
     cplx alpha, beta;
     int conj_acc;  // use conj(accumulator): conj(A.conj(B)) = conj(A).B
     int atomic;    // split-K: accumulate alpha*acc into C with FP64 atomics (C pre-scaled)
-    int kb_per_split;
 };
 
-template <int KIND>
-__global__ void __launch_bounds__(128, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int num_kb, int tiles_n,
-              Epi ep, int* err, int skip_tma, uint32_t wait_limit) {
+// Work units of the persistent kernel: (M tile, N tile, batch, K split).
+// Inside one split and batch the tiles run in groups of `group` M tiles with
+// the M tile fastest, so CTAs resident together share the B tiles they read.
+struct Sched {
+    int tiles_m, tiles_n, batch, splits, kps, num_kb, group;
+    long long units;
+};
+
+__device__ __forceinline__ void unit_coords(const Sched& s, long long u, int& tm, int& tn, int& bz, int& kb0,
+                                            int& kb1) {
+    const long long tiles = (long long)s.tiles_m * s.tiles_n;
+    const long long per_split = tiles * s.batch;
+    const int sp = (int)(u / per_split);
+    const long long r = u - (long long)sp * per_split;
+    bz = (int)(r / tiles);
+    const long long t = r - (long long)bz * tiles;
+    const long long gsz = (long long)s.group * s.tiles_n;
+    const int g = (int)(t / gsz);
+    const int w = (int)(t - (long long)g * gsz);
+    const int m0 = g * s.group;
+    const int gh = min(s.group, s.tiles_m - m0);
+    tm = m0 + w % gh;
+    tn = w / gh;
+    kb0 = sp * s.kps;
+    kb1 = min(s.num_kb, kb0 + s.kps);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+// bounded wait taken by a whole warp: every lane polls, and the warp goes on
+// only if all lanes saw the phase complete (so the .sync.aligned TMEM loads
+// that follow run converged)
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int* err, uint32_t limit) {
+    bool ok = mbar_wait(bar, parity, err, limit);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Persistent tcgen05 GEMM.  192 threads: warp 0 lane 0 issues TMA, warp 1
+// lane 0 issues MMAs, warps 2-5 drain accumulators (warp w reads TMEM lanes
+// 32 (w % 4) .. +31).  Two TMEM accumulators of BN columns alternate, so the
+// epilogue of one unit overlaps the main loop of the next.
+template <int KIND, int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, Sched sc, Epi ep,
+              int* err, int skip_tma, uint32_t wait_limit) {
+    constexpr int B_STAGE = BN * ROWB;
+    constexpr uint32_t TMEM_COLS = 2 * BN;
+    constexpr int KELEM = KIND == 0 ? 64 : 32;  // elements per 128-byte row
+    constexpr uint32_t IDESC = instr_desc(KIND == 0 ? 1u : 2u, BM, BN);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
     uint8_t* sB = smem + STAGES * A_STAGE;
     uint64_t* full = (uint64_t*)(sB + STAGES * B_STAGE);
     uint64_t* empty = full + STAGES;
-    uint64_t* accb = empty + STAGES;
-    uint32_t* tslot = (uint32_t*)(accb + 1);
-
+    uint64_t* accf = empty + STAGES;  // [2] accumulator complete
+    uint64_t* acce = accf + 2;        // [2] accumulator drained
+    uint64_t* done = acce + 2;        // every MMA of this CTA complete
+    uint32_t* tslot = (uint32_t*)(done + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile_m = blockIdx.x / tiles_n, tile_n = blockIdx.x % tiles_n;
-    const int bz = blockIdx.y;
-    const int kb0 = blockIdx.z * ep.kb_per_split;
-    const int kb1 = min(num_kb, kb0 + ep.kb_per_split);
-    constexpr int KELEM = KIND == 0 ? 64 : 32;  // elements per 128-byte row
-    constexpr uint32_t IDESC = instr_desc(KIND == 0 ? 1u : 2u, BM, BN);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], 4);
+        }
+        mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
@@ -182,87 +229,134 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (threadIdx.x == 0) {
-        // TMA producer
-        for (int kb = kb0; kb < kb1; ++kb) {
-            int i = kb - kb0;
-            int s = i % STAGES;
-            uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (!mbar_wait(&empty[s], ph ^ 1u, err, wait_limit)) break;
-            mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
-            if (skip_tma) continue;  // fault injection: the full barrier's bytes never arrive
-            tma_load_3d(sA + s * A_STAGE, &ta, &full[s], kb * KELEM, tile_m * BM, bz);
-            tma_load_3d(sB + s * B_STAGE, &tb, &full[s], kb * KELEM, tile_n * BN, bz);
-        }
-    } else if (threadIdx.x == 32) {
-        // MMA issuer
-        int done = 0;
-        for (int kb = kb0; kb < kb1; ++kb) {
-            int i = kb - kb0;
-            int s = i % STAGES;
-            uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph, err, wait_limit)) break;
-            tc_fence_after();
-            uint64_t ad = smem_desc(su32(sA + s * A_STAGE));
-            uint64_t bd = smem_desc(su32(sB + s * B_STAGE));
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                // 32 bytes of K per MMA (16 bf16 or 8 tf32): +2 in the >>4 address field
-                mma<KIND>(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), IDESC, (kb > kb0 || kk > 0) ? 1u : 0u);
-            }
-            mma_commit(&empty[s]);
-            done = kb + 1;
-        }
-        (void)done;
-        mma_commit(accb);
-    }
-    __syncwarp();
-
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 (accumulator rows)
-    bool got = mbar_wait(accb, 0, err, wait_limit);
-    if (!got) got = mbar_wait(accb, 0, err, wait_limit);  // second bounded wait before releasing TMEM
-    __syncwarp();
-    tc_fence_after();
-    const int64_t m = (int64_t)tile_m * BM + warp * 32 + lane;
-    cplx* Cb = ep.C + (int64_t)bz * ep.sCb;
-    const bool beta0 = ep.beta.x == 0.0 && ep.beta.y == 0.0;
-#pragma unroll 1
-    for (int c = 0; c < BN / 32; ++c) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-        if (got && kb1 > kb0 && m < ep.M) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                int64_t n = ((int64_t)tile_n * BN + c * 32 + 2 * j) >> 1;
-                if (n < ep.N) {
-                    double re = (double)__uint_as_float(r[2 * j]), im = (double)__uint_as_float(r[2 * j + 1]);
-                    if (ep.conj_acc) im = -im;
-                    cplx* cp = Cb + m * ep.sCm + n * ep.sCn;
-                    cplx v = make_double2(ep.alpha.x * re - ep.alpha.y * im, ep.alpha.x * im + ep.alpha.y * re);
-                    if (ep.atomic) {
-                        atomicAdd(&cp->x, v.x);
-                        atomicAdd(&cp->y, v.y);
-                        continue;
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer
+            int it = 0;  // stage uses armed so far
+            bool ok = true;
+            for (long long u = blockIdx.x; ok && u < sc.units; u += gridDim.x) {
+                int tm, tn, bz, kb0, kb1;
+                unit_coords(sc, u, tm, tn, bz, kb0, kb1);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, err, wait_limit)) {
+                        ok = false;
+                        break;
                     }
-                    if (!beta0) {
-                        cplx o = *cp;
-                        v.x += ep.beta.x * o.x - ep.beta.y * o.y;
-                        v.y += ep.beta.x * o.y + ep.beta.y * o.x;
-                    }
-                    *cp = v;
+                    mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
+                    ++it;
+                    if (skip_tma) continue;  // fault injection: the stage's bytes never arrive
+                    tma_load_3d(sA + s * A_STAGE, &ta, &full[s], kb * KELEM, tm * BM, bz);
+                    tma_load_3d(sB + s * B_STAGE, &tb, &full[s], kb * KELEM, tn * BN, bz);
                 }
             }
+            // copies still in flight land before the CTA exits: wait for the
+            // last armed phase of every stage (already complete on the normal path)
+            for (int s = 0; s < STAGES && s < it; ++s) {
+                const int last = s + STAGES * ((it - 1 - s) / STAGES);
+                mbar_wait(&full[s], (uint32_t)(last / STAGES) & 1u, err, wait_limit);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            int it = 0, ti = 0;
+            bool ok = true;
+            for (long long u = blockIdx.x; ok && u < sc.units; u += gridDim.x) {
+                int tm, tn, bz, kb0, kb1;
+                unit_coords(sc, u, tm, tn, bz, kb0, kb1);
+                const int acc = ti & 1;
+                if (!mbar_wait(&acce[acc], ((uint32_t)(ti >> 1) & 1u) ^ 1u, err, wait_limit)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * BN);
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!mbar_wait(&full[s], ph, err, wait_limit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = smem_desc(su32(sA + s * A_STAGE));
+                    const uint64_t bd = smem_desc(su32(sB + s * B_STAGE));
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        // 32 bytes of K per MMA (16 bf16 or 8 tf32): +2 in the >>4 address field
+                        mma<KIND>(d, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), IDESC,
+                                  (kb > kb0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&accf[acc]);
+                ++ti;
+            }
+            mma_commit(done);
+        }
+    } else {
+        // epilogue: FP32 accumulator pairs (Re, Im) -> alpha * acc (+ beta C) in FP64
+        const int q = warp & 3;
+        const bool beta0 = ep.beta.x == 0.0 && ep.beta.y == 0.0;
+        int ti = 0;
+        for (long long u = blockIdx.x; u < sc.units; u += gridDim.x) {
+            int tm, tn, bz, kb0, kb1;
+            unit_coords(sc, u, tm, tn, bz, kb0, kb1);
+            const int acc = ti & 1;
+            if (!warp_wait(&accf[acc], (uint32_t)(ti >> 1) & 1u, err, wait_limit)) break;
+            tc_fence_after();
+            const int64_t m = (int64_t)tm * BM + q * 32 + lane;
+            cplx* Cb = ep.C + (int64_t)bz * ep.sCb;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32), r);
+                if (kb1 > kb0 && m < ep.M) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int64_t n = (int64_t)tn * (BN / 2) + c * 16 + j;
+                        if (n < ep.N) {
+                            double re = (double)__uint_as_float(r[2 * j]), im = (double)__uint_as_float(r[2 * j + 1]);
+                            if (ep.conj_acc) im = -im;
+                            cplx* cp = Cb + m * ep.sCm + n * ep.sCn;
+                            cplx v = make_double2(ep.alpha.x * re - ep.alpha.y * im, ep.alpha.x * im + ep.alpha.y * re);
+                            if (ep.atomic) {
+                                atomicAdd(&cp->x, v.x);
+                                atomicAdd(&cp->y, v.y);
+                                continue;
+                            }
+                            if (!beta0) {
+                                cplx o = *cp;
+                                v.x += ep.beta.x * o.x - ep.beta.y * o.y;
+                                v.y += ep.beta.x * o.y + ep.beta.y * o.x;
+                            }
+                            *cp = v;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[acc]);
+            ++ti;
         }
     }
+    __syncwarp();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
+        // every MMA issued by this CTA has finished before its TMEM is released
+        bool fin = warp_wait(done, 0, err, wait_limit);
+        if (!fin) warp_wait(done, 0, err, wait_limit);
+        tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
 
 // ---------------------------------------------------------------------------
-// operand embedding (split / convert), written into zero-filled padded buffers
+// operand embedding (split / convert).  Embedded operands are [batch][rows][pitch]
+// with only the first S*K columns written: the tensor maps cover S*K columns and
+// the true row count, and TMA fills everything outside with zeros.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
@@ -270,60 +364,151 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     return r;
 }
 
-// A' [b][Mp][Kp]: row m, slots S*k + s
-template <int KIND>
-__global__ void k_embed_a(const cplx* __restrict__ A, int64_t sAb, int64_t sAm, int64_t sAk, int cA, int64_t batch,
-                          int64_t M, int64_t K, int64_t Mp, int64_t Kp, void* __restrict__ out) {
-    int64_t total = batch * M * K;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t k = idx % K, t = idx / K, m = t % M, b = t / M;
-        cplx a = A[b * sAb + m * sAm + k * sAk];
-        if (cA) a.y = -a.y;
-        int64_t row = (b * Mp + m) * Kp;
-        if (KIND == 0) {
-            __nv_bfloat16* o = (__nv_bfloat16*)out + row + 6 * k;
-            __nv_bfloat16 rh = __double2bfloat16(a.x), ih = __double2bfloat16(a.y);
-            __nv_bfloat16 rl = __double2bfloat16(a.x - (double)__bfloat162float(rh));
-            __nv_bfloat16 il = __double2bfloat16(a.y - (double)__bfloat162float(ih));
-            o[0] = rh; o[1] = ih; o[2] = rh; o[3] = ih; o[4] = rl; o[5] = il;
+__device__ __forceinline__ uint32_t bf2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// store the embedding of v = op(S)[b][r][k]: A rows (slots S*k..) or the B row
+// pair (2r: real output, 2r+1: imaginary output)
+template <int KIND, bool IS_B>
+__device__ __forceinline__ void embed_store(void* __restrict__ out, int64_t rows_e, int64_t pitch, int64_t b,
+                                            int64_t r, int64_t k, cplx v) {
+    if (KIND == 0) {
+        const __nv_bfloat16 rh = __double2bfloat16(v.x), ih = __double2bfloat16(v.y);
+        const __nv_bfloat16 rl = __double2bfloat16(v.x - (double)__bfloat162float(rh));
+        const __nv_bfloat16 il = __double2bfloat16(v.y - (double)__bfloat162float(ih));
+        if (!IS_B) {
+            uint32_t* o = (uint32_t*)((__nv_bfloat16*)out + (b * rows_e + r) * pitch + 6 * k);
+            const uint32_t hh = bf2(rh, ih);
+            o[0] = hh;
+            o[1] = hh;
+            o[2] = bf2(rl, il);
         } else {
-            uint32_t* o = (uint32_t*)out + row + 2 * k;
-            o[0] = to_tf32((float)a.x);
-            o[1] = to_tf32((float)a.y);
+            const __nv_bfloat16 nih = __hneg(ih), nil = __hneg(il);
+            uint32_t* o = (uint32_t*)((__nv_bfloat16*)out + (b * rows_e + 2 * r) * pitch + 6 * k);
+            const uint32_t re_h = bf2(rh, nih);
+            o[0] = re_h;
+            o[1] = bf2(rl, nil);
+            o[2] = re_h;
+            o = (uint32_t*)((char*)o + pitch * 2);
+            const uint32_t im_h = bf2(ih, rh);
+            o[0] = im_h;
+            o[1] = bf2(il, rl);
+            o[2] = im_h;
+        }
+    } else {
+        const uint32_t br = to_tf32((float)v.x), bi = to_tf32((float)v.y);
+        if (!IS_B) {
+            uint2* o = (uint2*)((uint32_t*)out + (b * rows_e + r) * pitch + 2 * k);
+            *o = make_uint2(br, bi);
+        } else {
+            uint2* o = (uint2*)((uint32_t*)out + (b * rows_e + 2 * r) * pitch + 2 * k);
+            *o = make_uint2(br, bi ^ 0x80000000u);
+            o = (uint2*)((char*)o + pitch * 4);
+            *o = make_uint2(bi, br);
         }
     }
 }
 
-// B' [b][Np2][Kp]: rows 2n (real output) and 2n+1 (imaginary output)
-template <int KIND>
-__global__ void k_embed_b(const cplx* __restrict__ B, int64_t sBb, int64_t sBk, int64_t sBn, int cB, int64_t batch,
-                          int64_t K, int64_t N, int64_t Np2, int64_t Kp, void* __restrict__ out) {
-    int64_t total = batch * N * K;
+// source S[b][r][k] with strides (sb, sr, sk); k fastest across threads
+template <int KIND, bool IS_B>
+__global__ void k_embed(const cplx* __restrict__ S, int64_t sb, int64_t sr, int64_t sk, int cj, int64_t batch,
+                        int64_t Rn, int64_t K, int64_t rows_e, int64_t pitch, void* __restrict__ out) {
+    const int64_t total = batch * Rn * K;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t k = idx % K, t = idx / K, n = t % N, b = t / N;
-        cplx v = B[b * sBb + k * sBk + n * sBn];
-        if (cB) v.y = -v.y;
-        int64_t r0 = (b * Np2 + 2 * n) * Kp, r1 = r0 + Kp;
-        if (KIND == 0) {
-            __nv_bfloat16 rh = __double2bfloat16(v.x), ih = __double2bfloat16(v.y);
-            __nv_bfloat16 rl = __double2bfloat16(v.x - (double)__bfloat162float(rh));
-            __nv_bfloat16 il = __double2bfloat16(v.y - (double)__bfloat162float(ih));
-            __nv_bfloat16 nih = __hneg(ih), nil = __hneg(il);
-            __nv_bfloat16* o = (__nv_bfloat16*)out + r0 + 6 * k;
-            o[0] = rh; o[1] = nih; o[2] = rl; o[3] = nil; o[4] = rh; o[5] = nih;
-            o = (__nv_bfloat16*)out + r1 + 6 * k;
-            o[0] = ih; o[1] = rh; o[2] = il; o[3] = rl; o[4] = ih; o[5] = rh;
-        } else {
-            uint32_t* o = (uint32_t*)out + r0 + 2 * k;
-            uint32_t br = to_tf32((float)v.x), bi = to_tf32((float)v.y);
-            o[0] = br;
-            o[1] = bi ^ 0x80000000u;
-            o = (uint32_t*)out + r1 + 2 * k;
-            o[0] = bi;
-            o[1] = br;
+        const int64_t k = idx % K, t = idx / K, r = t % Rn, b = t / Rn;
+        cplx v = S[b * sb + r * sr + k * sk];
+        if (cj) v.y = -v.y;
+        embed_store<KIND, IS_B>(out, rows_e, pitch, b, r, k, v);
+    }
+}
+
+// the same for sources contiguous in r: 32x32 tiles read along r, written along k
+template <int KIND, bool IS_B>
+__global__ void __launch_bounds__(256) k_embed_t(const cplx* __restrict__ S, int64_t sb, int64_t sk, int cj,
+                                                 int64_t batch, int64_t Rn, int64_t K, int64_t rows_e,
+                                                 int64_t pitch, void* __restrict__ out) {
+    __shared__ cplx tile[32][33];
+    const int64_t tr_n = (Rn + 31) / 32, tk_n = (K + 31) / 32;
+    const int64_t ntiles = batch * tr_n * tk_n;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t tk = t % tk_n, u = t / tk_n, tr = u % tr_n, b = u / tr_n;
+        const int64_t r0 = tr * 32, k0 = tk * 32;
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t r = r0 + tx, k = k0 + j;
+            cplx v = make_double2(0.0, 0.0);
+            if (r < Rn && k < K) v = S[b * sb + r + k * sk];
+            tile[j][tx] = v;
         }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t r = r0 + j, k = k0 + tx;
+            if (r < Rn && k < K) {
+                cplx v = tile[tx][j];
+                if (cj) v.y = -v.y;
+                embed_store<KIND, IS_B>(out, rows_e, pitch, b, r, k, v);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// (p, q) of pair index k among n (p < q, row-major strict upper triangle)
+__device__ __forceinline__ void pair_of(int64_t k, int64_t n, int64_t& p, int64_t& q) {
+    const double a = double(2 * n - 1);
+    int64_t pp = (int64_t)floor((a - sqrt(fmax(a * a - 8.0 * double(k), 0.0))) * 0.5);
+    if (pp < 0) pp = 0;
+    while (pp > 0 && pp * (2 * n - pp - 1) / 2 > k) --pp;
+    while (pp < n - 2 && (pp + 1) * (2 * n - pp - 2) / 2 <= k) ++pp;
+    p = pp;
+    q = k - pp * (2 * n - pp - 1) / 2 + pp + 1;
+}
+
+// Embedded <ab||ef> rows of one ladder slab, straight from the assembly GEMM:
+//   W_ab,ef = GT[(b-gb0)V + f][(a-a0)V + e] - GT[(b-gb0)V + e][(a-a0)V + f],  e < f,
+// GT[(b,f)][(a,e)] = sum_L Bvv^L_ae Bvv^L_bf = <ab|ef>.  One task = one row
+// (a,b) and one 32x32 (e,f) tile pair with te <= tf; both GT blocks are read
+// along their contiguous (a,e) index and transposed through shared memory.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_embed_antisym(const cplx* __restrict__ GT, int64_t ldt, int64_t a0,
+                                                       int64_t gb0, int64_t prow0, int64_t nrows, int64_t V,
+                                                       int64_t pitch, void* __restrict__ out) {
+    __shared__ cplx t1[32][33];
+    __shared__ cplx t2[32][33];
+    const int64_t T = (V + 31) / 32, npair = T * (T + 1) / 2;
+    const int64_t tasks = nrows * npair;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const cplx zero = make_double2(0.0, 0.0);
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const int64_t row = t / npair;
+        int64_t rem = t - row * npair, te = 0;
+        while (rem >= T - te) {
+            rem -= T - te;
+            ++te;
+        }
+        const int64_t tf = te + rem;
+        int64_t a, b;
+        pair_of(prow0 + row, V, a, b);
+        const int64_t ra = (a - a0) * V, cb = (b - gb0) * V;
+        const int64_t e0 = te * 32, f0 = tf * 32;
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t f = f0 + j, e = e0 + tx;
+            t1[j][tx] = (f < V && e < V) ? GT[(cb + f) * ldt + ra + e] : zero;  // <ab|ef>, [f][e]
+            const int64_t e2 = e0 + j, f2 = f0 + tx;
+            t2[j][tx] = (e2 < V && f2 < V) ? GT[(cb + e2) * ldt + ra + f2] : zero;  // <ab|fe>, [e][f]
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t e = e0 + j, f = f0 + tx;
+            if (e < f && f < V) {
+                const cplx u = t1[tx][j], w = t2[j][tx];
+                const int64_t ef = e * (2 * V - e - 1) / 2 + (f - e - 1);
+                embed_store<KIND, false>(out, nrows, pitch, 0, row, ef, make_double2(u.x - w.x, u.y - w.y));
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -347,75 +532,148 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-void encode(CUtensorMap* map, void* base, int kind, uint64_t Kp, uint64_t rows, uint64_t batch, uint32_t box_rows) {
+void encode(CUtensorMap* map, const void* base, int kind, uint64_t kd, uint64_t pitch, uint64_t rows,
+            uint64_t batch, uint32_t box_rows) {
     CUtensorMapDataType dt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    uint64_t es = kind == 0 ? 2 : 4;
-    cuuint64_t dims[3] = {Kp, rows, batch};
-    cuuint64_t strides[2] = {Kp * es, Kp * rows * es};
+    const uint64_t es = kind == 0 ? 2 : 4;
+    cuuint64_t dims[3] = {kd, rows, batch};
+    cuuint64_t strides[2] = {pitch * es, pitch * rows * es};
     cuuint32_t box[3] = {(cuuint32_t)(ROWB / es), box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode_fn()(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = encode_fn()(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) throw LrccError(LRCC_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
 }
 
-bool g_attr_set[2] = {false, false};
+constexpr int stages_for(int bn) { return bn == 256 ? 4 : bn == 128 ? 6 : 8; }
+
+template <int KIND, int BN>
+void launch_tc(Dev& D, const CUtensorMap& ta, const CUtensorMap& tb, const Sched& sc, const Epi& ep, int grid,
+               int skip, uint32_t limit) {
+    constexpr int ST = stages_for(BN);
+    constexpr int SMEM = smem_bytes(BN, ST);
+    static_assert(SMEM <= 232448, "shared memory over the per-CTA limit");
+    static bool attr = false;
+    if (!attr) {
+        CK(cudaFuncSetAttribute(k_tc_gemm<KIND, BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+        attr = true;
+    }
+    k_tc_gemm<KIND, BN, ST><<<grid, 192, SMEM, D.st>>>(ta, tb, sc, ep, D.err_flag, skip, limit);
+}
+
+// accumulator tile width for n2 = 2N real output columns: the fewest padded
+// columns, with a small penalty on narrow tiles (more A re-reads per output)
+int bn_for(int64_t n2) {
+    static const int cand[4] = {256, 128, 64, 32};
+    static const double pen[4] = {1.0, 1.05, 1.15, 1.3};
+    int best = 256;
+    double bc = 1e300;
+    for (int i = 0; i < 4; ++i) {
+        double c = double((n2 + cand[i] - 1) / cand[i] * cand[i]) * pen[i];
+        if (c < bc) {
+            bc = c;
+            best = cand[i];
+        }
+    }
+    return best;
+}
+
+int64_t slots(int kind) { return kind == 0 ? 6 : 2; }
 
 }  // namespace
 
 bool gemm_tc_available() { return true; }
 
-size_t tc_embed_bytes(int prec, int64_t rows, int64_t K, int64_t batch, int64_t& rows_p, int64_t& Kp, bool is_b) {
+size_t tc_embed_bytes(int prec, int64_t rows, int64_t K, int64_t batch, int64_t& rows_e, int64_t& pitch, bool is_b) {
     const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
-    const int64_t S = kind == 0 ? 6 : 2, es = kind == 0 ? 2 : 4, kelem = ROWB / es;
-    Kp = (S * K + kelem - 1) / kelem * kelem;
-    rows_p = is_b ? (2 * rows + BN - 1) / BN * BN : (rows + BM - 1) / BM * BM;
-    return (size_t)(batch * rows_p * Kp * es);
+    const int64_t es = kind == 0 ? 2 : 4, q = 16 / es;
+    pitch = (slots(kind) * K + q - 1) / q * q;
+    rows_e = is_b ? 2 * rows : rows;
+    return (size_t)(batch * rows_e * pitch * es);
 }
 
 void tc_embed_a(Dev& D, int prec, const cplx* A, int64_t sAb, int64_t sAm, int64_t sAk, bool cA, int64_t batch,
-                int64_t M, int64_t K, int64_t Mp, int64_t Kp, void* out) {
-    if (prec == LRCC_MIXED_BF16X3)
-        k_embed_a<0><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, Mp, Kp, out);
-    else
-        k_embed_a<1><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, Mp, Kp, out);
+                int64_t M, int64_t K, int64_t pitch, void* out) {
+    if (batch * M * K == 0) return;
+    const bool tiled = sAm == 1 && sAk != 1;
+    const int64_t nt = batch * ((M + 31) / 32) * ((K + 31) / 32);
+    const int gt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)D.sm_count * 8));
+    if (prec == LRCC_MIXED_BF16X3) {
+        if (tiled) k_embed_t<0, false><<<gt, 256, 0, D.st>>>(A, sAb, sAk, cA, batch, M, K, M, pitch, out);
+        else k_embed<0, false><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, M, pitch, out);
+    } else {
+        if (tiled) k_embed_t<1, false><<<gt, 256, 0, D.st>>>(A, sAb, sAk, cA, batch, M, K, M, pitch, out);
+        else k_embed<1, false><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, M, pitch, out);
+    }
     LAUNCH_CHECK(D);
 }
 
 void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64_t sBn, bool cB, int64_t batch,
-                int64_t K, int64_t N, int64_t Np2, int64_t Kp, void* out) {
-    if (prec == LRCC_MIXED_BF16X3)
-        k_embed_b<0><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBk, sBn, cB, batch, K, N, Np2, Kp, out);
-    else
-        k_embed_b<1><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBk, sBn, cB, batch, K, N, Np2, Kp, out);
+                int64_t K, int64_t N, int64_t pitch, void* out) {
+    if (batch * N * K == 0) return;
+    const bool tiled = sBn == 1 && sBk != 1;
+    const int64_t nt = batch * ((N + 31) / 32) * ((K + 31) / 32);
+    const int gt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)D.sm_count * 8));
+    if (prec == LRCC_MIXED_BF16X3) {
+        if (tiled) k_embed_t<0, true><<<gt, 256, 0, D.st>>>(B, sBb, sBk, cB, batch, N, K, 2 * N, pitch, out);
+        else k_embed<0, true><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBn, sBk, cB, batch, N, K, 2 * N, pitch, out);
+    } else {
+        if (tiled) k_embed_t<1, true><<<gt, 256, 0, D.st>>>(B, sBb, sBk, cB, batch, N, K, 2 * N, pitch, out);
+        else k_embed<1, true><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBn, sBk, cB, batch, N, K, 2 * N, pitch, out);
+    }
     LAUNCH_CHECK(D);
 }
 
-// C = alpha * op(A' B'^T) + beta C on embedded operands A' [batch][Mp][Kp], B' [batch][Np2][Kp]
+// C = alpha * op(A' B'^T) + beta C on embedded operands A' [batch][M][pitch],
+// B' [batch][2N][pitch], complex K (S*K embedded columns)
 void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
-                      int64_t Mp, int64_t Np2, int64_t Kp, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
+                      int64_t K, int64_t pitch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
                       cplx beta, bool conj_acc, double useful_flops) {
     REQUIRE(D.err_flag != nullptr, "gemm_tc: no error word");
-    REQUIRE(batch <= 65535, "gemm_tc: batch too large");
+    if (M <= 0 || N <= 0 || batch <= 0) return;
     const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
-    const int64_t es = kind == 0 ? 2 : 4, kelem = ROWB / es;
+    const int64_t es = kind == 0 ? 2 : 4, kelem = ROWB / es, kd = slots(kind) * K;
+    REQUIRE(K > 0 && pitch >= kd && (pitch * es) % 16 == 0, "gemm_tc: bad embedded K");
+    REQUIRE(((uintptr_t)pa % 16) == 0 && ((uintptr_t)pb % 16) == 0, "gemm_tc: operands not 16-byte aligned");
+    const int bn = bn_for(2 * N);
     CUtensorMap ta, tb;
-    encode(&ta, const_cast<void*>(pa), kind, Kp, Mp, batch, BM);
-    encode(&tb, const_cast<void*>(pb), kind, Kp, Np2, batch, BN);
-    int tiles_n = (int)(Np2 / BN);
-    int64_t tiles = (Mp / BM) * tiles_n;
-    REQUIRE(tiles < INT32_MAX, "gemm_tc: too many tiles");
-    int num_kb = (int)(Kp / kelem);
-    // split K when the tile grid cannot fill the SMs
-    int64_t ctas = tiles * batch;
-    int splits = 1;
-    if (ctas < 2 * D.sm_count && num_kb >= 32)
-        splits = (int)std::min<int64_t>((2 * D.sm_count + ctas - 1) / ctas, num_kb / 16);
-    splits = std::max(1, std::min(splits, 256));
-    int kps = (num_kb + splits - 1) / splits;
-    splits = (num_kb + kps - 1) / kps;
-    Epi ep{M, N, C, sCb, sCm, sCn, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0, kps};
+    encode(&ta, pa, kind, (uint64_t)kd, (uint64_t)pitch, (uint64_t)M, (uint64_t)batch, BM);
+    encode(&tb, pb, kind, (uint64_t)kd, (uint64_t)pitch, (uint64_t)(2 * N), (uint64_t)batch, (uint32_t)bn);
+    const int64_t tiles_m = (M + BM - 1) / BM, tiles_n = (2 * N + bn - 1) / bn;
+    const int64_t tiles = tiles_m * tiles_n * batch;
+    REQUIRE(tiles_m < INT32_MAX && tiles_n < INT32_MAX && tiles < ((int64_t)1 << 40), "gemm_tc: too many tiles");
+    const int num_kb = (int)((kd + kelem - 1) / kelem);
+    // K splits: fewest estimated waves x (k-blocks per unit + per-unit overhead);
+    // split units add their partial tiles to C with FP64 atomics
+    const int64_t sm = D.sm_count;
+    static const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+    int splits = 1, kps = num_kb;
+    double best = 1e300;
+    for (int S : cand) {
+        if (S > 1 && num_kb / S < 8) break;
+        const int k1 = (num_kb + S - 1) / S;
+        const int se = (num_kb + k1 - 1) / k1;
+        const int64_t units = tiles * se;
+        const double waves = double((units + sm - 1) / sm);
+        const double cost = waves * (k1 + 3.0 + (se > 1 ? 4.0 * bn / 256.0 : 0.0));
+        if (cost < best * 0.97) {
+            best = cost;
+            splits = se;
+            kps = k1;
+        }
+    }
+    Sched sc;
+    sc.tiles_m = (int)tiles_m;
+    sc.tiles_n = (int)tiles_n;
+    sc.batch = (int)batch;
+    sc.splits = splits;
+    sc.kps = kps;
+    sc.num_kb = num_kb;
+    sc.group = (int)std::min<int64_t>(tiles_m, 16);
+    sc.units = (long long)tiles * splits;
+    REQUIRE(batch < INT32_MAX, "gemm_tc: batch too large");
+    Epi ep{M, N, C, sCb, sCm, sCn, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0};
     if (splits > 1) {
         GemmArgs pg{};
         pg.M = M; pg.N = N; pg.batch = batch; pg.C = C; pg.sCb = sCb; pg.sCm = sCm; pg.sCn = sCn; pg.beta = beta;
@@ -424,45 +682,69 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
     // host-side fault injection for the failure-detection test: the producer
     // skips its TMA issues so the consumers' bounded waits expire (short limit)
     const char* inj = getenv("LRCC_INJECT_TMA_SKIP");
-    int skip = (inj && inj[0] == '1') ? 1 : 0;
-    uint32_t limit = skip ? WAIT_LIMIT_INJECT : WAIT_LIMIT;
-    dim3 grid((unsigned)tiles, (unsigned)batch, (unsigned)splits);
+    const int skip = (inj && inj[0] == '1') ? 1 : 0;
+    const uint32_t limit = skip ? WAIT_LIMIT_INJECT : WAIT_LIMIT;
+    const int grid = (int)std::min<int64_t>(sc.units, sm);
     KTimer kt(D, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32", useful_flops,
-              (double)(batch * (Mp + Np2) * Kp * es) + 16.0 * M * N * batch, M, N, Kp, batch);
-    if (kind == 0) {
-        if (!g_attr_set[0]) {
-            CK(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-            g_attr_set[0] = true;
-        }
-        k_tc_gemm<0><<<grid, 128, SMEM_BYTES, D.st>>>(ta, tb, num_kb, tiles_n, ep, D.err_flag, skip, limit);
-    } else {
-        if (!g_attr_set[1]) {
-            CK(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-            g_attr_set[1] = true;
-        }
-        k_tc_gemm<1><<<grid, 128, SMEM_BYTES, D.st>>>(ta, tb, num_kb, tiles_n, ep, D.err_flag, skip, limit);
+              (double)(batch * (M + 2 * N) * kd * es) + 16.0 * M * N * batch, M, N, kd, batch);
+    switch (kind * 4 + (bn == 256 ? 0 : bn == 128 ? 1 : bn == 64 ? 2 : 3)) {
+        case 0: launch_tc<0, 256>(D, ta, tb, sc, ep, grid, skip, limit); break;
+        case 1: launch_tc<0, 128>(D, ta, tb, sc, ep, grid, skip, limit); break;
+        case 2: launch_tc<0, 64>(D, ta, tb, sc, ep, grid, skip, limit); break;
+        case 3: launch_tc<0, 32>(D, ta, tb, sc, ep, grid, skip, limit); break;
+        case 4: launch_tc<1, 256>(D, ta, tb, sc, ep, grid, skip, limit); break;
+        case 5: launch_tc<1, 128>(D, ta, tb, sc, ep, grid, skip, limit); break;
+        case 6: launch_tc<1, 64>(D, ta, tb, sc, ep, grid, skip, limit); break;
+        default: launch_tc<1, 32>(D, ta, tb, sc, ep, grid, skip, limit); break;
     }
     LAUNCH_CHECK(D);
 }
 
-void gemm_tc(Dev& D, const GemmArgs& g, int prec) {
-    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+// relative cost of running C[M][N] in this orientation: padded tensor-core
+// work, with a penalty when the epilogue's lanes (consecutive m) do not write
+// consecutive addresses
+static double orient_cost(int64_t M, int64_t N, int64_t sCm) {
+    const int bn = bn_for(2 * N);
+    const double pm = double((M + BM - 1) / BM * BM), pn = double((2 * N + bn - 1) / bn * bn);
+    return pm * pn * (sCm == 1 ? 1.0 : 1.15);
+}
+
+void gemm_tc(Dev& D, const GemmArgs& g0, int prec) {
+    if (g0.M <= 0 || g0.N <= 0 || g0.batch <= 0) return;
     REQUIRE(prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3, "gemm_tc: bad precision");
-    if (g.K <= 0) {
-        gemm_f64(D, g);  // pure beta scaling
+    if (g0.K <= 0) {
+        gemm_f64(D, g0);  // pure beta scaling
         return;
     }
-    int64_t Mp, Kp, Np2, Kp2;
-    size_t bytesA = tc_embed_bytes(prec, g.M, g.K, g.batch, Mp, Kp, false);
-    size_t bytesB = tc_embed_bytes(prec, g.N, g.K, g.batch, Np2, Kp2, true);
+    // C^T = B^T A^T: run the orientation with less padding / coalesced stores
+    GemmArgs g = g0;
+    if (orient_cost(g0.N, g0.M, g0.sCn) < orient_cost(g0.M, g0.N, g0.sCm)) {
+        g.M = g0.N; g.N = g0.M;
+        g.A = g0.B; g.sAb = g0.sBb; g.sAm = g0.sBn; g.sAk = g0.sBk; g.cA = g0.cB;
+        g.B = g0.A; g.sBb = g0.sAb; g.sBk = g0.sAk; g.sBn = g0.sAm; g.cB = g0.cA;
+        g.sCm = g0.sCn; g.sCn = g0.sCm;
+    }
+    int64_t rowsA, pitch, rowsB, pitch2;
+    size_t bytesA = tc_embed_bytes(prec, g.M, g.K, g.batch, rowsA, pitch, false);
+    size_t bytesB = tc_embed_bytes(prec, g.N, g.K, g.batch, rowsB, pitch2, true);
     void* pa = D.pool.get(bytesA);
     std::shared_ptr<DevBuf> ha(new DevBuf{&D.pool, pa, bytesA});
     void* pb = D.pool.get(bytesB);
     std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
-    CK(cudaMemsetAsync(pa, 0, bytesA, D.st));
-    CK(cudaMemsetAsync(pb, 0, bytesB, D.st));
-    tc_embed_a(D, prec, g.A, g.sAb, g.sAm, g.sAk, g.cA, g.batch, g.M, g.K, Mp, Kp, pa);
-    tc_embed_b(D, prec, g.B, g.sBb, g.sBk, g.sBn, g.cB, g.batch, g.K, g.N, Np2, Kp, pb);
-    tc_gemm_embedded(D, prec, pa, pb, g.batch, g.M, g.N, Mp, Np2, Kp, g.C, g.sCb, g.sCm, g.sCn, g.alpha, g.beta,
+    tc_embed_a(D, prec, g.A, g.sAb, g.sAm, g.sAk, g.cA, g.batch, g.M, g.K, pitch, pa);
+    tc_embed_b(D, prec, g.B, g.sBb, g.sBk, g.sBn, g.cB, g.batch, g.K, g.N, pitch, pb);
+    tc_gemm_embedded(D, prec, pa, pb, g.batch, g.M, g.N, g.K, pitch, g.C, g.sCb, g.sCm, g.sCn, g.alpha, g.beta,
                      false, 8.0 * g.M * g.N * g.K * g.batch);
+}
+
+void tc_embed_antisym_slab(Dev& D, int prec, const cplx* GT, int64_t ldt, int64_t a0, int64_t gb0, int64_t prow0,
+                           int64_t nrows, int64_t V, int64_t pitch, void* out) {
+    const int64_t T = (V + 31) / 32, tasks = nrows * T * (T + 1) / 2;
+    if (tasks <= 0) return;
+    const int grid = (int)std::min<int64_t>(tasks, (int64_t)D.sm_count * 8);
+    if (prec == LRCC_MIXED_BF16X3)
+        k_embed_antisym<0><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, pitch, out);
+    else
+        k_embed_antisym<1><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, pitch, out);
+    LAUNCH_CHECK(D);
 }

@@ -44,6 +44,16 @@ Tensor dev_copy_c(Dev& D, const double* host, std::vector<int64_t> shape) {
     return t;
 }
 
+// the virtual-virtual block of B, the only integrals the ladder reads
+void ensure_bvv(lrcc_ctx* c) {
+    if (c->lad.Bvv.p) return;
+    Dev& D = c->D;
+    const int O = c->O, V = c->V;
+    c->lad.Bvv = empty(D, {(int64_t)c->L, (int64_t)V, (int64_t)V});
+    axpby(D, mkc(1.0), c->B.slice(1, O, V).slice(2, O, V), false, mkc(0.0), c->lad.Bvv);
+    c->lad.slab_rows = c->opt.slab_rows;
+}
+
 void build_ham_impl(lrcc_ctx* c) {
     Dev& D = c->D;
     int O = c->O, V = c->V;
@@ -75,9 +85,7 @@ void build_ham_impl(lrcc_ctx* c) {
     H.ovvv = anti_block(D, B, 0, O, O, V, O, V, O, V);
     H.vovv = anti_block(D, B, O, V, 0, O, O, V, O, V);
     H.vvvo = anti_block(D, B, O, V, O, V, O, V, 0, O);
-    c->lad.Bvv = empty(D, {(int64_t)c->L, (int64_t)V, (int64_t)V});
-    axpby(D, mkc(1.0), B.slice(1, O, V).slice(2, O, V), false, mkc(0.0), c->lad.Bvv);
-    c->lad.slab_rows = c->opt.slab_rows;
+    ensure_bvv(c);
     c->Hmu.clear();
     for (int k = 0; k < c->ncomp; ++k) {
         Ham h;
@@ -887,6 +895,32 @@ lrcc_status lrcc_ladder_dev(lrcc_ctx* c, const double* x, double* z, int R, int 
         Tensor X = wrap((cplx*)x, {R, c->O, c->O, c->V, c->V});
         Tensor Z = wrap((cplx*)z, {R, c->O, c->O, c->V, c->V});
         ladder(c->D, c->lad, X, mkc(1.0), mkc(0.0), Z, transpose != 0, prec);
+        check_device_error(c->D);
+        CK(cudaEventRecord(ev, c->D.st));
+        CK(cudaStreamWaitEvent(st, ev, 0));
+        CK(cudaEventDestroy(ev));
+        return LRCC_OK;
+    } catch (const LrccError& e) {
+        return fail(c, e);
+    } catch (const std::exception& e) {
+        c->err = e.what();
+        return LRCC_ECUDA;
+    }
+}
+
+lrcc_status lrcc_ladder_packed_dev(lrcc_ctx* c, const double* xt, double* zt, int64_t ncol, int transpose, int prec,
+                                   void* stream) {
+    if (!c) return LRCC_EINVAL;
+    try {
+        REQUIRE(xt && zt && ncol >= 1, "bad ladder arguments");
+        REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_MIXED_BF16X3, "bad precision");
+        ensure_bvv(c);
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, st));
+        CK(cudaStreamWaitEvent(c->D.st, ev, 0));
+        ladder_packed(c->D, c->lad, (const cplx*)xt, (cplx*)zt, ncol, transpose != 0, prec);
         check_device_error(c->D);
         CK(cudaEventRecord(ev, c->D.st));
         CK(cudaStreamWaitEvent(st, ev, 0));

@@ -200,15 +200,17 @@ void gemm_prescale(Dev& D, const GemmArgs& g);
 // tensor-core split-precision GEMM (gemm_tc.cu); prec = LRCC_MIXED_*
 bool gemm_tc_available();
 void gemm_tc(Dev& D, const GemmArgs& g, int prec);
-// pieces: embedded-operand sizes (rows padded to the tile, K to 128 bytes),
-// the split/convert kernels, and the GEMM on already embedded operands
-size_t tc_embed_bytes(int prec, int64_t rows, int64_t K, int64_t batch, int64_t& rows_p, int64_t& Kp, bool is_b);
+// pieces: embedded-operand layout [batch][rows_e][pitch] (rows_e = rows for
+// A, 2 rows for B; pitch = S K rounded up to 16 bytes; nothing outside S K
+// columns is written or read), the split/convert kernels, and the GEMM on
+// already embedded operands (complex K)
+size_t tc_embed_bytes(int prec, int64_t rows, int64_t K, int64_t batch, int64_t& rows_e, int64_t& pitch, bool is_b);
 void tc_embed_a(Dev& D, int prec, const cplx* A, int64_t sAb, int64_t sAm, int64_t sAk, bool cA, int64_t batch,
-                int64_t M, int64_t K, int64_t Mp, int64_t Kp, void* out);
+                int64_t M, int64_t K, int64_t pitch, void* out);
 void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64_t sBn, bool cB, int64_t batch,
-                int64_t K, int64_t N, int64_t Np2, int64_t Kp, void* out);
+                int64_t K, int64_t N, int64_t pitch, void* out);
 void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
-                      int64_t Mp, int64_t Np2, int64_t Kp, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
+                      int64_t K, int64_t pitch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
                       cplx beta, bool conj_acc, double useful_flops);
 
 // ---------------------------------------------------------------------------
@@ -228,18 +230,29 @@ void perm_axpby(Dev& D, const std::string& spec, cplx alpha, const Tensor& x, cp
 // <ab|ef> = sum_L Bvv^L_ae Bvv^L_bf; transpose -> Bvv conjugated.
 struct LadderCtx {
     Tensor Bvv;      // [L][V][V]
-    int slab_rows = 0;
-    // cached embedded <ab||ef> matrix W' [Mp][Kp] (rows a<b, K = pairs e<f) for
-    // one mixed precision, built on first use when it fits in device memory
+    int slab_rows = 0;  // > 0: no <ab||ef> cache; assemble per call in slabs of this many rows
+    // cached embedded <ab||ef> matrix W' [P_V][pitch] (rows a<b, K = pairs e<f)
+    // for one mixed precision, built on first use when it fits in device memory
     std::shared_ptr<DevBuf> wcache;
     int wcache_prec = -1;
-    int64_t w_Mp = 0, w_Kp = 0;
+    int64_t w_pitch = 0;
     bool wcache_disabled = false;
+    // embedded Bvv as the B operand (n = (b,f), k = L) of the slab assembly
+    std::shared_ptr<DevBuf> bcache;
+    int bcache_prec = -1;
+    int64_t b_pitch = 0;
     // cached FP64 <ab||ef> matrix [P_V][P_V] for the FP64 ladder, when it fits
     Tensor w64;
     bool w64_disabled = false;
 };
 void ladder(Dev& D, LadderCtx& L, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose, int prec);
+// packed form: Zt[n][ab] = sum_{e<f} <ab||ef> Xt[n][ef] (transpose: conj <ab||ef>),
+// Xt, Zt [ncol][P_V] (pair order a<b row-major), Zt overwritten
+void ladder_packed(Dev& D, LadderCtx& L, const cplx* Xt, cplx* Zt, int64_t ncol, bool transpose, int prec);
+// embedded <ab||ef> rows of one slab from GT[(b,f)][(a,e)] (leading dimension ldt),
+// rows (a,b) = pair(prow0 + row), written as A operand rows [nrows][pitch]
+void tc_embed_antisym_slab(Dev& D, int prec, const cplx* GT, int64_t ldt, int64_t a0, int64_t gb0, int64_t prow0,
+                           int64_t nrows, int64_t V, int64_t pitch, void* out);
 
 // pair index of (p<q) among n, row-major strict upper triangle
 __host__ __device__ inline int64_t pair_index(int64_t p, int64_t q, int64_t n) {

@@ -57,6 +57,7 @@ SIGNATURES = [
     ("lrcc_residual_dev", ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          _vp, _vp]),
     ("lrcc_ladder_dev", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
+    ("lrcc_ladder_packed_dev", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _vp]),
     ("lrcc_phase_times", ctypes.c_int, [_vp, _dp]),
     ("lrcc_kernel_launches", ctypes.c_int64, [_vp]),
     ("lrcc_profile", ctypes.c_int, [_vp, ctypes.c_int]),
@@ -235,6 +236,19 @@ def lrcc_ladder_dev(ctx: Context, x, transpose: bool = False, prec: int = LRCC_F
     ctx.check(library().lrcc_ladder_dev(ctx.h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(z.data_ptr()),
                                         x.shape[0], int(transpose), prec, _stream_ptr()))
     return z
+
+
+def lrcc_ladder_packed_dev(ctx: Context, xt, transpose: bool = False, prec: int = LRCC_FP64, out=None):
+    """xt: torch.complex128 CUDA [ncol, P_V] (pairs e<f) -> Zt [ncol, P_V],
+    Zt[n][ab] = sum_{e<f} <ab||ef> Xt[n][ef]."""
+    import torch
+    xt = xt.resolve_conj().contiguous()
+    assert xt.is_cuda and xt.dtype == torch.complex128 and xt.dim() == 2
+    zt = torch.empty_like(xt) if out is None else out
+    ctx.check(library().lrcc_ladder_packed_dev(ctx.h, ctypes.c_void_p(xt.data_ptr()),
+                                               ctypes.c_void_p(zt.data_ptr()), xt.shape[0], int(transpose), prec,
+                                               _stream_ptr()))
+    return zt
 
 
 def lrcc_ladder_noalloc(bvv, x, transpose: bool = False, out=None):
