@@ -189,6 +189,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--fns", action="store_true",
                     help="FNS++ workload: truncate to the config's 'keep' virtuals, then ground state and alpha")
+    ap.add_argument("--profile-csv", default=None,
+                    help="write every timed GEMM launch (kernel, M, N, K, batch, ms, flops) to this CSV file")
     ap.add_argument("--ladder-only", action="store_true",
                     help="time only the particle-particle ladder (no ground state); used for kernel profiling")
     args = ap.parse_args()
@@ -271,6 +273,8 @@ def main():
     if pg:
         pg.barrier()
     L.lrcc_profile(ctx, False)
+    if args.profile_csv:
+        L.lrcc_profile_dump(ctx, args.profile_csv)
     ms = [a.elapsed_time(b) for a, b in ev]
     launches = (L.lrcc_kernel_launches(ctx) - launches0) // args.steps
     stats = L.lrcc_kernel_stats(ctx)
@@ -392,39 +396,53 @@ def fns_run(args, L, ctx, cfg, rank):
 
 
 def ladder_only(args, L, ctx, O, V, Lx, R, prec, world, rank, local, pg):
-    """The particle-particle ladder alone on R right-hand sides of the workload."""
+    """The particle-particle ladder alone on R right-hand sides of the workload,
+    on packed amplitudes (lrcc_ladder_packed_dev: only B_vv is read, so the
+    largest virtual spaces fit).  <ab||ef> is cached when it fits in a third of
+    the free memory, else assembled per call in slabs (counted in F_ladder)."""
     import torch
     dev = torch.device("cuda", local)
+    po, pv = O * (O - 1) // 2, V * (V - 1) // 2
     g = torch.Generator(device=dev).manual_seed(7 + rank)
-    x = torch.randn(R, O, O, V, V, dtype=torch.complex128, device=dev, generator=g)
-    x = x - x.transpose(1, 2)
-    x = x - x.transpose(3, 4)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    xt = torch.randn(R * po, pv, dtype=torch.complex128, device=dev, generator=g)
+    zt = torch.empty_like(xt)
     for _ in range(max(1, args.warmup)):
-        L.lrcc_ladder_dev(ctx, x, prec=prec)
+        L.lrcc_ladder_packed_dev(ctx, xt, prec=prec, out=zt)
     torch.cuda.synchronize()
     L.lrcc_profile(ctx, True)
+    clocks = Clocks()
+    clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.nvtx.range_push("timed")
     for k in range(args.steps):
-        flush.zero_()
         ev[k][0].record()
-        L.lrcc_ladder_dev(ctx, x, prec=prec)
+        L.lrcc_ladder_packed_dev(ctx, xt, prec=prec, out=zt)
         ev[k][1].record()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
+    clk = clocks.stop()
     L.lrcc_profile(ctx, False)
+    if args.profile_csv:
+        L.lrcc_profile_dump(ctx, args.profile_csv)
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    po, pv = O * (O - 1) // 2, V * (V - 1) // 2
     F = 8.0 * (R * po * pv * pv + pv * pv * Lx)
     stats = L.lrcc_kernel_stats(ctx)
+    hbm, bf16, bf16s, src = load_peaks()
+    # a ladder call runs for seconds at the large workloads: the sustained bf16 peak
+    peak = {"bf16x3": bf16s / 3.0, "tf32": bf16s / 2.0}.get(args.prec)
     if rank == 0:
-        print(json.dumps({"metric": "ladder TFLOP/s (nominal F_ladder)", "value": world * F / (ms / 1e3) / 1e12,
-                          "unit": "TFLOP/s", "ms_per_step": ms, "steps": args.steps, "workload": args.workload,
-                          "O": O, "V": V, "L": Lx, "R": R, "precision": args.prec,
-                          "kernels": {k: {"count": v["count"], "ms": v["ms"],
-                                          "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9} for k, v in stats.items()}}),
-              flush=True)
+        line = {"metric": "ladder TFLOP/s (nominal F_ladder)", "value": world * F / (ms / 1e3) / 1e12,
+                "unit": "TFLOP/s", "ms_per_step": ms, "steps": args.steps, "workload": args.workload,
+                "O": O, "V": V, "L": Lx, "R": R, "ncol": R * po, "precision": args.prec, "clocks": clk,
+                "F_ladder": F,
+                "kernels": {k: {"count": v["count"], "ms": v["ms"] / args.steps,
+                                "tflops": v["flops"] / max(v["ms"], 1e-9) / 1e9} for k, v in stats.items()}}
+        if peak:
+            line["frac_of_peak"] = line["value"] / peak
+            line["peak"] = {"value": peak, "unit": "TFLOP/s",
+                            "note": f"bf16 {src} sustained peak / {3 if args.prec == 'bf16x3' else 2} "
+                                    "(useful complex flops, 8 per CMAC)"}
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -320,36 +320,62 @@ __global__ void k_unpack_z(const cplx* __restrict__ Zp, cplx* __restrict__ Z, in
 }
 
 // packed layouts of the batched paths: Xt[n][ef], Zt[n][ab], n = r*PO + ij
-// Xt[n][ef] = 1/2 (X[r][i][j][e][f] - X[r][i][j][f][e]),  i<j, e<f
-__global__ void k_pack_xt(const cplx* __restrict__ X, cplx* __restrict__ Xt, int64_t R, int64_t O, int64_t V) {
-    int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
-    int64_t total = R * PO * PV;
+// index (r, i, j, a, b) of a contiguous [R][O][O][V][V] element
+__device__ __forceinline__ void decode5(int64_t idx, int64_t O, int64_t V, const FastDiv& fO, const FastDiv& fV,
+                                        bool fast, int64_t& r, int64_t& i, int64_t& j, int64_t& a, int64_t& b) {
+    if (fast) {
+        uint32_t u = (uint32_t)idx, q = fV.div(u);
+        b = u - q * fV.d;
+        u = q;
+        q = fV.div(u);
+        a = u - q * fV.d;
+        u = q;
+        q = fO.div(u);
+        j = u - q * fO.d;
+        u = q;
+        q = fO.div(u);
+        i = u - q * fO.d;
+        r = q;
+        return;
+    }
+    b = idx % V;
+    int64_t t = idx / V;
+    a = t % V;
+    t /= V;
+    j = t % O;
+    t /= O;
+    i = t % O;
+    r = t / O;
+}
+
+// Xt[r*PO + ij][ef] = 1/2 (X[r][i][j][e][f] - X[r][i][j][f][e]),  i<j, e<f
+// (threads run over the full array, so the first read is contiguous)
+__global__ void k_pack_xt(const cplx* __restrict__ X, cplx* __restrict__ Xt, int64_t R, int64_t O, int64_t V,
+                          FastDiv fO, FastDiv fV) {
+    const int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
+    const int64_t total = R * O * O * V * V;
+    const bool fast = total < FAST_INDEX_LIMIT;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t ef = idx % PV, n = idx / PV;
-        int64_t r = n / PO, ij = n % PO;
-        int64_t e, f, i, j;
-        pair_decode(ef, V, e, f);
-        pair_decode(ij, O, i, j);
-        const cplx* x = X + ((r * O + i) * O + j) * V * V;
-        cplx u = x[e * V + f], w = x[f * V + e];
-        Xt[idx] = make_double2(0.5 * (u.x - w.x), 0.5 * (u.y - w.y));
+        int64_t r, i, j, e, f;
+        decode5(idx, O, V, fO, fV, fast, r, i, j, e, f);
+        if (i >= j || e >= f) continue;
+        const cplx u = X[idx], w = X[idx + (f - e) * (V - 1)];  // [e][f] -> [f][e]
+        Xt[(r * PO + pair_index(i, j, O)) * PV + pair_index(e, f, V)] =
+            make_double2(0.5 * (u.x - w.x), 0.5 * (u.y - w.y));
     }
 }
 
 // Z[r][i][j][a][b] = alpha * sign * Zt[r*PO + ij][ab] + beta * Z
 __global__ void k_unpack_zt(const cplx* __restrict__ Zt, cplx* __restrict__ Z, int64_t R, int64_t O, int64_t V,
-                            cplx alpha, cplx beta, int beta0) {
+                            FastDiv fO, FastDiv fV, cplx alpha, cplx beta, int beta0) {
     int64_t PO = O * (O - 1) / 2, PV = V * (V - 1) / 2;
     int64_t total = R * O * O * V * V;
+    const bool fast = total < FAST_INDEX_LIMIT;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t b = idx % V, t = idx / V;
-        int64_t a = t % V;
-        t /= V;
-        int64_t j = t % O;
-        t /= O;
-        int64_t i = t % O, r = t / O;
+        int64_t r, i, j, a, b;
+        decode5(idx, O, V, fO, fV, fast, r, i, j, a, b);
         cplx v = make_double2(0.0, 0.0);
         if (i != j && a != b) {
             double sg = 1.0;
@@ -430,11 +456,55 @@ static std::vector<Slab> plan_slabs(int64_t V, int64_t budget_el, int64_t row_ca
     return out;
 }
 
-static int64_t slab_budget_el(Dev& D) {
+static double free_bytes(Dev& D) {
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
-    double bytes = std::min(0.3 * double(fr + D.pool.cached), 24.0 * (1 << 30));
-    return std::max<int64_t>(1 << 20, (int64_t)(std::max(bytes, double(1 << 30)) / 16));
+    return double(fr + D.pool.cached);
+}
+
+// GT elements of one assembly chunk (a staging buffer: a modest share of memory)
+static int64_t slab_budget_el(Dev& D, double share = 0.12, double cap = 6.0 * (1 << 30)) {
+    double bytes = std::min(share * free_bytes(D), cap);
+    return std::max<int64_t>(1 << 20, (int64_t)(std::max(bytes, double(1 << 26)) / 16));
+}
+
+// Consecutive assembly chunks form one contraction group (one GEMM of
+// nrows x ncol x P_V); rows are contiguous in the pair order across chunks.
+struct SlabGroup {
+    int64_t prow0, nrows;
+    size_t c0, c1;  // chunks [c0, c1) of the plan
+};
+
+static std::vector<SlabGroup> group_chunks(const std::vector<Slab>& plan, int64_t cap_rows) {
+    std::vector<SlabGroup> out;
+    for (size_t c = 0; c < plan.size(); ++c) {
+        if (!out.empty() && out.back().nrows + plan[c].nrows <= cap_rows) {
+            out.back().nrows += plan[c].nrows;
+            out.back().c1 = c + 1;
+        } else {
+            out.push_back(SlabGroup{plan[c].prow0, plan[c].nrows, c, c + 1});
+        }
+    }
+    return out;
+}
+
+// rows per contraction group: the most 128-row M tiles that fit in w_bytes of
+// W rows (row_bytes each), among counts whose tile grid (x tiles_n) fills
+// whole waves of the SMs best
+static int64_t group_rows(Dev& D, double w_bytes, double row_bytes, int64_t ncol) {
+    const int64_t kmax = std::max<int64_t>(1, (int64_t)(w_bytes / row_bytes) / 128);
+    const int64_t tn = std::max<int64_t>(1, (2 * ncol + 255) / 256), sm = D.sm_count;
+    int64_t best = kmax;
+    double be = -1.0;
+    for (int64_t k = kmax; k >= std::max<int64_t>(1, kmax / 2); --k) {
+        const int64_t t = k * tn;
+        const double eff = double(t) / double((t + sm - 1) / sm * sm);
+        if (eff > be + 1e-3) {
+            be = eff;
+            best = k;
+        }
+    }
+    return 128 * best;
 }
 
 // embedded B operand of the slab GEMMs: n = (b,f), k = L (built once per precision)
@@ -467,12 +537,6 @@ struct SlabScratch {
         gt = gt_buf.p;
     }
 };
-
-static int64_t max_rows(const std::vector<Slab>& plan) {
-    int64_t m = 0;
-    for (const Slab& sl : plan) m = std::max(m, sl.nrows);
-    return m;
-}
 
 static void assemble_slab(Dev& D, LadderCtx& LC, const Slab& sl, int prec, bool conj, cplx* W, void* Wemb,
                           int64_t pitch_w, SlabScratch& sc) {
@@ -579,13 +643,20 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
             return;
         }
         const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), LC.slab_rows);
+        const int64_t cap = LC.slab_rows > 0 ? 3 * LC.slab_rows
+                                             : group_rows(D, 0.25 * free_bytes(D), 16.0 * PV, ncol);
+        const std::vector<SlabGroup> groups = group_chunks(plan, cap);
         SlabScratch sc(D, plan, V);
-        Tensor W = empty(D, {max_rows(plan), PV});
-        for (const Slab& sl : plan) {
-            assemble_slab(D, LC, sl, LRCC_FP64, transpose, W.p, nullptr, 0, sc);
-            g2.M = sl.nrows; g2.K = PV;
+        int64_t wrows = 0;
+        for (const SlabGroup& gr : groups) wrows = std::max(wrows, gr.nrows);
+        Tensor W = empty(D, {wrows, PV});
+        for (const SlabGroup& gr : groups) {
+            for (size_t c = gr.c0; c < gr.c1; ++c)
+                assemble_slab(D, LC, plan[c], LRCC_FP64, transpose, W.p + (plan[c].prow0 - gr.prow0) * PV, nullptr, 0,
+                              sc);
+            g2.M = gr.nrows; g2.K = PV;
             g2.A = W.p; g2.sAb = 0; g2.sAm = PV; g2.sAk = 1; g2.cA = false;
-            g2.C = Zt + sl.prow0;
+            g2.C = Zt + gr.prow0;
             gemm_f64(D, g2);
         }
         return;
@@ -605,14 +676,21 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
     const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
     ensure_bcache(D, LC, prec);
     const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), LC.slab_rows);
+    const int64_t cap = LC.slab_rows > 0 ? 3 * LC.slab_rows
+                                         : group_rows(D, 0.25 * free_bytes(D), double(pitch * es), ncol);
+    const std::vector<SlabGroup> groups = group_chunks(plan, cap);
     SlabScratch sc(D, plan, V);
-    const size_t wb = (size_t)(max_rows(plan) * pitch * es);
+    int64_t wrows = 0;
+    for (const SlabGroup& gr : groups) wrows = std::max(wrows, gr.nrows);
+    const size_t wb = (size_t)(wrows * pitch * es);
     void* pw = D.pool.get(wb);
     std::shared_ptr<DevBuf> hw(new DevBuf{&D.pool, pw, wb});
-    for (const Slab& sl : plan) {
-        assemble_slab(D, LC, sl, prec, false, nullptr, pw, pitch, sc);
-        tc_gemm_embedded(D, prec, pw, pb, 1, sl.nrows, ncol, PV, pitch, Zt + sl.prow0, 0, 1, PV, mkc(1.0),
-                         mkc(0.0), transpose, 8.0 * sl.nrows * PV * ncol);
+    for (const SlabGroup& gr : groups) {
+        for (size_t c = gr.c0; c < gr.c1; ++c)
+            assemble_slab(D, LC, plan[c], prec, false, nullptr,
+                          (char*)pw + (size_t)((plan[c].prow0 - gr.prow0) * pitch * es), pitch, sc);
+        tc_gemm_embedded(D, prec, pw, pb, 1, gr.nrows, ncol, PV, pitch, Zt + gr.prow0, 0, 1, PV, mkc(1.0),
+                         mkc(0.0), transpose, 8.0 * gr.nrows * PV * ncol);
     }
 }
 
@@ -628,11 +706,12 @@ void ladder(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tenso
         return;
     }
     Tensor Xt = empty(D, {R * PO, PV});
-    k_pack_xt<<<grid_n(D, R * PO * PV), 256, 0, D.st>>>(X.p, Xt.p, R, O, V);
+    k_pack_xt<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(X.p, Xt.p, R, O, V, FastDiv(O), FastDiv(V));
     LAUNCH_CHECK(D);
     Tensor Zt = empty(D, {R * PO, PV});
     ladder_packed(D, LC, Xt.p, Zt.p, R * PO, transpose, prec);
-    k_unpack_zt<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zt.p, Z.p, R, O, V, alpha, beta, beta0);
+    k_unpack_zt<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zt.p, Z.p, R, O, V, FastDiv(O), FastDiv(V), alpha,
+                                                               beta, beta0);
     LAUNCH_CHECK(D);
 }
 

@@ -142,6 +142,16 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
     }
 
     cplx* C = g.C + b * g.sCb;
+    // old C values first (all loads in flight together), then the stores
+    const bool rd = !g.atomic && (g.beta.x != 0.0 || g.beta.y != 0.0);
+    cplx old[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            old[i][j] = (rd && m < g.M && n < g.N) ? C[m * g.sCm + n * g.sCn] : make_double2(0.0, 0.0);
+        }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         int64_t m = m0 + ty + 16 * i;
@@ -157,11 +167,9 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
                 atomicAdd(&c->x, r.x);
                 atomicAdd(&c->y, r.y);
             } else {
-                if (g.beta.x != 0.0 || g.beta.y != 0.0) {
-                    cplx o = *c;
-                    r.x += g.beta.x * o.x - g.beta.y * o.y;
-                    r.y += g.beta.x * o.y + g.beta.y * o.x;
-                }
+                const cplx o = old[i][j];
+                r.x += g.beta.x * o.x - g.beta.y * o.y;
+                r.y += g.beta.x * o.y + g.beta.y * o.x;
                 *c = r;
             }
         }
@@ -211,6 +219,11 @@ __global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
     }
     if (m >= g.M) return;
     cplx* C = g.C + b * g.sCb;
+    const bool rd = !g.atomic && (g.beta.x != 0.0 || g.beta.y != 0.0);
+    cplx old[NMAX];
+#pragma unroll
+    for (int n = 0; n < NMAX; ++n)
+        old[n] = (rd && n < N) ? C[m * g.sCm + n * g.sCn] : make_double2(0.0, 0.0);
 #pragma unroll
     for (int n = 0; n < NMAX; ++n) {
         if (n >= N) break;
@@ -222,11 +235,9 @@ __global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
             atomicAdd(&c->y, r.y);
             continue;
         }
-        if (g.beta.x != 0.0 || g.beta.y != 0.0) {
-            cplx o = *c;
-            r.x += g.beta.x * o.x - g.beta.y * o.y;
-            r.y += g.beta.x * o.y + g.beta.y * o.x;
-        }
+        const cplx o = old[n];
+        r.x += g.beta.x * o.x - g.beta.y * o.y;
+        r.y += g.beta.x * o.y + g.beta.y * o.x;
         *c = r;
     }
 }

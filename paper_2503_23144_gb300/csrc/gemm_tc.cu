@@ -38,6 +38,10 @@ constexpr int ROWB = 128;                 // bytes of K per row per stage
 constexpr int A_STAGE = BM * ROWB;        // 16 KB
 constexpr int smem_bytes(int bn, int stages) { return stages * (A_STAGE + bn * ROWB) + 1024 + 256; }
 constexpr uint32_t WAIT_LIMIT = 1u << 25;  // polls (with backoff) before giving up
+// k-blocks (of 128 bytes of K per row, 4 MMAs each) summed in one FP32 TMEM
+// accumulator; longer K ranges are added chunk by chunk into C in FP64, so
+// the FP32 accumulation error does not grow with the full contraction length
+constexpr int KCHUNK = 128;
 constexpr uint32_t WAIT_LIMIT_INJECT = 1u << 14;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -146,6 +150,7 @@ struct Epi {
 // the M tile fastest, so CTAs resident together share the B tiles they read.
 struct Sched {
     int tiles_m, tiles_n, batch, splits, kps, num_kb, group;
+    int kchunk;  // k-blocks accumulated in FP32 before the epilogue adds them to C in FP64
     long long units;
 };
 
@@ -266,31 +271,38 @@ __global__ void __launch_bounds__(192, 1)
             for (long long u = blockIdx.x; ok && u < sc.units; u += gridDim.x) {
                 int tm, tn, bz, kb0, kb1;
                 unit_coords(sc, u, tm, tn, bz, kb0, kb1);
-                const int acc = ti & 1;
-                if (!mbar_wait(&acce[acc], ((uint32_t)(ti >> 1) & 1u) ^ 1u, err, wait_limit)) break;
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(acc * BN);
-                for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                    if (!mbar_wait(&full[s], ph, err, wait_limit)) {
+                // the unit's K range in chunks, each into the next accumulator
+                for (int c0 = kb0; ok && c0 < kb1; c0 += sc.kchunk) {
+                    const int c1 = min(kb1, c0 + sc.kchunk);
+                    const int acc = ti & 1;
+                    if (!mbar_wait(&acce[acc], ((uint32_t)(ti >> 1) & 1u) ^ 1u, err, wait_limit)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t ad = smem_desc(su32(sA + s * A_STAGE));
-                    const uint64_t bd = smem_desc(su32(sB + s * B_STAGE));
+                    const uint32_t d = tmem + (uint32_t)(acc * BN);
+                    for (int kb = c0; kb < c1; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                        if (!mbar_wait(&full[s], ph, err, wait_limit)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t ad = smem_desc(su32(sA + s * A_STAGE));
+                        const uint64_t bd = smem_desc(su32(sB + s * B_STAGE));
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        // 32 bytes of K per MMA (16 bf16 or 8 tf32): +2 in the >>4 address field
-                        mma<KIND>(d, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), IDESC,
-                                  (kb > kb0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            // 32 bytes of K per MMA (16 bf16 or 8 tf32): +2 in the >>4 address field
+                            mma<KIND>(d, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), IDESC,
+                                      (kb > c0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(&empty[s]);
                     }
-                    mma_commit(&empty[s]);
+                    if (!ok) break;
+                    mma_commit(&accf[acc]);
+                    ++ti;
                 }
-                if (!ok) break;
-                mma_commit(&accf[acc]);
-                ++ti;
             }
             mma_commit(done);
         }
@@ -299,46 +311,63 @@ __global__ void __launch_bounds__(192, 1)
         const int q = warp & 3;
         const bool beta0 = ep.beta.x == 0.0 && ep.beta.y == 0.0;
         int ti = 0;
-        for (long long u = blockIdx.x; u < sc.units; u += gridDim.x) {
+        bool ok = true;
+        for (long long u = blockIdx.x; ok && u < sc.units; u += gridDim.x) {
             int tm, tn, bz, kb0, kb1;
             unit_coords(sc, u, tm, tn, bz, kb0, kb1);
-            const int acc = ti & 1;
-            if (!warp_wait(&accf[acc], (uint32_t)(ti >> 1) & 1u, err, wait_limit)) break;
-            tc_fence_after();
-            const int64_t m = (int64_t)tm * BM + q * 32 + lane;
-            cplx* Cb = ep.C + (int64_t)bz * ep.sCb;
+            for (int c0 = kb0; c0 < kb1; c0 += sc.kchunk) {
+                // first chunk: C = alpha acc + beta C; later chunks: C += alpha acc
+                const bool first = c0 == kb0;
+                const bool rd = !ep.atomic && (!first || !beta0);
+                const cplx bc = first ? ep.beta : make_double2(1.0, 0.0);
+                const int acc = ti & 1;
+                if (!warp_wait(&accf[acc], (uint32_t)(ti >> 1) & 1u, err, wait_limit)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int64_t m = (int64_t)tm * BM + q * 32 + lane;
+                const bool live = m < ep.M;
+                cplx* Cb = ep.C + (int64_t)bz * ep.sCb;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32), r);
-                if (kb1 > kb0 && m < ep.M) {
+                for (int c = 0; c < BN / 32; ++c) {
+                    uint32_t r[32];
+                    const int64_t n0 = (int64_t)tn * (BN / 2) + c * 16;
+                    // old C values are loaded before the TMEM read, all in flight together
+                    cplx old[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int64_t n = (int64_t)tn * (BN / 2) + c * 16 + j;
-                        if (n < ep.N) {
-                            double re = (double)__uint_as_float(r[2 * j]), im = (double)__uint_as_float(r[2 * j + 1]);
-                            if (ep.conj_acc) im = -im;
-                            cplx* cp = Cb + m * ep.sCm + n * ep.sCn;
-                            cplx v = make_double2(ep.alpha.x * re - ep.alpha.y * im, ep.alpha.x * im + ep.alpha.y * re);
-                            if (ep.atomic) {
-                                atomicAdd(&cp->x, v.x);
-                                atomicAdd(&cp->y, v.y);
-                                continue;
+                    for (int j = 0; j < 16; ++j)
+                        old[j] = (rd && live && n0 + j < ep.N) ? Cb[m * ep.sCm + (n0 + j) * ep.sCn]
+                                                               : make_double2(0.0, 0.0);
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32), r);
+                    if (live) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int64_t n = n0 + j;
+                            if (n < ep.N) {
+                                double re = (double)__uint_as_float(r[2 * j]);
+                                double im = (double)__uint_as_float(r[2 * j + 1]);
+                                if (ep.conj_acc) im = -im;
+                                cplx* cp = Cb + m * ep.sCm + n * ep.sCn;
+                                cplx v = make_double2(ep.alpha.x * re - ep.alpha.y * im,
+                                                      ep.alpha.x * im + ep.alpha.y * re);
+                                if (ep.atomic) {
+                                    atomicAdd(&cp->x, v.x);
+                                    atomicAdd(&cp->y, v.y);
+                                    continue;
+                                }
+                                v.x += bc.x * old[j].x - bc.y * old[j].y;
+                                v.y += bc.x * old[j].y + bc.y * old[j].x;
+                                *cp = v;
                             }
-                            if (!beta0) {
-                                cplx o = *cp;
-                                v.x += ep.beta.x * o.x - ep.beta.y * o.y;
-                                v.y += ep.beta.x * o.y + ep.beta.y * o.x;
-                            }
-                            *cp = v;
                         }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acce[acc]);
+                ++ti;
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[acc]);
-            ++ti;
         }
     }
     __syncwarp();
@@ -413,11 +442,24 @@ __device__ __forceinline__ void embed_store(void* __restrict__ out, int64_t rows
 // source S[b][r][k] with strides (sb, sr, sk); k fastest across threads
 template <int KIND, bool IS_B>
 __global__ void k_embed(const cplx* __restrict__ S, int64_t sb, int64_t sr, int64_t sk, int cj, int64_t batch,
-                        int64_t Rn, int64_t K, int64_t rows_e, int64_t pitch, void* __restrict__ out) {
+                        int64_t Rn, int64_t K, FastDiv fR, FastDiv fK, int64_t rows_e, int64_t pitch,
+                        void* __restrict__ out) {
     const int64_t total = batch * Rn * K;
+    const bool fast = total < FAST_INDEX_LIMIT;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = idx % K, t = idx / K, r = t % Rn, b = t / Rn;
+        int64_t k, r, b;
+        if (fast) {
+            const uint32_t t = fK.div((uint32_t)idx), bb = fR.div(t);
+            k = (uint32_t)idx - t * fK.d;
+            r = t - bb * fR.d;
+            b = bb;
+        } else {
+            const int64_t t = idx / K;
+            k = idx % K;
+            r = t % Rn;
+            b = t / Rn;
+        }
         cplx v = S[b * sb + r * sr + k * sk];
         if (cj) v.y = -v.y;
         embed_store<KIND, IS_B>(out, rows_e, pitch, b, r, k, v);
@@ -566,7 +608,7 @@ void launch_tc(Dev& D, const CUtensorMap& ta, const CUtensorMap& tb, const Sched
 // columns, with a small penalty on narrow tiles (more A re-reads per output)
 int bn_for(int64_t n2) {
     static const int cand[4] = {256, 128, 64, 32};
-    static const double pen[4] = {1.0, 1.05, 1.15, 1.3};
+    static const double pen[4] = {1.0, 1.25, 1.6, 2.2};
     int best = 256;
     double bc = 1e300;
     for (int i = 0; i < 4; ++i) {
@@ -601,10 +643,10 @@ void tc_embed_a(Dev& D, int prec, const cplx* A, int64_t sAb, int64_t sAm, int64
     const int gt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)D.sm_count * 8));
     if (prec == LRCC_MIXED_BF16X3) {
         if (tiled) k_embed_t<0, false><<<gt, 256, 0, D.st>>>(A, sAb, sAk, cA, batch, M, K, M, pitch, out);
-        else k_embed<0, false><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, M, pitch, out);
+        else k_embed<0, false><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, FastDiv(M), FastDiv(K), M, pitch, out);
     } else {
         if (tiled) k_embed_t<1, false><<<gt, 256, 0, D.st>>>(A, sAb, sAk, cA, batch, M, K, M, pitch, out);
-        else k_embed<1, false><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, M, pitch, out);
+        else k_embed<1, false><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, FastDiv(M), FastDiv(K), M, pitch, out);
     }
     LAUNCH_CHECK(D);
 }
@@ -617,10 +659,10 @@ void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64
     const int gt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)D.sm_count * 8));
     if (prec == LRCC_MIXED_BF16X3) {
         if (tiled) k_embed_t<0, true><<<gt, 256, 0, D.st>>>(B, sBb, sBk, cB, batch, N, K, 2 * N, pitch, out);
-        else k_embed<0, true><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBn, sBk, cB, batch, N, K, 2 * N, pitch, out);
+        else k_embed<0, true><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBn, sBk, cB, batch, N, K, FastDiv(N), FastDiv(K), 2 * N, pitch, out);
     } else {
         if (tiled) k_embed_t<1, true><<<gt, 256, 0, D.st>>>(B, sBb, sBk, cB, batch, N, K, 2 * N, pitch, out);
-        else k_embed<1, true><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBn, sBk, cB, batch, N, K, 2 * N, pitch, out);
+        else k_embed<1, true><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBn, sBk, cB, batch, N, K, FastDiv(N), FastDiv(K), 2 * N, pitch, out);
     }
     LAUNCH_CHECK(D);
 }
@@ -647,16 +689,17 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
     // K splits: fewest estimated waves x (k-blocks per unit + per-unit overhead);
     // split units add their partial tiles to C with FP64 atomics
     const int64_t sm = D.sm_count;
-    static const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
     int splits = 1, kps = num_kb;
     double best = 1e300;
-    for (int S : cand) {
+    for (int S = 1; S <= 96; ++S) {
         if (S > 1 && num_kb / S < 8) break;
         const int k1 = (num_kb + S - 1) / S;
         const int se = (num_kb + k1 - 1) / k1;
+        if (se != S) continue;
         const int64_t units = tiles * se;
         const double waves = double((units + sm - 1) / sm);
-        const double cost = waves * (k1 + 3.0 + (se > 1 ? 4.0 * bn / 256.0 : 0.0));
+        const int chunks = (k1 + KCHUNK - 1) / KCHUNK;
+        const double cost = waves * (k1 + 3.0 + (se > 1 ? 4.0 * bn / 256.0 * chunks : 0.0));
         if (cost < best * 0.97) {
             best = cost;
             splits = se;
@@ -671,6 +714,7 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
     sc.kps = kps;
     sc.num_kb = num_kb;
     sc.group = (int)std::min<int64_t>(tiles_m, 16);
+    sc.kchunk = KCHUNK;
     sc.units = (long long)tiles * splits;
     REQUIRE(batch < INT32_MAX, "gemm_tc: batch too large");
     Epi ep{M, N, C, sCb, sCm, sCn, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0};

@@ -119,10 +119,41 @@ Tensor Tensor::permute(const std::vector<int>& perm) const {
 // ---------------------------------------------------------------------------
 struct ShapeStrides {
     int nd;
+    int fast;  // index space below 2^31: decode with fd[]
     int64_t d[MAXD];
     int64_t sx[MAXD];
     int64_t sy[MAXD];
+    FastDiv fd[MAXD];
 };
+
+// offsets of linear index idx (innermost dimension last) in the x and y views
+__device__ __forceinline__ void offsets2(const ShapeStrides& ss, int64_t idx, int64_t& ox, int64_t& oy) {
+    ox = 0;
+    oy = 0;
+    if (ss.fast) {
+        uint32_t r = (uint32_t)idx;
+        for (int k = ss.nd - 1; k >= 0; --k) {
+            const uint32_t q = ss.fd[k].div(r);
+            const int64_t c = (int64_t)(r - q * ss.fd[k].d);
+            r = q;
+            ox += c * ss.sx[k];
+            oy += c * ss.sy[k];
+        }
+        return;
+    }
+    int64_t r = idx;
+    for (int k = ss.nd - 1; k >= 0; --k) {
+        const int64_t c = r % ss.d[k];
+        r /= ss.d[k];
+        ox += c * ss.sx[k];
+        oy += c * ss.sy[k];
+    }
+}
+
+static void set_fast(ShapeStrides& ss, int64_t n) {
+    ss.fast = n < FAST_INDEX_LIMIT;
+    for (int k = 0; k < ss.nd; ++k) ss.fd[k] = FastDiv(ss.fast ? ss.d[k] : 1);
+}
 
 __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -133,13 +164,8 @@ __global__ void k_axpby(ShapeStrides ss, int64_t n, cplx alpha, const cplx* __re
                         cplx beta, cplx* __restrict__ y) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = idx, ox = 0, oy = 0;
-        for (int k = ss.nd - 1; k >= 0; --k) {
-            int64_t c = r % ss.d[k];
-            r /= ss.d[k];
-            ox += c * ss.sx[k];
-            oy += c * ss.sy[k];
-        }
+        int64_t ox, oy;
+        offsets2(ss, idx, ox, oy);
         cplx v = x[ox];
         if (conjx) v.y = -v.y;
         v = cmul(alpha, v);
@@ -155,12 +181,8 @@ __global__ void k_axpby(ShapeStrides ss, int64_t n, cplx alpha, const cplx* __re
 __global__ void k_fill(ShapeStrides ss, int64_t n, cplx v, cplx* __restrict__ y) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = idx, oy = 0;
-        for (int k = ss.nd - 1; k >= 0; --k) {
-            int64_t c = r % ss.d[k];
-            r /= ss.d[k];
-            oy += c * ss.sy[k];
-        }
+        int64_t ox, oy;
+        offsets2(ss, idx, ox, oy);
         y[oy] = v;
     }
 }
@@ -216,6 +238,7 @@ static ShapeStrides simplify(const Tensor& x, const Tensor& y) {
         ss.sx[0] = 0;
         ss.sy[0] = 0;
     }
+    set_fast(ss, y.numel());
     return ss;
 }
 
@@ -347,12 +370,8 @@ __global__ void k_maxabs(ShapeStrides ss, int64_t n, int64_t per_row, const cplx
     double m = 0.0;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < per_row;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = row * per_row + idx, oy = 0;
-        for (int k = ss.nd - 1; k >= 0; --k) {
-            int64_t c = r % ss.d[k];
-            r /= ss.d[k];
-            oy += c * ss.sy[k];
-        }
+        int64_t ox, oy;
+        offsets2(ss, row * per_row + idx, ox, oy);
         cplx v = y[oy];
         double a = sqrt(v.x * v.x + v.y * v.y);
         if (!(a <= 1e300)) a = 1e308;  // NaN / Inf -> huge
@@ -412,8 +431,10 @@ double max_abs(Dev& D, const Tensor& y) {
 // ---------------------------------------------------------------------------
 struct Str3 {
     int nd;
+    int fast;
     int64_t d[MAXD];
     int64_t sa[MAXD], sb[MAXD], sc[MAXD];
+    FastDiv fd[MAXD];
 };
 
 template <bool BETA0>
@@ -421,13 +442,26 @@ __global__ void k_outer(Str3 s, int64_t n, cplx alpha, const cplx* __restrict__ 
                         int cb, cplx beta, cplx* __restrict__ c) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = idx, oa = 0, ob = 0, oc = 0;
-        for (int k = s.nd - 1; k >= 0; --k) {
-            int64_t q = r % s.d[k];
-            r /= s.d[k];
-            oa += q * s.sa[k];
-            ob += q * s.sb[k];
-            oc += q * s.sc[k];
+        int64_t oa = 0, ob = 0, oc = 0;
+        if (s.fast) {
+            uint32_t r = (uint32_t)idx;
+            for (int k = s.nd - 1; k >= 0; --k) {
+                const uint32_t qq = s.fd[k].div(r);
+                const int64_t q = (int64_t)(r - qq * s.fd[k].d);
+                r = qq;
+                oa += q * s.sa[k];
+                ob += q * s.sb[k];
+                oc += q * s.sc[k];
+            }
+        } else {
+            int64_t r = idx;
+            for (int k = s.nd - 1; k >= 0; --k) {
+                int64_t q = r % s.d[k];
+                r /= s.d[k];
+                oa += q * s.sa[k];
+                ob += q * s.sb[k];
+                oc += q * s.sc[k];
+            }
         }
         cplx u = a[oa], v = b[ob];
         if (ca) u.y = -u.y;
@@ -471,6 +505,8 @@ void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, 
     }
     int64_t n = C.numel();
     if (n == 0) return;
+    s.fast = n < FAST_INDEX_LIMIT;
+    for (int k = 0; k < s.nd; ++k) s.fd[k] = FastDiv(s.fast ? s.d[k] : 1);
     bool beta0 = beta.x == 0.0 && beta.y == 0.0;
     int th = 256, g = grid_for(D, n, th);
     if (beta0) k_outer<true><<<g, th, 0, D.st>>>(s, n, alpha, A.p, ca, B.p, cb, beta, C.p);
@@ -484,16 +520,36 @@ void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, 
 // y = alpha * P x + beta * y.  Each P is its own transpose.
 // ---------------------------------------------------------------------------
 template <bool BETA0>
-__global__ void k_asym(int mode, int64_t n, int64_t O, int64_t V, cplx alpha, const cplx* __restrict__ x, cplx beta,
-                       cplx* __restrict__ y) {
+__global__ void k_asym(int mode, int64_t n, int64_t O, int64_t V, FastDiv fO, FastDiv fV, cplx alpha,
+                       const cplx* __restrict__ x, cplx beta, cplx* __restrict__ y) {
     const int64_t VV = V * V, OVV = O * VV;
+    const bool fast = n < FAST_INDEX_LIMIT;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t b = idx % V, t = idx / V, a = t % V;
-        t /= V;
-        int64_t j = t % O;
-        t /= O;
-        int64_t i = t % O, r = t / O;
+        int64_t b, a, j, i, r;
+        if (fast) {
+            uint32_t u = (uint32_t)idx, q = fV.div(u);
+            b = u - q * fV.d;
+            u = q;
+            q = fV.div(u);
+            a = u - q * fV.d;
+            u = q;
+            q = fO.div(u);
+            j = u - q * fO.d;
+            u = q;
+            q = fO.div(u);
+            i = u - q * fO.d;
+            r = q;
+        } else {
+            int64_t t = idx / V;
+            b = idx % V;
+            a = t % V;
+            t /= V;
+            j = t % O;
+            t /= O;
+            i = t % O;
+            r = t / O;
+        }
         const cplx* xr = x + r * O * OVV;
         cplx v = xr[i * OVV + j * VV + a * V + b];
         if (mode & 1) {
@@ -531,7 +587,8 @@ void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor
     if (n == 0) return;
     bool beta0 = beta.x == 0.0 && beta.y == 0.0;
     int th = 256, g = grid_for(D, n, th);
-    if (beta0) k_asym<true><<<g, th, 0, D.st>>>(mode, n, O, V, alpha, x.p, beta, y.p);
-    else k_asym<false><<<g, th, 0, D.st>>>(mode, n, O, V, alpha, x.p, beta, y.p);
+    FastDiv fO(O), fV(V);
+    if (beta0) k_asym<true><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, x.p, beta, y.p);
+    else k_asym<false><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, x.p, beta, y.p);
     LAUNCH_CHECK(D);
 }

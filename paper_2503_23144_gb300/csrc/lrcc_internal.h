@@ -107,6 +107,26 @@ struct KTimer {
 };
 
 // ---------------------------------------------------------------------------
+// n / d and n % d for 0 <= n < 2^31 with one multiply-high (the round-up
+// method of Granlund and Montgomery, PLDI 1994): s = ceil(log2 d),
+// m = floor(2^32 (2^s - d) / d) + 1, n / d = (mulhi(n, m) + n) >> s.
+// Index decoding in the elementwise kernels uses it instead of 64-bit division.
+// ---------------------------------------------------------------------------
+struct FastDiv {
+    uint32_t d = 1, m = 1, s = 0;
+    FastDiv() = default;
+    explicit FastDiv(int64_t div) {
+        d = (uint32_t)(div < 1 ? 1 : div);
+        s = 0;
+        while ((uint64_t(1) << s) < d) ++s;
+        m = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << s) - d)) / d + 1);
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const { return (__umulhi(n, m) + n) >> s; }
+};
+// elementwise index spaces below 2^31 decode with FastDiv
+constexpr int64_t FAST_INDEX_LIMIT = int64_t(1) << 31;
+
+// ---------------------------------------------------------------------------
 // strided complex tensor (row-major by default), up to 8 dimensions
 // ---------------------------------------------------------------------------
 constexpr int MAXD = 8;

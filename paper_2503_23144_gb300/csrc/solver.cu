@@ -14,42 +14,75 @@ int grid_n(Dev& D, int64_t n) {
 // out = x - r / (D + shift[r]);  D1 = ev[a]-eo[i], D2 = ev[a]+ev[b]-eo[i]-eo[j]
 __global__ void k_precond(const cplx* __restrict__ x1, const cplx* __restrict__ r1, cplx* __restrict__ o1,
                           const cplx* __restrict__ x2, const cplx* __restrict__ r2, cplx* __restrict__ o2,
-                          int64_t R, int64_t O, int64_t V, const double* __restrict__ eo,
-                          const double* __restrict__ ev, const double* __restrict__ shift, int x_zero) {
+                          int64_t R, int64_t O, int64_t V, FastDiv fO, FastDiv fV, FastDiv fn1, FastDiv fn2,
+                          const double* __restrict__ eo, const double* __restrict__ ev,
+                          const double* __restrict__ shift, int x_zero) {
     int64_t n1 = O * V, n2 = O * O * V * V;
     int64_t total = R * (n1 + n2);
+    const bool fast = total < FAST_INDEX_LIMIT;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         bool singles = idx < R * n1;
         int64_t k = singles ? idx : idx - R * n1;
-        int64_t n = singles ? n1 : n2;
-        int64_t r = k / n, e = k % n;
-        double d;
-        if (singles) {
-            d = ev[e % V] - eo[e / V];
+        int64_t r, i, j = 0, a, b = 0;
+        if (fast) {
+            uint32_t u = (uint32_t)k, q;
+            if (singles) {
+                q = fn1.div(u);
+                r = q;
+                u -= q * fn1.d;
+                q = fV.div(u);
+                a = u - q * fV.d;
+                i = q;
+            } else {
+                q = fn2.div(u);
+                r = q;
+                u -= q * fn2.d;
+                q = fV.div(u);
+                b = u - q * fV.d;
+                u = q;
+                q = fV.div(u);
+                a = u - q * fV.d;
+                u = q;
+                q = fO.div(u);
+                j = u - q * fO.d;
+                i = q;
+            }
         } else {
-            int64_t b = e % V, t = e / V, a = t % V;
-            t /= V;
-            int64_t j = t % O, i = t / O;
-            d = ev[a] + ev[b] - eo[i] - eo[j];
+            int64_t n = singles ? n1 : n2;
+            r = k / n;
+            int64_t e = k % n;
+            if (singles) {
+                a = e % V;
+                i = e / V;
+            } else {
+                b = e % V;
+                int64_t t = e / V;
+                a = t % V;
+                t /= V;
+                j = t % O;
+                i = t / O;
+            }
         }
-        d += shift[r];
+        double d = singles ? ev[a] - eo[i] : ev[a] + ev[b] - eo[i] - eo[j];
+        const double inv = 1.0 / (d + shift[r]);
         const cplx* x = singles ? x1 : x2;
         const cplx* rr = singles ? r1 : r2;
         cplx* o = singles ? o1 : o2;
         cplx v = rr[k];
         cplx xv = x_zero ? make_double2(0.0, 0.0) : x[k];
-        o[k] = make_double2(xv.x - v.x / d, xv.y - v.y / d);
+        o[k] = make_double2(xv.x - v.x * inv, xv.y - v.y * inv);
     }
 }
 
 // out[r][e] = s[r][e] + coef[r] * x[r][e] + b[r][e]     (b may be null)
-__global__ void k_combine(int64_t R, int64_t n, const cplx* __restrict__ s, const cplx* __restrict__ x,
+__global__ void k_combine(int64_t R, int64_t n, FastDiv fn, const cplx* __restrict__ s, const cplx* __restrict__ x,
                           const double* __restrict__ coef, const cplx* __restrict__ b, cplx* __restrict__ out) {
     int64_t total = R * n;
+    const bool fast = total < FAST_INDEX_LIMIT;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = idx / n;
+        int64_t r = fast ? (int64_t)fn.div((uint32_t)idx) : idx / n;
         cplx v = s[idx], xv = x[idx];
         double c = coef[r];
         v.x += c * xv.x;
@@ -146,13 +179,14 @@ struct Ptrs {
 };
 
 // out[r][e] = sum_i coef[r][slot_i] * v_i[r][e]
-__global__ void k_lincomb(int64_t R, int64_t n, Ptrs v, int k, const int* slots_unused, const cplx* coef,
-                          int nmax, const int* slots, cplx* __restrict__ out) {
+__global__ void k_lincomb(int64_t R, int64_t n, FastDiv fn, Ptrs v, int k, const int* slots_unused,
+                          const cplx* coef, int nmax, const int* slots, cplx* __restrict__ out) {
     (void)slots_unused;
     int64_t total = R * n;
+    const bool fast = total < FAST_INDEX_LIMIT;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = idx / n;
+        int64_t r = fast ? (int64_t)fn.div((uint32_t)idx) : idx / n;
         double sx = 0, sy = 0;
         for (int i = 0; i < k; ++i) {
             cplx c = coef[r * nmax + slots[i]];
@@ -179,16 +213,18 @@ void precond(Dev& D, const Amp* x, const Amp& r, Amp& out, const double* eo, con
     int64_t R = r.t1.d[0], O = r.t1.d[1], V = r.t1.d[2];
     int64_t total = R * (O * V + O * O * V * V);
     k_precond<<<grid_n(D, total), 256, 0, D.st>>>(x ? x->t1.p : nullptr, r.t1.p, out.t1.p, x ? x->t2.p : nullptr,
-                                                     r.t2.p, out.t2.p, R, O, V, eo, ev, shift_dev, x ? 0 : 1);
+                                                     r.t2.p, out.t2.p, R, O, V, FastDiv(O), FastDiv(V),
+                                                     FastDiv(O * V), FastDiv(O * O * V * V), eo, ev, shift_dev,
+                                                     x ? 0 : 1);
     LAUNCH_CHECK(D);
 }
 
 void combine(Dev& D, const Amp& s, const Amp& x, const double* coef_dev, const Amp* b, Amp& out) {
     int64_t R = s.t1.d[0];
     int64_t n1 = s.t1.numel() / R, n2 = s.t2.numel() / R;
-    k_combine<<<grid_n(D, R * n1), 256, 0, D.st>>>(R, n1, s.t1.p, x.t1.p, coef_dev, b ? b->t1.p : nullptr, out.t1.p);
+    k_combine<<<grid_n(D, R * n1), 256, 0, D.st>>>(R, n1, FastDiv(n1), s.t1.p, x.t1.p, coef_dev, b ? b->t1.p : nullptr, out.t1.p);
     LAUNCH_CHECK(D);
-    k_combine<<<grid_n(D, R * n2), 256, 0, D.st>>>(R, n2, s.t2.p, x.t2.p, coef_dev, b ? b->t2.p : nullptr, out.t2.p);
+    k_combine<<<grid_n(D, R * n2), 256, 0, D.st>>>(R, n2, FastDiv(n2), s.t2.p, x.t2.p, coef_dev, b ? b->t2.p : nullptr, out.t2.p);
     LAUNCH_CHECK(D);
 }
 
@@ -288,9 +324,9 @@ Amp Diis::push_extrapolate(Dev& D, const Amp& x, const Amp& e) {
         p2.p[i] = xs[sl[i]].t2.p;
     }
     int64_t n1 = x.t1.numel() / R, n2 = x.t2.numel() / R;
-    k_lincomb<<<grid_n(D, R * n1), 256, 0, D.st>>>(R, n1, p1, k, nullptr, coef.p, nmax, slots_dev, out.t1.p);
+    k_lincomb<<<grid_n(D, R * n1), 256, 0, D.st>>>(R, n1, FastDiv(n1), p1, k, nullptr, coef.p, nmax, slots_dev, out.t1.p);
     LAUNCH_CHECK(D);
-    k_lincomb<<<grid_n(D, R * n2), 256, 0, D.st>>>(R, n2, p2, k, nullptr, coef.p, nmax, slots_dev, out.t2.p);
+    k_lincomb<<<grid_n(D, R * n2), 256, 0, D.st>>>(R, n2, FastDiv(n2), p2, k, nullptr, coef.p, nmax, slots_dev, out.t2.p);
     LAUNCH_CHECK(D);
     // the host copy of the slot list must outlive the async copy
     CK(cudaStreamSynchronize(D.st));

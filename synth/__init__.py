@@ -25,7 +25,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["CONFIGS", "make_system", "random_amplitudes", "random_unitary",
-           "pair_count", "omega_grid"]
+           "random_packed", "pair_count", "omega_grid"]
 
 
 def pair_count(n: int) -> int:
@@ -113,3 +113,16 @@ def random_unitary(n: int, seed: int) -> np.ndarray:
     q, r = np.linalg.qr(z)
     d = np.diagonal(r)
     return q * (d / np.abs(d))
+
+
+def random_packed(nrow: int, ncol: int, seed: int, block: int = 64) -> np.ndarray:
+    """Complex matrix [nrow, ncol] with unit-normal real and imaginary parts,
+    drawn from one PCG64 stream block by block of rows (real parts of a block,
+    then its imaginary parts), without full-size temporaries."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((nrow, ncol), dtype=np.complex128)
+    for r0 in range(0, nrow, block):
+        r1 = min(nrow, r0 + block)
+        out[r0:r1].real = rng.standard_normal((r1 - r0, ncol))
+        out[r0:r1].imag = rng.standard_normal((r1 - r0, ncol))
+    return out
