@@ -30,8 +30,9 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-PREC_NAMES = {"fp64": 0, "tf32": 1, "bf16x3": 2}
-DTYPE_NAMES = {"fp64": "c128 (f64)", "tf32": "tf32 tensor-core + f64", "bf16x3": "bf16x3 tensor-core + f64"}
+PREC_NAMES = {"fp64": 0, "tf32": 1, "bf16x3": 2, "fp64emu": 3}
+DTYPE_NAMES = {"fp64": "c128 (f64)", "tf32": "tf32 tensor-core + f64", "bf16x3": "bf16x3 tensor-core + f64",
+               "fp64emu": "c128 via 7x6-bit integer slices on bf16 tensor cores"}
 
 
 def nominal_flops(O, V, L, R, assembly=True):
@@ -330,6 +331,10 @@ def main():
         if name == "gemm_tc_bf16x3":
             peak, unit, bound = bf16 / 3.0, "TFLOP/s", "tensor"     # 3 bf16 products per real product
             note = f"bf16 {src} peak / 3 (bf16x3 split); complex flops counted 8 per CMAC"
+        elif name == "gemm_tc_f64emu":
+            # 28 bf16 slice products (7 diagonals) per real product, 4 real per complex
+            peak, unit, bound = bf16 / 28.0, "TFLOP/s", "tensor"
+            note = f"bf16 {src} peak / 28 (7x6-bit slices, diagonals 0..6); complex flops counted 8 per CMAC"
         elif name == "gemm_tc_tf32":
             peak, unit, bound = bf16 / 2.0, "TFLOP/s", "tensor"     # tf32 dense = bf16 / 2 nominal
             note = f"bf16 {src} peak x tf32/bf16 nominal ratio 1/2"

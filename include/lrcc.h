@@ -51,7 +51,10 @@ typedef enum {
 typedef enum {
     LRCC_FP64 = 0,          /* every contraction in FP64                        */
     LRCC_MIXED_TF32 = 1,    /* ladder/ring on tcgen05 kind::tf32, FP64 refine   */
-    LRCC_MIXED_BF16X3 = 2   /* ladder/ring as 3 bf16 products, FP64 refine      */
+    LRCC_MIXED_BF16X3 = 2,  /* ladder/ring as 3 bf16 products, FP64 refine      */
+    LRCC_FP64_EMULATED = 3  /* FP64 solver; large contractions as exact integer-
+                               slice products on bf16 tensor cores (7 slices of
+                               6 bits, FP64 sums; ~1e-12 relative per product) */
 } lrcc_precision;
 
 typedef struct {
@@ -70,6 +73,10 @@ typedef struct {
                               when it fits in a third of free memory, else slabs sized to it */
     int pm_omega;          /* 1: response function of Eq. 36 (solves X(+w) and X(-w),
                               no Y); 0 (default): Eq. 35 (X(w) and Y(w))            */
+    int fp64_products;     /* mixed modes: the FP64-accurate maps (outer residuals,
+                              F X, ground-state polish) use 1 (default): integer-slice
+                              products on the tensor cores (as LRCC_FP64_EMULATED),
+                              0: FP64 SIMT products                                  */
 } lrcc_options;
 
 /* Fill *opt with the defaults above. */

@@ -197,9 +197,11 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
     double flops = 8.0 * double(g.M) * double(g.N) * double(g.K) * double(g.batch);
     // mixed mode: every contraction with real work goes to the tensor cores
     // (the O-sized contractions too: FP64 on this part is 1.25 TFLOP/s)
-    bool tc = prec != LRCC_FP64 && gemm_tc_available() && flops >= 5e7 && g.K >= 48;
-    if (tc) gemm_tc(D, g, prec);
-    else if (prec != LRCC_FP64) gemm_f32c(D, g);
+    const bool mixed = prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3;
+    const bool big = gemm_tc_available() && flops >= 5e7 && g.K >= 48;
+    if (mixed && big) gemm_tc(D, g, prec);
+    else if (mixed) gemm_f32c(D, g);
+    else if (prec == LRCC_FP64_EMULATED && big && std::min(g.M, g.N) >= 8) gemm_tc_f64(D, g);
     else gemm_f64(D, g);
     if (!c_ok) perm_axpby(D, lc + "->" + sp.c, alpha, Ct, beta, C);
 }
@@ -425,6 +427,12 @@ int grid_n(Dev& D, int64_t n) {
 // GT[(b,f)][(a,e)] = sum_L Bvv^L_bf Bvv^L_ae (b >= gb0) come from one GEMM
 // over L, then W_ab,ef = GT[(b,f)][(a,e)] - GT[(b,e)][(a,f)] for e < f.
 // ---------------------------------------------------------------------------
+// FP64 products (SIMT) or FP64-class products on the tensor cores
+static void gemm_fp64_class(Dev& D, const GemmArgs& g, int prec) {
+    if (prec == LRCC_FP64_EMULATED && gemm_tc_available()) gemm_tc_f64(D, g);
+    else gemm_f64(D, g);
+}
+
 struct Slab {
     int64_t a0, a1, b0, b1, gb0, prow0, nrows;
 };
@@ -544,14 +552,14 @@ static void assemble_slab(Dev& D, LadderCtx& LC, const Slab& sl, int prec, bool 
     const int64_t M = (sl.a1 - sl.a0) * V, N = (sl.b1 - sl.gb0) * V;
     REQUIRE(sc.gt && M * N <= sc.gt_el, "ladder: slab product buffer too small");
     Tensor GT = wrap(sc.gt, {N, M});
-    if (prec == LRCC_FP64) {
+    if (prec == LRCC_FP64 || prec == LRCC_FP64_EMULATED) {
         GemmArgs g;
         g.M = M; g.N = N; g.K = L; g.batch = 1;
         g.A = LC.Bvv.p + sl.a0 * V; g.sAb = 0; g.sAm = 1; g.sAk = V * V; g.cA = conj;
         g.B = LC.Bvv.p + sl.gb0 * V; g.sBb = 0; g.sBk = V * V; g.sBn = 1; g.cB = conj;
         g.C = GT.p; g.sCb = 0; g.sCm = 1; g.sCn = M;
         g.alpha = mkc(1.0); g.beta = mkc(0.0);
-        gemm_f64(D, g);
+        gemm_fp64_class(D, g, prec);
         k_antisym_gt<<<grid_n(D, sl.nrows * (V * (V - 1) / 2)), 256, 0, D.st>>>(GT.p, M, sl.a0, sl.gb0, sl.prow0,
                                                                                sl.nrows, V, W);
         LAUNCH_CHECK(D);
@@ -607,10 +615,12 @@ static bool ensure_wcache(Dev& D, LadderCtx& LC, int64_t V, int prec) {
 }
 
 // FP64 <ab||ef> matrix W [P_V][P_V] (rows a<b, columns e<f), built once if it
-// fits in a third of the free device memory.
-static bool ensure_w64(Dev& D, LadderCtx& LC, int64_t V) {
-    if (LC.w64.p) return true;
+// fits in a third of the free device memory, with FP64 or FP64-class products
+// (`builder`); a matrix built with FP64 products serves both.
+static bool ensure_w64(Dev& D, LadderCtx& LC, int64_t V, int builder) {
+    if (LC.w64.p && (LC.w64_prec == LRCC_FP64 || LC.w64_prec == builder)) return true;
     if (LC.w64_disabled || LC.slab_rows > 0) return false;
+    LC.w64 = Tensor();
     const int64_t PV = V * (V - 1) / 2;
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
@@ -621,25 +631,56 @@ static bool ensure_w64(Dev& D, LadderCtx& LC, int64_t V) {
     Tensor W = empty(D, {PV, PV});
     const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), 0);
     SlabScratch sc(D, plan, V);
-    for (const Slab& sl : plan) assemble_slab(D, LC, sl, LRCC_FP64, false, W.p + sl.prow0 * PV, nullptr, 0, sc);
+    for (const Slab& sl : plan) assemble_slab(D, LC, sl, builder, false, W.p + sl.prow0 * PV, nullptr, 0, sc);
     LC.w64 = W;
+    LC.w64_prec = builder;
+    return true;
+}
+
+// the FP64 W as sliced A operand of the FP64-class products, cached when it fits
+static bool ensure_ozcache(Dev& D, LadderCtx& LC, int64_t V) {
+    if (LC.ozcache) return true;
+    if (LC.ozcache_disabled) return false;
+    const int64_t PV = V * (V - 1) / 2;
+    int64_t rows_e, kpad;
+    const size_t bytes = oz_embed_bytes(PV, PV, 1, rows_e, kpad, false);
+    if ((double)bytes > 0.33 * free_bytes(D)) {
+        LC.ozcache_disabled = true;
+        return false;
+    }
+    void* p = D.pool.get(bytes);
+    LC.ozcache.reset(new DevBuf{&D.pool, p, bytes});
+    oz_embed_a(D, LC.w64.p, 0, PV, 1, false, 1, PV, PV, kpad, p);
+    LC.oz_kpad = kpad;
     return true;
 }
 
 void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol, bool transpose, int prec) {
     const int64_t V = LC.Bvv.d[1], PV = V * (V - 1) / 2;
     if (ncol <= 0 || PV <= 0) return;
-    if (prec == LRCC_FP64) {
+    if (prec == LRCC_FP64 || prec == LRCC_FP64_EMULATED) {
         GemmArgs g2;
         g2.N = ncol; g2.batch = 1;
         g2.B = Xt; g2.sBb = 0; g2.sBk = 1; g2.sBn = PV; g2.cB = false;
         g2.sCb = 0; g2.sCm = 1; g2.sCn = PV;
         g2.alpha = mkc(1.0); g2.beta = mkc(0.0);
-        if (ensure_w64(D, LC, V)) {
+        if (ensure_w64(D, LC, V, prec)) {
+            if (prec == LRCC_FP64_EMULATED && ensure_ozcache(D, LC, V)) {
+                // conj(W X) = conj(W) conj-free: X sliced conjugated, conjugate accumulator
+                int64_t rows_e, kpad;
+                const size_t bytesB = oz_embed_bytes(ncol, PV, 1, rows_e, kpad, true);
+                REQUIRE(kpad == LC.oz_kpad, "ladder: sliced K padding mismatch");
+                void* pb = D.pool.get(bytesB);
+                std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
+                oz_embed_b(D, Xt, 0, 1, PV, transpose, 1, PV, ncol, kpad, pb);
+                oz_gemm_embedded(D, LC.ozcache->p, pb, 1, PV, ncol, PV, kpad, Zt, 0, 1, PV, mkc(1.0), mkc(0.0),
+                                 transpose);
+                return;
+            }
             g2.M = PV; g2.K = PV;
             g2.A = LC.w64.p; g2.sAb = 0; g2.sAm = PV; g2.sAk = 1; g2.cA = transpose;  // B^T = conj B: conj(W)
             g2.C = Zt;
-            gemm_f64(D, g2);
+            gemm_fp64_class(D, g2, prec);
             return;
         }
         const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), LC.slab_rows);
@@ -652,12 +693,11 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
         Tensor W = empty(D, {wrows, PV});
         for (const SlabGroup& gr : groups) {
             for (size_t c = gr.c0; c < gr.c1; ++c)
-                assemble_slab(D, LC, plan[c], LRCC_FP64, transpose, W.p + (plan[c].prow0 - gr.prow0) * PV, nullptr, 0,
-                              sc);
+                assemble_slab(D, LC, plan[c], prec, transpose, W.p + (plan[c].prow0 - gr.prow0) * PV, nullptr, 0, sc);
             g2.M = gr.nrows; g2.K = PV;
             g2.A = W.p; g2.sAb = 0; g2.sAm = PV; g2.sAk = 1; g2.cA = false;
             g2.C = Zt + gr.prow0;
-            gemm_f64(D, g2);
+            gemm_fp64_class(D, g2, prec);
         }
         return;
     }

@@ -497,6 +497,157 @@ __global__ void __launch_bounds__(256) k_embed_t(const cplx* __restrict__ S, int
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP64-class products on bf16 tensor cores (the splitting scheme of Ozaki,
+// Ogita, Oishi and Rump, Numer. Algorithms 59 (2012), with integer slices).
+// Every row r of an operand gets an exponent e_r with |x| < 2^e_r for all its
+// elements (real and imaginary parts); x 2^-e_r is written as OZ_S digits of
+// OZ_BITS bits, d_s in (-2^OZ_BITS, 2^OZ_BITS), x = sum_s d_s 2^(e_r - OZ_BITS (s+1))
+// + (remainder below 2^(e_r - OZ_BITS OZ_S)).  Each slice d_s 2^(...) is exact
+// in bf16.  For one output element, all products of the slice pairs (s, t)
+// with s + t = d are integer multiples of one power of two, each at most
+// (2^OZ_BITS - 1)^2 < 2^12 of it, so an FP32 accumulation chain of up to
+// 4096 products (64 k-blocks of 64 bf16) is exact; the chains are added into
+// C in FP64.  Diagonals d = 0 .. OZ_S-1 are kept (products below
+// 2^-(OZ_BITS OZ_S) of the leading term are dropped): relative error ~1e-12
+// of max|A_row| max|B_col| per product.
+// ---------------------------------------------------------------------------
+constexpr int OZ_S = 7, OZ_BITS = 6, OZ_KCHUNK = 64;
+
+// e[b Rn + r]: smallest e with |Re|, |Im| < 2^e over the row (0 for a zero row)
+__device__ __forceinline__ int exp_of(double m) {
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);
+    return e;
+}
+
+// one warp per row, lanes along k
+__global__ void k_row_exp_w(const cplx* __restrict__ S, int64_t sb, int64_t sr, int64_t sk, int64_t batch,
+                            int64_t Rn, int64_t K, int cj, int* __restrict__ e) {
+    (void)cj;
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = batch * Rn;
+    for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < rows;
+         row += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t b = row / Rn, r = row % Rn;
+        const cplx* p = S + b * sb + r * sr;
+        double m = 0.0;
+        for (int64_t k = lane; k < K; k += 32) {
+            const cplx v = p[k * sk];
+            m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) e[row] = exp_of(m);
+    }
+}
+
+// one thread per row (for sources contiguous along r: consecutive threads read
+// consecutive addresses)
+__global__ void k_row_exp_t(const cplx* __restrict__ S, int64_t sb, int64_t sr, int64_t sk, int64_t batch,
+                            int64_t Rn, int64_t K, int* __restrict__ e) {
+    const int64_t rows = batch * Rn;
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < rows;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = row / Rn, r = row % Rn;
+        const cplx* p = S + b * sb + r * sr;
+        double m = 0.0;
+        for (int64_t k = 0; k < K; ++k) {
+            const cplx v = p[k * sk];
+            m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+        }
+        e[row] = exp_of(m);
+    }
+}
+
+// slices of v = op(S)[b][r][k] with row exponent e.  A rows: slice s at
+// columns s*kpad + 2k, 2k+1 = (Re, Im).  B row pairs (2r: real output, 2r+1:
+// imaginary output) in reversed slice order: slice t at (OZ_S-1-t)*kpad,
+// real row (Re, -Im), imaginary row (Im, Re).
+template <bool IS_B>
+__device__ __forceinline__ void oz_store(void* __restrict__ out, int64_t rows_e, int64_t kpad, int64_t b, int64_t r,
+                                         int64_t k, cplx v, int e) {
+    const int64_t pitch = OZ_S * kpad;
+    __nv_bfloat16* row = (__nv_bfloat16*)out + (b * rows_e + (IS_B ? 2 * r : r)) * pitch + 2 * k;
+    double yr = ldexp(v.x, -e), yi = ldexp(v.y, -e);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+        yr *= double(1 << OZ_BITS);
+        yi *= double(1 << OZ_BITS);
+        const double dr = trunc(yr), di = trunc(yi);
+        yr -= dr;
+        yi -= di;
+        const double sc = ldexp(1.0, e - OZ_BITS * (s + 1));
+        const __nv_bfloat16 hr = __double2bfloat16(dr * sc), hi = __double2bfloat16(di * sc);
+        if (!IS_B) {
+            *(uint32_t*)(row + s * kpad) = bf2(hr, hi);
+        } else {
+            const int64_t off = (OZ_S - 1 - s) * kpad;
+            *(uint32_t*)(row + off) = bf2(hr, __hneg(hi));
+            *(uint32_t*)(row + pitch + off) = bf2(hi, hr);
+        }
+    }
+}
+
+// k runs over the padded range [0, kpad/2); positions k >= K are written as zeros
+template <bool IS_B>
+__global__ void k_oz_embed(const cplx* __restrict__ S, int64_t sb, int64_t sr, int64_t sk, int cj, int64_t batch,
+                           int64_t Rn, int64_t K, int64_t K2, FastDiv fR, FastDiv fK2, const int* __restrict__ e,
+                           int64_t rows_e, int64_t kpad, void* __restrict__ out) {
+    const int64_t total = batch * Rn * K2;
+    const bool fast = total < FAST_INDEX_LIMIT;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t k, r, b;
+        if (fast) {
+            const uint32_t t = fK2.div((uint32_t)idx), bb = fR.div(t);
+            k = (uint32_t)idx - t * fK2.d;
+            r = t - bb * fR.d;
+            b = bb;
+        } else {
+            const int64_t t = idx / K2;
+            k = idx % K2;
+            r = t % Rn;
+            b = t / Rn;
+        }
+        cplx v = make_double2(0.0, 0.0);
+        if (k < K) v = S[b * sb + r * sr + k * sk];
+        if (cj) v.y = -v.y;
+        oz_store<IS_B>(out, rows_e, kpad, b, r, k, v, e[b * Rn + r]);
+    }
+}
+
+// the same for sources contiguous in r: 32x32 tiles read along r, written along k
+template <bool IS_B>
+__global__ void __launch_bounds__(256) k_oz_embed_t(const cplx* __restrict__ S, int64_t sb, int64_t sk, int cj,
+                                                    int64_t batch, int64_t Rn, int64_t K, int64_t K2,
+                                                    const int* __restrict__ e, int64_t rows_e, int64_t kpad,
+                                                    void* __restrict__ out) {
+    __shared__ cplx tile[32][33];
+    const int64_t tr_n = (Rn + 31) / 32, tk_n = (K2 + 31) / 32;
+    const int64_t ntiles = batch * tr_n * tk_n;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t tk = t % tk_n, u = t / tk_n, tr = u % tr_n, b = u / tr_n;
+        const int64_t r0 = tr * 32, k0 = tk * 32;
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t r = r0 + tx, k = k0 + j;
+            cplx v = make_double2(0.0, 0.0);
+            if (r < Rn && k < K) v = S[b * sb + r + k * sk];
+            tile[j][tx] = v;
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t r = r0 + j, k = k0 + tx;
+            if (r < Rn && k < K2) {
+                cplx v = tile[tx][j];
+                if (cj) v.y = -v.y;
+                oz_store<IS_B>(out, rows_e, kpad, b, r, k, v, e[b * Rn + r]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // (p, q) of pair index k among n (p < q, row-major strict upper triangle)
 __device__ __forceinline__ void pair_of(int64_t k, int64_t n, int64_t& p, int64_t& q) {
     const double a = double(2 * n - 1);
@@ -667,16 +818,17 @@ void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64
     LAUNCH_CHECK(D);
 }
 
-// C = alpha * op(A' B'^T) + beta C on embedded operands A' [batch][M][pitch],
-// B' [batch][2N][pitch], complex K (S*K embedded columns)
-void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
-                      int64_t K, int64_t pitch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
-                      cplx beta, bool conj_acc, double useful_flops) {
+// One persistent launch: C = alpha op(A' B'^T) + beta C on embedded operands
+// A' [batch][M][pitch], B' [batch][2N][pitch] of which the first kd columns
+// take part (kind 0: bf16, 1: tf32); FP32 accumulation chains of at most
+// kchunk k-blocks, added to C in FP64.
+static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
+                      int64_t kd, int64_t pitch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
+                      cplx beta, bool conj_acc, int kchunk, double useful_flops, const char* name) {
     REQUIRE(D.err_flag != nullptr, "gemm_tc: no error word");
     if (M <= 0 || N <= 0 || batch <= 0) return;
-    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
-    const int64_t es = kind == 0 ? 2 : 4, kelem = ROWB / es, kd = slots(kind) * K;
-    REQUIRE(K > 0 && pitch >= kd && (pitch * es) % 16 == 0, "gemm_tc: bad embedded K");
+    const int64_t es = kind == 0 ? 2 : 4, kelem = ROWB / es;
+    REQUIRE(kd > 0 && pitch >= kd && (pitch * es) % 16 == 0, "gemm_tc: bad embedded K");
     REQUIRE(((uintptr_t)pa % 16) == 0 && ((uintptr_t)pb % 16) == 0, "gemm_tc: operands not 16-byte aligned");
     const int bn = bn_for(2 * N);
     CUtensorMap ta, tb;
@@ -698,7 +850,7 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
         if (se != S) continue;
         const int64_t units = tiles * se;
         const double waves = double((units + sm - 1) / sm);
-        const int chunks = (k1 + KCHUNK - 1) / KCHUNK;
+        const int chunks = (k1 + kchunk - 1) / kchunk;
         const double cost = waves * (k1 + 3.0 + (se > 1 ? 4.0 * bn / 256.0 * chunks : 0.0));
         if (cost < best * 0.97) {
             best = cost;
@@ -714,7 +866,7 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
     sc.kps = kps;
     sc.num_kb = num_kb;
     sc.group = (int)std::min<int64_t>(tiles_m, 16);
-    sc.kchunk = KCHUNK;
+    sc.kchunk = kchunk;
     sc.units = (long long)tiles * splits;
     REQUIRE(batch < INT32_MAX, "gemm_tc: batch too large");
     Epi ep{M, N, C, sCb, sCm, sCn, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0};
@@ -729,8 +881,8 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
     const int skip = (inj && inj[0] == '1') ? 1 : 0;
     const uint32_t limit = skip ? WAIT_LIMIT_INJECT : WAIT_LIMIT;
     const int grid = (int)std::min<int64_t>(sc.units, sm);
-    KTimer kt(D, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32", useful_flops,
-              (double)(batch * (M + 2 * N) * kd * es) + 16.0 * M * N * batch, M, N, kd, batch);
+    KTimer kt(D, name, useful_flops, (double)(batch * (M + 2 * N) * kd * es) + 16.0 * M * N * batch, M, N, kd,
+              batch);
     switch (kind * 4 + (bn == 256 ? 0 : bn == 128 ? 1 : bn == 64 ? 2 : 3)) {
         case 0: launch_tc<0, 256>(D, ta, tb, sc, ep, grid, skip, limit); break;
         case 1: launch_tc<0, 128>(D, ta, tb, sc, ep, grid, skip, limit); break;
@@ -742,6 +894,17 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
         default: launch_tc<1, 32>(D, ta, tb, sc, ep, grid, skip, limit); break;
     }
     LAUNCH_CHECK(D);
+}
+
+// C = alpha * op(A' B'^T) + beta C on embedded operands A' [batch][M][pitch],
+// B' [batch][2N][pitch], complex K (S*K embedded columns)
+void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
+                      int64_t K, int64_t pitch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
+                      cplx beta, bool conj_acc, double useful_flops) {
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    REQUIRE(K > 0, "gemm_tc: bad embedded K");
+    tc_launch(D, kind, pa, pb, batch, M, N, slots(kind) * K, pitch, C, sCb, sCm, sCn, alpha, beta, conj_acc, KCHUNK,
+              useful_flops, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32");
 }
 
 // relative cost of running C[M][N] in this orientation: padded tensor-core
@@ -792,3 +955,98 @@ void tc_embed_antisym_slab(Dev& D, int prec, const cplx* GT, int64_t ldt, int64_
         k_embed_antisym<1><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, pitch, out);
     LAUNCH_CHECK(D);
 }
+
+// ---------------------------------------------------------------------------
+// FP64-class complex GEMM on the tensor cores (host side of the slicing
+// scheme above)
+// ---------------------------------------------------------------------------
+size_t oz_embed_bytes(int64_t rows, int64_t K, int64_t batch, int64_t& rows_e, int64_t& kpad, bool is_b) {
+    kpad = (2 * K + 7) / 8 * 8;
+    rows_e = is_b ? 2 * rows : rows;
+    return (size_t)(batch * rows_e * OZ_S * kpad * 2);
+}
+
+// exponents and slices of op(S)[b][r][k] (strides sb, sr, sk): e [batch*Rn]
+static void oz_embed(Dev& D, bool is_b, const cplx* S, int64_t sb, int64_t sr, int64_t sk, bool cj, int64_t batch,
+                     int64_t Rn, int64_t K, int64_t kpad, int* e, void* out) {
+    if (batch * Rn == 0) return;
+    const bool rows_contig = sr == 1 && sk != 1;
+    const int64_t rows = batch * Rn;
+    if (rows_contig) {
+        k_row_exp_t<<<(int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, D.sm_count * 16)), 256, 0,
+                      D.st>>>(S, sb, sr, sk, batch, Rn, K, e);
+    } else {
+        k_row_exp_w<<<(int)std::max<int64_t>(1, std::min<int64_t>((rows * 32 + 255) / 256, D.sm_count * 16)), 256,
+                      0, D.st>>>(S, sb, sr, sk, batch, Rn, K, 0, e);
+    }
+    LAUNCH_CHECK(D);
+    const int64_t K2 = kpad / 2, rows_e = is_b ? 2 * Rn : Rn;
+    if (rows_contig) {
+        const int64_t nt = batch * ((Rn + 31) / 32) * ((K2 + 31) / 32);
+        const int gt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)D.sm_count * 8));
+        if (is_b) k_oz_embed_t<true><<<gt, 256, 0, D.st>>>(S, sb, sk, cj, batch, Rn, K, K2, e, rows_e, kpad, out);
+        else k_oz_embed_t<false><<<gt, 256, 0, D.st>>>(S, sb, sk, cj, batch, Rn, K, K2, e, rows_e, kpad, out);
+    } else {
+        const int g = grid_n(D, batch * Rn * K2);
+        if (is_b)
+            k_oz_embed<true><<<g, 256, 0, D.st>>>(S, sb, sr, sk, cj, batch, Rn, K, K2, FastDiv(Rn), FastDiv(K2), e,
+                                                  rows_e, kpad, out);
+        else
+            k_oz_embed<false><<<g, 256, 0, D.st>>>(S, sb, sr, sk, cj, batch, Rn, K, K2, FastDiv(Rn), FastDiv(K2), e,
+                                                   rows_e, kpad, out);
+    }
+    LAUNCH_CHECK(D);
+}
+
+void oz_embed_a(Dev& D, const cplx* A, int64_t sAb, int64_t sAm, int64_t sAk, bool cA, int64_t batch, int64_t M,
+                int64_t K, int64_t kpad, void* out) {
+    int* e = (int*)D.pool.get(sizeof(int) * batch * M);
+    std::shared_ptr<DevBuf> he(new DevBuf{&D.pool, e, sizeof(int) * (size_t)(batch * M)});
+    oz_embed(D, false, A, sAb, sAm, sAk, cA, batch, M, K, kpad, e, out);
+}
+
+void oz_embed_b(Dev& D, const cplx* B, int64_t sBb, int64_t sBk, int64_t sBn, bool cB, int64_t batch, int64_t K,
+                int64_t N, int64_t kpad, void* out) {
+    int* e = (int*)D.pool.get(sizeof(int) * batch * N);
+    std::shared_ptr<DevBuf> he(new DevBuf{&D.pool, e, sizeof(int) * (size_t)(batch * N)});
+    oz_embed(D, true, B, sBb, sBn, sBk, cB, batch, N, K, kpad, e, out);
+}
+
+// C = alpha op(A B) + beta C from sliced operands: one launch per diagonal
+// d = s + t, over the concatenated K of the pairs (A_0..A_d) x (B_d..B_0)
+void oz_gemm_embedded(Dev& D, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N, int64_t K,
+                      int64_t kpad, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha, cplx beta,
+                      bool conj_acc) {
+    const double useful = 8.0 * M * N * K * batch, pairs = OZ_S * (OZ_S + 1) / 2.0;
+    for (int d = 0; d < OZ_S; ++d) {
+        const char* pbd = (const char*)pb + (size_t)((OZ_S - 1 - d) * kpad * 2);
+        tc_launch(D, 0, pa, pbd, batch, M, N, (d + 1) * kpad, OZ_S * kpad, C, sCb, sCm, sCn, alpha,
+                  d == 0 ? beta : mkc(1.0), conj_acc, OZ_KCHUNK, useful * (d + 1) / pairs, "gemm_tc_f64emu");
+    }
+}
+
+void gemm_tc_f64(Dev& D, const GemmArgs& g0) {
+    if (g0.M <= 0 || g0.N <= 0 || g0.batch <= 0) return;
+    if (g0.K <= 0) {
+        gemm_f64(D, g0);  // pure beta scaling
+        return;
+    }
+    GemmArgs g = g0;
+    if (orient_cost(g0.N, g0.M, g0.sCn) < orient_cost(g0.M, g0.N, g0.sCm)) {
+        g.M = g0.N; g.N = g0.M;
+        g.A = g0.B; g.sAb = g0.sBb; g.sAm = g0.sBn; g.sAk = g0.sBk; g.cA = g0.cB;
+        g.B = g0.A; g.sBb = g0.sAb; g.sBk = g0.sAk; g.sBn = g0.sAm; g.cB = g0.cA;
+        g.sCm = g0.sCn; g.sCn = g0.sCm;
+    }
+    int64_t rowsA, kpad, rowsB, kpad2;
+    size_t bytesA = oz_embed_bytes(g.M, g.K, g.batch, rowsA, kpad, false);
+    size_t bytesB = oz_embed_bytes(g.N, g.K, g.batch, rowsB, kpad2, true);
+    void* pa = D.pool.get(bytesA);
+    std::shared_ptr<DevBuf> ha(new DevBuf{&D.pool, pa, bytesA});
+    void* pb = D.pool.get(bytesB);
+    std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
+    oz_embed_a(D, g.A, g.sAb, g.sAm, g.sAk, g.cA, g.batch, g.M, g.K, kpad, pa);
+    oz_embed_b(D, g.B, g.sBb, g.sBk, g.sBn, g.cB, g.batch, g.K, g.N, kpad, pb);
+    oz_gemm_embedded(D, pa, pb, g.batch, g.M, g.N, g.K, kpad, g.C, g.sCb, g.sCm, g.sCn, g.alpha, g.beta, false);
+}
+

@@ -17,6 +17,17 @@ void set_global_error(const std::string& msg) { g_setup_err = msg; }
 
 namespace {
 
+bool is_mixed(int prec) { return prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3; }
+
+// precision of the maps that must be FP64-accurate (outer residuals, F X,
+// ground-state polish): FP64 products in the plain FP64 mode, tensor-core
+// integer slices in the emulated mode and (by default) in the mixed modes
+int p64(const lrcc_ctx* c) {
+    if (c->opt.prec == LRCC_FP64) return LRCC_FP64;
+    if (c->opt.prec == LRCC_FP64_EMULATED || c->opt.fp64_products) return LRCC_FP64_EMULATED;
+    return LRCC_FP64;
+}
+
 struct Timer {
     cudaEvent_t a, b;
     Dev& D;
@@ -258,26 +269,26 @@ void do_ground(lrcc_ctx* c, cplx& E, int& itT, int& itL) {
         Timer tm(D);
         // MP2 start: one Jacobi step from T = 0
         Amp T0 = amp_zeros(D, 1, O, V);
-        Amp r0 = residual_T(D, *c->cc, T0, 0, LRCC_FP64);
+        Amp r0 = residual_T(D, *c->cc, T0, 0, p64(c));
         Amp T = amp_empty(D, 1, O, V);
         precond(D, nullptr, r0, T, c->eo, c->ev, sh);
         itT = 0;
-        if (c->opt.prec != LRCC_FP64) {
+        if (is_mixed(c->opt.prec)) {
             // tensor-core residual until it stalls near its own precision, then FP64
             const int p = c->opt.prec;
             auto resm = [&](const Amp& x) { return amp_copy(D, residual_T(D, *c->cc, x, 0, p)); };
             itT += solve_loop(c, T, resm, zero, std::max(1e-6, c->opt.r_tol), c->opt.max_iter, nullptr, false);
         }
-        auto res = [&](const Amp& x) { return amp_copy(D, residual_T(D, *c->cc, x, 0, LRCC_FP64)); };
+        auto res = [&](const Amp& x) { return amp_copy(D, residual_T(D, *c->cc, x, 0, p64(c))); };
         itT += solve_loop(c, T, res, zero, c->opt.r_tol, c->opt.max_iter);
         c->T = amp_copy(D, T);
-        residual_T(D, *c->cc, c->T, 0, LRCC_FP64, &E);  // primal cached at converged T
+        residual_T(D, *c->cc, c->T, 0, p64(c), &E);  // primal cached at converged T
         c->phase_ms[0] = tm.stop();
     }
     {
         // Lambda: A^T lambda = -dE/dT  (same refinement scheme as the left response)
         Timer tm(D);
-        Amp gE = grad_energy(D, *c->cc, O, V, LRCC_FP64);
+        Amp gE = grad_energy(D, *c->cc, O, V, p64(c));
         Amp Lm = amp_empty(D, 1, O, V);
         std::vector<double> res;
         int n64 = 0, nmix = 0;
@@ -310,7 +321,7 @@ Amp fx_product(lrcc_ctx* c, const Amp& X) {
     axpby(D, mkc(0.25), c->Lam.t2, false, mkc(0.0), l2);
     Tensor ce = empty(D, {1});
     fill(D, ce, mkc(1.0));
-    std::vector<Tensor> d = cp.P.jvp_of_vjp(D, {X.t1, X.t2}, {c->Lam.t1, l2, ce}, {cp.R1, cp.R2, cp.E}, LRCC_FP64);
+    std::vector<Tensor> d = cp.P.jvp_of_vjp(D, {X.t1, X.t2}, {c->Lam.t1, l2, ce}, {cp.R1, cp.R2, cp.E}, p64(c));
     (void)O;
     (void)V;
     (void)R;
@@ -331,13 +342,13 @@ void response_solve(lrcc_ctx* c, Amp& z, const Amp& b, const std::vector<double>
     int O = c->O, V = c->V;
     precond(D, nullptr, b, z, c->eo, c->ev, shift_dev);
     auto res64 = [&](const Amp& x) {
-        Amp s = apply(x, LRCC_FP64);
+        Amp s = apply(x, p64(c));
         n64++;
         Amp r = amp_empty(D, R, O, V);
         combine(D, s, x, shift_dev, &b, r);
         return r;
     };
-    if (c->opt.prec == LRCC_FP64) {
+    if (!is_mixed(c->opt.prec)) {
         solve_loop(c, z, res64, shift, c->opt.x_tol, c->opt.max_iter, &final_res);
         return;
     }
@@ -604,6 +615,7 @@ void lrcc_default_options(lrcc_options* o) {
     o->plus_omega = 0;
     o->slab_rows = 0;
     o->pm_omega = 0;
+    o->fp64_products = 1;
 }
 
 const char* lrcc_last_error(const lrcc_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
@@ -644,7 +656,7 @@ lrcc_status lrcc_setup(const double* eps, const double* B, int L, const double* 
         c = new lrcc_ctx();
         if (opt) c->opt = *opt;
         else lrcc_default_options(&c->opt);
-        REQUIRE(c->opt.prec >= LRCC_FP64 && c->opt.prec <= LRCC_MIXED_BF16X3, "bad precision mode");
+        REQUIRE(c->opt.prec >= LRCC_FP64 && c->opt.prec <= LRCC_FP64_EMULATED, "bad precision mode");
         REQUIRE(c->opt.max_iter >= 1 && c->opt.diis_size >= 2 && c->opt.rhs_chunk >= 1, "bad solver options");
         int dev = 0;
         CK(cudaGetDevice(&dev));
@@ -730,7 +742,7 @@ static lrcc_status residual_impl(lrcc_ctx* c, int kind, const double* t, const d
     int64_t n1 = O * V, n2 = O * O * V * V, nt = n1 + n2;
     REQUIRE(R >= 1 && in && out, "bad residual arguments");
     REQUIRE(kind >= LRCC_RES_T && kind <= LRCC_RES_VJP_FULL, "bad residual kind");
-    REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_MIXED_BF16X3, "bad precision");
+    REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_FP64_EMULATED, "bad precision");
     ensure_ham(c);
     // stage inputs as [R][nt] on the device
     Tensor inb;
@@ -885,7 +897,7 @@ lrcc_status lrcc_ladder_dev(lrcc_ctx* c, const double* x, double* z, int R, int 
     if (!c) return LRCC_EINVAL;
     try {
         REQUIRE(x && z && R >= 1, "bad ladder arguments");
-        REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_MIXED_BF16X3, "bad precision");
+        REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_FP64_EMULATED, "bad precision");
         ensure_ham(c);
         cudaStream_t st = (cudaStream_t)stream;
         cudaEvent_t ev;
@@ -913,7 +925,7 @@ lrcc_status lrcc_ladder_packed_dev(lrcc_ctx* c, const double* xt, double* zt, in
     if (!c) return LRCC_EINVAL;
     try {
         REQUIRE(xt && zt && ncol >= 1, "bad ladder arguments");
-        REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_MIXED_BF16X3, "bad precision");
+        REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_FP64_EMULATED, "bad precision");
         ensure_bvv(c);
         cudaStream_t st = (cudaStream_t)stream;
         cudaEvent_t ev;

@@ -229,6 +229,19 @@ void tc_embed_a(Dev& D, int prec, const cplx* A, int64_t sAb, int64_t sAm, int64
                 int64_t M, int64_t K, int64_t pitch, void* out);
 void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64_t sBn, bool cB, int64_t batch,
                 int64_t K, int64_t N, int64_t pitch, void* out);
+// FP64-class complex GEMM on bf16 tensor cores (integer slices with per-row
+// exponents, exact FP32 chains, FP64 sums): gemm_tc_f64 is the whole GEMM;
+// the pieces embed operands as [batch][rows_e][7 kpad] bf16 and run the
+// diagonals on them
+void gemm_tc_f64(Dev& D, const GemmArgs& g);
+size_t oz_embed_bytes(int64_t rows, int64_t K, int64_t batch, int64_t& rows_e, int64_t& kpad, bool is_b);
+void oz_embed_a(Dev& D, const cplx* A, int64_t sAb, int64_t sAm, int64_t sAk, bool cA, int64_t batch, int64_t M,
+                int64_t K, int64_t kpad, void* out);
+void oz_embed_b(Dev& D, const cplx* B, int64_t sBb, int64_t sBk, int64_t sBn, bool cB, int64_t batch, int64_t K,
+                int64_t N, int64_t kpad, void* out);
+void oz_gemm_embedded(Dev& D, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N, int64_t K,
+                      int64_t kpad, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha, cplx beta,
+                      bool conj_acc);
 void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
                       int64_t K, int64_t pitch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
                       cplx beta, bool conj_acc, double useful_flops);
@@ -261,9 +274,15 @@ struct LadderCtx {
     std::shared_ptr<DevBuf> bcache;
     int bcache_prec = -1;
     int64_t b_pitch = 0;
-    // cached FP64 <ab||ef> matrix [P_V][P_V] for the FP64 ladder, when it fits
+    // cached FP64 <ab||ef> matrix [P_V][P_V] for the FP64 ladder, when it fits,
+    // built with FP64 (LRCC_FP64) or FP64-class (LRCC_FP64_EMULATED) products
     Tensor w64;
+    int w64_prec = -1;
     bool w64_disabled = false;
+    // that matrix sliced for the FP64-class products
+    std::shared_ptr<DevBuf> ozcache;
+    int64_t oz_kpad = 0;
+    bool ozcache_disabled = false;
 };
 void ladder(Dev& D, LadderCtx& L, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose, int prec);
 // packed form: Zt[n][ab] = sum_{e<f} <ab||ef> Xt[n][ef] (transpose: conj <ab||ef>),

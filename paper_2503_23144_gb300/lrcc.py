@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_lrcc.so")
 
 LRCC_OK, LRCC_EINVAL, LRCC_ENOMEM, LRCC_ENOCONV, LRCC_ETIMEOUT, LRCC_ECUDA, LRCC_ESTATE = range(7)
-LRCC_FP64, LRCC_MIXED_TF32, LRCC_MIXED_BF16X3 = 0, 1, 2
+LRCC_FP64, LRCC_MIXED_TF32, LRCC_MIXED_BF16X3, LRCC_FP64_EMULATED = 0, 1, 2, 3
 LRCC_RES_T, LRCC_RES_SIGMA, LRCC_RES_VJP, LRCC_RES_XI, LRCC_RES_ENERGY, LRCC_RES_VJP_FULL = range(6)
 
 STATUS_NAMES = {0: "LRCC_OK", 1: "LRCC_EINVAL", 2: "LRCC_ENOMEM", 3: "LRCC_ENOCONV", 4: "LRCC_ETIMEOUT",
@@ -28,7 +28,7 @@ class lrcc_options(ctypes.Structure):
     _fields_ = [("r_tol", ctypes.c_double), ("x_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_size", ctypes.c_int), ("rhs_chunk", ctypes.c_int), ("prec", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("plus_omega", ctypes.c_int), ("slab_rows", ctypes.c_int),
-                ("pm_omega", ctypes.c_int)]
+                ("pm_omega", ctypes.c_int), ("fp64_products", ctypes.c_int)]
 
 
 class LrccError(RuntimeError):
