@@ -35,12 +35,19 @@ template <> struct CT<double> {
     __device__ static C cvt(cplx v) { return v; }
     __device__ static cplx back(C v) { return v; }
     __device__ static C zero() { return make_double2(0.0, 0.0); }
+    __device__ static cplx scale(C v, cplx a) { return make_double2(a.x * v.x - a.y * v.y, a.x * v.y + a.y * v.x); }
 };
 template <> struct CT<float> {
     typedef float2 C;
     __device__ static C cvt(cplx v) { return make_float2((float)v.x, (float)v.y); }
     __device__ static cplx back(C v) { return make_double2((double)v.x, (double)v.y); }
     __device__ static C zero() { return make_float2(0.f, 0.f); }
+    // alpha applied in FP32: the FP64 pipe (2 FMA per SM per clock on GB300)
+    // is left to the adds into C
+    __device__ static cplx scale(C v, cplx a) {
+        const float ax = (float)a.x, ay = (float)a.y;
+        return make_double2((double)(ax * v.x - ay * v.y), (double)(ax * v.y + ay * v.x));
+    }
 };
 
 struct GemmK {
@@ -144,6 +151,7 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
     cplx* C = g.C + b * g.sCb;
     // old C values first (all loads in flight together), then the stores
     const bool rd = !g.atomic && (g.beta.x != 0.0 || g.beta.y != 0.0);
+    const bool beta1 = rd && g.beta.x == 1.0 && g.beta.y == 0.0;
     cplx old[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -160,16 +168,20 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
         for (int j = 0; j < 4; ++j) {
             int64_t n = n0 + tx + 16 * j;
             if (n >= g.N) continue;
-            cplx v = CT<T>::back(acc[i][j]);
-            cplx r = make_double2(g.alpha.x * v.x - g.alpha.y * v.y, g.alpha.x * v.y + g.alpha.y * v.x);
+            cplx r = CT<T>::scale(acc[i][j], g.alpha);
             cplx* c = C + m * g.sCm + n * g.sCn;
             if (g.atomic) {
                 atomicAdd(&c->x, r.x);
                 atomicAdd(&c->y, r.y);
             } else {
                 const cplx o = old[i][j];
-                r.x += g.beta.x * o.x - g.beta.y * o.y;
-                r.y += g.beta.x * o.y + g.beta.y * o.x;
+                if (beta1) {
+                    r.x += o.x;
+                    r.y += o.y;
+                } else if (rd) {
+                    r.x += g.beta.x * o.x - g.beta.y * o.y;
+                    r.y += g.beta.x * o.y + g.beta.y * o.x;
+                }
                 *c = r;
             }
         }
@@ -220,6 +232,7 @@ __global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
     if (m >= g.M) return;
     cplx* C = g.C + b * g.sCb;
     const bool rd = !g.atomic && (g.beta.x != 0.0 || g.beta.y != 0.0);
+    const bool beta1 = rd && g.beta.x == 1.0 && g.beta.y == 0.0;
     cplx old[NMAX];
 #pragma unroll
     for (int n = 0; n < NMAX; ++n)
@@ -227,8 +240,7 @@ __global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
 #pragma unroll
     for (int n = 0; n < NMAX; ++n) {
         if (n >= N) break;
-        cplx v = CT<T>::back(acc[n]);
-        cplx r = make_double2(g.alpha.x * v.x - g.alpha.y * v.y, g.alpha.x * v.y + g.alpha.y * v.x);
+        cplx r = CT<T>::scale(acc[n], g.alpha);
         cplx* c = C + m * g.sCm + n * g.sCn;
         if (g.atomic) {
             atomicAdd(&c->x, r.x);
@@ -236,8 +248,13 @@ __global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
             continue;
         }
         const cplx o = old[n];
-        r.x += g.beta.x * o.x - g.beta.y * o.y;
-        r.y += g.beta.x * o.y + g.beta.y * o.x;
+        if (beta1) {
+            r.x += o.x;
+            r.y += o.y;
+        } else if (rd) {
+            r.x += g.beta.x * o.x - g.beta.y * o.y;
+            r.y += g.beta.x * o.y + g.beta.y * o.x;
+        }
         *c = r;
     }
 }

@@ -136,13 +136,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// FP64 work in the epilogue is kept to the adds into C (GB300 issues two FP64
+// FMAs per SM per clock): alpha scales the FP32 accumulator in FP32 unless
+// the products are exact integer chains (exact_alpha), and beta = 0 / 1 skip
+// their multiplies.
 struct Epi {
     int64_t M, N;
     cplx* C;
     int64_t sCb, sCm, sCn;
     cplx alpha, beta;
-    int conj_acc;  // use conj(accumulator): conj(A.conj(B)) = conj(A).B
-    int atomic;    // split-K: accumulate alpha*acc into C with FP64 atomics (C pre-scaled)
+    int conj_acc;     // use conj(accumulator): conj(A.conj(B)) = conj(A).B
+    int atomic;       // split-K: accumulate alpha*acc into C with FP64 atomics (C pre-scaled)
+    int exact_alpha;  // apply alpha in FP64 (accumulators that are exact sums)
 };
 
 // Work units of the persistent kernel: (M tile, N tile, batch, K split).
@@ -310,6 +315,9 @@ __global__ void __launch_bounds__(192, 1)
         // epilogue: FP32 accumulator pairs (Re, Im) -> alpha * acc (+ beta C) in FP64
         const int q = warp & 3;
         const bool beta0 = ep.beta.x == 0.0 && ep.beta.y == 0.0;
+        const bool beta1 = ep.beta.x == 1.0 && ep.beta.y == 0.0;
+        const bool alpha1 = ep.alpha.x == 1.0 && ep.alpha.y == 0.0;
+        const float afx = (float)ep.alpha.x, afy = (float)ep.alpha.y;
         int ti = 0;
         bool ok = true;
         for (long long u = blockIdx.x; ok && u < sc.units; u += gridDim.x) {
@@ -319,7 +327,7 @@ __global__ void __launch_bounds__(192, 1)
                 // first chunk: C = alpha acc + beta C; later chunks: C += alpha acc
                 const bool first = c0 == kb0;
                 const bool rd = !ep.atomic && (!first || !beta0);
-                const cplx bc = first ? ep.beta : make_double2(1.0, 0.0);
+                const bool add1 = !first || beta1;  // old C enters with factor 1
                 const int acc = ti & 1;
                 if (!warp_wait(&accf[acc], (uint32_t)(ti >> 1) & 1u, err, wait_limit)) {
                     ok = false;
@@ -345,19 +353,32 @@ __global__ void __launch_bounds__(192, 1)
                         for (int j = 0; j < 16; ++j) {
                             const int64_t n = n0 + j;
                             if (n < ep.N) {
-                                double re = (double)__uint_as_float(r[2 * j]);
-                                double im = (double)__uint_as_float(r[2 * j + 1]);
-                                if (ep.conj_acc) im = -im;
+                                const float fr = __uint_as_float(r[2 * j]);
+                                const float fi = ep.conj_acc ? -__uint_as_float(r[2 * j + 1])
+                                                             : __uint_as_float(r[2 * j + 1]);
+                                cplx v;
+                                if (alpha1) {
+                                    v = make_double2((double)fr, (double)fi);
+                                } else if (ep.exact_alpha) {
+                                    const double re = fr, im = fi;
+                                    v = make_double2(ep.alpha.x * re - ep.alpha.y * im,
+                                                     ep.alpha.x * im + ep.alpha.y * re);
+                                } else {
+                                    v = make_double2((double)(afx * fr - afy * fi), (double)(afx * fi + afy * fr));
+                                }
                                 cplx* cp = Cb + m * ep.sCm + n * ep.sCn;
-                                cplx v = make_double2(ep.alpha.x * re - ep.alpha.y * im,
-                                                      ep.alpha.x * im + ep.alpha.y * re);
                                 if (ep.atomic) {
                                     atomicAdd(&cp->x, v.x);
                                     atomicAdd(&cp->y, v.y);
                                     continue;
                                 }
-                                v.x += bc.x * old[j].x - bc.y * old[j].y;
-                                v.y += bc.x * old[j].y + bc.y * old[j].x;
+                                if (add1) {
+                                    v.x += old[j].x;
+                                    v.y += old[j].y;
+                                } else if (!beta0) {
+                                    v.x += ep.beta.x * old[j].x - ep.beta.y * old[j].y;
+                                    v.y += ep.beta.x * old[j].y + ep.beta.y * old[j].x;
+                                }
                                 *cp = v;
                             }
                         }
@@ -397,15 +418,33 @@ __device__ __forceinline__ uint32_t bf2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
+// FP64 -> FP32 by truncating the significand, from the IEEE-754 bit fields with
+// integer operations only (GB300 issues two FP64 instructions per SM per clock,
+// which made FP64-side conversions the bottleneck of these memory-bound
+// kernels).  Magnitudes below the FP32 normal range flush to zero; overflow
+// gives infinity; NaN stays NaN.  The dropped bits are below 2^-23 relative,
+// far under the 2^-17 of the bf16x3 split and the 2^-11 of TF32.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0x7FF)
+        return __uint_as_float(sign | 0x7F800000u | ((b & 0xFFFFFFFFFFFFFull) ? 0x400000u : 0u));
+    const int ef = ex - 1023 + 127;
+    if (ef <= 0) return __uint_as_float(sign);
+    if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((uint32_t)ef << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
+}
+
 // store the embedding of v = op(S)[b][r][k]: A rows (slots S*k..) or the B row
 // pair (2r: real output, 2r+1: imaginary output)
 template <int KIND, bool IS_B>
 __device__ __forceinline__ void embed_store(void* __restrict__ out, int64_t rows_e, int64_t pitch, int64_t b,
-                                            int64_t r, int64_t k, cplx v) {
+                                            int64_t r, int64_t k, float vr, float vi) {
     if (KIND == 0) {
-        const __nv_bfloat16 rh = __double2bfloat16(v.x), ih = __double2bfloat16(v.y);
-        const __nv_bfloat16 rl = __double2bfloat16(v.x - (double)__bfloat162float(rh));
-        const __nv_bfloat16 il = __double2bfloat16(v.y - (double)__bfloat162float(ih));
+        const __nv_bfloat16 rh = __float2bfloat16(vr), ih = __float2bfloat16(vi);
+        const __nv_bfloat16 rl = __float2bfloat16(vr - __bfloat162float(rh));
+        const __nv_bfloat16 il = __float2bfloat16(vi - __bfloat162float(ih));
         if (!IS_B) {
             uint32_t* o = (uint32_t*)((__nv_bfloat16*)out + (b * rows_e + r) * pitch + 6 * k);
             const uint32_t hh = bf2(rh, ih);
@@ -426,7 +465,7 @@ __device__ __forceinline__ void embed_store(void* __restrict__ out, int64_t rows
             o[2] = im_h;
         }
     } else {
-        const uint32_t br = to_tf32((float)v.x), bi = to_tf32((float)v.y);
+        const uint32_t br = to_tf32(vr), bi = to_tf32(vi);
         if (!IS_B) {
             uint2* o = (uint2*)((uint32_t*)out + (b * rows_e + r) * pitch + 2 * k);
             *o = make_uint2(br, bi);
@@ -460,9 +499,9 @@ __global__ void k_embed(const cplx* __restrict__ S, int64_t sb, int64_t sr, int6
             r = t % Rn;
             b = t / Rn;
         }
-        cplx v = S[b * sb + r * sr + k * sk];
-        if (cj) v.y = -v.y;
-        embed_store<KIND, IS_B>(out, rows_e, pitch, b, r, k, v);
+        const cplx v = S[b * sb + r * sr + k * sk];
+        const float vi = f64_to_f32_rz(v.y);
+        embed_store<KIND, IS_B>(out, rows_e, pitch, b, r, k, f64_to_f32_rz(v.x), cj ? -vi : vi);
     }
 }
 
@@ -488,9 +527,9 @@ __global__ void __launch_bounds__(256) k_embed_t(const cplx* __restrict__ S, int
         for (int j = ty; j < 32; j += 8) {
             const int64_t r = r0 + j, k = k0 + tx;
             if (r < Rn && k < K) {
-                cplx v = tile[tx][j];
-                if (cj) v.y = -v.y;
-                embed_store<KIND, IS_B>(out, rows_e, pitch, b, r, k, v);
+                const cplx v = tile[tx][j];
+                const float vi = f64_to_f32_rz(v.y);
+                embed_store<KIND, IS_B>(out, rows_e, pitch, b, r, k, f64_to_f32_rz(v.x), cj ? -vi : vi);
             }
         }
         __syncthreads();
@@ -514,30 +553,35 @@ __global__ void __launch_bounds__(256) k_embed_t(const cplx* __restrict__ S, int
 // ---------------------------------------------------------------------------
 constexpr int OZ_S = 7, OZ_BITS = 6, OZ_KCHUNK = 64;
 
-// e[b Rn + r]: smallest e with |Re|, |Im| < 2^e over the row (0 for a zero row)
-__device__ __forceinline__ int exp_of(double m) {
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);
-    return e;
+// Row exponents from the IEEE bit fields (integer operations only): for
+// non-negative doubles the bit patterns order like the values, so the row
+// maximum of |Re|, |Im| is an integer maximum; e = biased exponent - 1022 gives
+// max < 2^e (zero rows: e = 0; subnormal maxima: e = -1022).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ int exp_of_bits(unsigned long long m) {
+    if (m == 0) return 0;
+    const int ex = (int)(m >> 52);
+    return ex == 0 ? -1022 : ex - 1022;
 }
 
 // one warp per row, lanes along k
 __global__ void k_row_exp_w(const cplx* __restrict__ S, int64_t sb, int64_t sr, int64_t sk, int64_t batch,
-                            int64_t Rn, int64_t K, int cj, int* __restrict__ e) {
-    (void)cj;
+                            int64_t Rn, int64_t K, int* __restrict__ e) {
     const int lane = threadIdx.x & 31;
     const int64_t rows = batch * Rn;
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < rows;
          row += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int64_t b = row / Rn, r = row % Rn;
         const cplx* p = S + b * sb + r * sr;
-        double m = 0.0;
+        unsigned long long m = 0;
         for (int64_t k = lane; k < K; k += 32) {
             const cplx v = p[k * sk];
-            m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+            m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
         }
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) e[row] = exp_of(m);
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) e[row] = exp_of_bits(m);
     }
 }
 
@@ -550,13 +594,39 @@ __global__ void k_row_exp_t(const cplx* __restrict__ S, int64_t sb, int64_t sr, 
          row += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = row / Rn, r = row % Rn;
         const cplx* p = S + b * sb + r * sr;
-        double m = 0.0;
+        unsigned long long m = 0;
         for (int64_t k = 0; k < K; ++k) {
             const cplx v = p[k * sk];
-            m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+            m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
         }
-        e[row] = exp_of(m);
+        e[row] = exp_of_bits(m);
     }
+}
+
+// F = floor(|x| 2^(OZ_BITS OZ_S - e)) from the bit fields: x = M 2^(ex - 1075)
+// with the 53-bit integer M; |x| < 2^e keeps F below 2^(OZ_BITS OZ_S).
+// Its base-2^OZ_BITS digits, most significant first, are the slices' digits
+// (truncation toward zero of |x|; the sign is carried separately).
+__device__ __forceinline__ unsigned long long oz_fixed(double x, int e, uint32_t& sign) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    sign = (uint32_t)(b >> 63);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0) return 0;  // zero; subnormals lie below every slice kept
+    const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = ex - 1075 - e + OZ_BITS * OZ_S;
+    if (sh >= 0) return M << sh;
+    return sh <= -64 ? 0ull : (M >> (-sh));
+}
+
+// bf16 bit pattern of sign * d * 2^p for a digit 0 <= d < 2^OZ_BITS (exact:
+// d has at most 6 significant bits); below the bf16 normal range -> zero
+__device__ __forceinline__ uint32_t bf16_digit(uint32_t d, int p, uint32_t sign) {
+    if (d == 0) return 0u;
+    const int len = 32 - __clz(d);
+    const int be = p + len - 1 + 127;
+    if (be <= 0) return 0u;
+    if (be >= 255) return (sign << 15) | 0x7F80u;
+    return (sign << 15) | ((uint32_t)be << 7) | ((d << (8 - len)) & 0x7Fu);
 }
 
 // slices of v = op(S)[b][r][k] with row exponent e.  A rows: slice s at
@@ -565,25 +635,25 @@ __global__ void k_row_exp_t(const cplx* __restrict__ S, int64_t sb, int64_t sr, 
 // real row (Re, -Im), imaginary row (Im, Re).
 template <bool IS_B>
 __device__ __forceinline__ void oz_store(void* __restrict__ out, int64_t rows_e, int64_t kpad, int64_t b, int64_t r,
-                                         int64_t k, cplx v, int e) {
+                                         int64_t k, cplx v, bool conj, int e) {
     const int64_t pitch = OZ_S * kpad;
-    __nv_bfloat16* row = (__nv_bfloat16*)out + (b * rows_e + (IS_B ? 2 * r : r)) * pitch + 2 * k;
-    double yr = ldexp(v.x, -e), yi = ldexp(v.y, -e);
+    uint16_t* row = (uint16_t*)out + (b * rows_e + (IS_B ? 2 * r : r)) * pitch + 2 * k;
+    uint32_t sr, si;
+    const unsigned long long Fr = oz_fixed(v.x, e, sr), Fi = oz_fixed(v.y, e, si);
+    if (conj) si ^= 1u;
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
-        yr *= double(1 << OZ_BITS);
-        yi *= double(1 << OZ_BITS);
-        const double dr = trunc(yr), di = trunc(yi);
-        yr -= dr;
-        yi -= di;
-        const double sc = ldexp(1.0, e - OZ_BITS * (s + 1));
-        const __nv_bfloat16 hr = __double2bfloat16(dr * sc), hi = __double2bfloat16(di * sc);
+        const int sh = OZ_BITS * (OZ_S - 1 - s), p = e - OZ_BITS * (s + 1);
+        const uint32_t dr = (uint32_t)(Fr >> sh) & ((1u << OZ_BITS) - 1u);
+        const uint32_t di = (uint32_t)(Fi >> sh) & ((1u << OZ_BITS) - 1u);
+        const uint32_t hr = bf16_digit(dr, p, sr), hi = bf16_digit(di, p, si);
         if (!IS_B) {
-            *(uint32_t*)(row + s * kpad) = bf2(hr, hi);
+            *(uint32_t*)(row + s * kpad) = hr | (hi << 16);
         } else {
             const int64_t off = (OZ_S - 1 - s) * kpad;
-            *(uint32_t*)(row + off) = bf2(hr, __hneg(hi));
-            *(uint32_t*)(row + pitch + off) = bf2(hi, hr);
+            const uint32_t nhi = hi ? hi ^ 0x8000u : 0u;
+            *(uint32_t*)(row + off) = hr | (nhi << 16);
+            *(uint32_t*)(row + pitch + off) = hi | (hr << 16);
         }
     }
 }
@@ -611,8 +681,7 @@ __global__ void k_oz_embed(const cplx* __restrict__ S, int64_t sb, int64_t sr, i
         }
         cplx v = make_double2(0.0, 0.0);
         if (k < K) v = S[b * sb + r * sr + k * sk];
-        if (cj) v.y = -v.y;
-        oz_store<IS_B>(out, rows_e, kpad, b, r, k, v, e[b * Rn + r]);
+        oz_store<IS_B>(out, rows_e, kpad, b, r, k, v, cj != 0, e[b * Rn + r]);
     }
 }
 
@@ -638,11 +707,7 @@ __global__ void __launch_bounds__(256) k_oz_embed_t(const cplx* __restrict__ S, 
         __syncthreads();
         for (int j = ty; j < 32; j += 8) {
             const int64_t r = r0 + j, k = k0 + tx;
-            if (r < Rn && k < K2) {
-                cplx v = tile[tx][j];
-                if (cj) v.y = -v.y;
-                oz_store<IS_B>(out, rows_e, kpad, b, r, k, v, e[b * Rn + r]);
-            }
+            if (r < Rn && k < K2) oz_store<IS_B>(out, rows_e, kpad, b, r, k, tile[tx][j], cj != 0, e[b * Rn + r]);
         }
         __syncthreads();
     }
@@ -698,7 +763,8 @@ __global__ void __launch_bounds__(256) k_embed_antisym(const cplx* __restrict__ 
             if (e < f && f < V) {
                 const cplx u = t1[tx][j], w = t2[j][tx];
                 const int64_t ef = e * (2 * V - e - 1) / 2 + (f - e - 1);
-                embed_store<KIND, false>(out, nrows, pitch, 0, row, ef, make_double2(u.x - w.x, u.y - w.y));
+                embed_store<KIND, false>(out, nrows, pitch, 0, row, ef, f64_to_f32_rz(u.x - w.x),
+                                         f64_to_f32_rz(u.y - w.y));
             }
         }
         __syncthreads();
@@ -824,7 +890,8 @@ void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64
 // kchunk k-blocks, added to C in FP64.
 static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
                       int64_t kd, int64_t pitch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
-                      cplx beta, bool conj_acc, int kchunk, double useful_flops, const char* name) {
+                      cplx beta, bool conj_acc, int kchunk, bool exact_alpha, double useful_flops,
+                      const char* name) {
     REQUIRE(D.err_flag != nullptr, "gemm_tc: no error word");
     if (M <= 0 || N <= 0 || batch <= 0) return;
     const int64_t es = kind == 0 ? 2 : 4, kelem = ROWB / es;
@@ -869,7 +936,7 @@ static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t 
     sc.kchunk = kchunk;
     sc.units = (long long)tiles * splits;
     REQUIRE(batch < INT32_MAX, "gemm_tc: batch too large");
-    Epi ep{M, N, C, sCb, sCm, sCn, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0};
+    Epi ep{M, N, C, sCb, sCm, sCn, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0, exact_alpha ? 1 : 0};
     if (splits > 1) {
         GemmArgs pg{};
         pg.M = M; pg.N = N; pg.batch = batch; pg.C = C; pg.sCb = sCb; pg.sCm = sCm; pg.sCn = sCn; pg.beta = beta;
@@ -904,7 +971,7 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
     const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
     REQUIRE(K > 0, "gemm_tc: bad embedded K");
     tc_launch(D, kind, pa, pb, batch, M, N, slots(kind) * K, pitch, C, sCb, sCm, sCn, alpha, beta, conj_acc, KCHUNK,
-              useful_flops, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32");
+              false, useful_flops, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32");
 }
 
 // relative cost of running C[M][N] in this orientation: padded tensor-core
@@ -977,7 +1044,7 @@ static void oz_embed(Dev& D, bool is_b, const cplx* S, int64_t sb, int64_t sr, i
                       D.st>>>(S, sb, sr, sk, batch, Rn, K, e);
     } else {
         k_row_exp_w<<<(int)std::max<int64_t>(1, std::min<int64_t>((rows * 32 + 255) / 256, D.sm_count * 16)), 256,
-                      0, D.st>>>(S, sb, sr, sk, batch, Rn, K, 0, e);
+                      0, D.st>>>(S, sb, sr, sk, batch, Rn, K, e);
     }
     LAUNCH_CHECK(D);
     const int64_t K2 = kpad / 2, rows_e = is_b ? 2 * Rn : Rn;
@@ -1021,7 +1088,7 @@ void oz_gemm_embedded(Dev& D, const void* pa, const void* pb, int64_t batch, int
     for (int d = 0; d < OZ_S; ++d) {
         const char* pbd = (const char*)pb + (size_t)((OZ_S - 1 - d) * kpad * 2);
         tc_launch(D, 0, pa, pbd, batch, M, N, (d + 1) * kpad, OZ_S * kpad, C, sCb, sCm, sCn, alpha,
-                  d == 0 ? beta : mkc(1.0), conj_acc, OZ_KCHUNK, useful * (d + 1) / pairs, "gemm_tc_f64emu");
+                  d == 0 ? beta : mkc(1.0), conj_acc, OZ_KCHUNK, true, useful * (d + 1) / pairs, "gemm_tc_f64emu");
     }
 }
 

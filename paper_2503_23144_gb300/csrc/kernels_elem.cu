@@ -159,18 +159,37 @@ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// a * v with the kind of the coefficient decided once per launch (0: +1,
+// 1: -1, 2: real, 3: complex): GB300 issues two FP64 FMAs per SM per clock,
+// so these memory-bound kernels spend FP64 work only where a coefficient needs it
+__device__ __forceinline__ cplx cscale(cplx a, int k, cplx v) {
+    if (k == 0) return v;
+    if (k == 1) return make_double2(-v.x, -v.y);
+    if (k == 2) return make_double2(a.x * v.x, a.x * v.y);
+    return cmul(a, v);
+}
+
+static int ckind(cplx a) {
+    if (a.y == 0.0) {
+        if (a.x == 1.0) return 0;
+        if (a.x == -1.0) return 1;
+        return 2;
+    }
+    return 3;
+}
+
 template <bool BETA0>
-__global__ void k_axpby(ShapeStrides ss, int64_t n, cplx alpha, const cplx* __restrict__ x, int conjx,
-                        cplx beta, cplx* __restrict__ y) {
+__global__ void k_axpby(ShapeStrides ss, int64_t n, cplx alpha, int ka, const cplx* __restrict__ x, int conjx,
+                        cplx beta, int kb, cplx* __restrict__ y) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         int64_t ox, oy;
         offsets2(ss, idx, ox, oy);
         cplx v = x[ox];
         if (conjx) v.y = -v.y;
-        v = cmul(alpha, v);
+        v = cscale(alpha, ka, v);
         if (!BETA0) {
-            cplx w = cmul(beta, y[oy]);
+            cplx w = cscale(beta, kb, y[oy]);
             v.x += w.x;
             v.y += w.y;
         }
@@ -189,15 +208,15 @@ __global__ void k_fill(ShapeStrides ss, int64_t n, cplx v, cplx* __restrict__ y)
 
 // contiguous fast path
 template <bool BETA0>
-__global__ void k_axpby_contig(int64_t n, cplx alpha, const cplx* __restrict__ x, int conjx, cplx beta,
-                               cplx* __restrict__ y) {
+__global__ void k_axpby_contig(int64_t n, cplx alpha, int ka, const cplx* __restrict__ x, int conjx, cplx beta,
+                               int kb, cplx* __restrict__ y) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         cplx v = x[idx];
         if (conjx) v.y = -v.y;
-        v = cmul(alpha, v);
+        v = cscale(alpha, ka, v);
         if (!BETA0) {
-            cplx w = cmul(beta, y[idx]);
+            cplx w = cscale(beta, kb, y[idx]);
             v.x += w.x;
             v.y += w.y;
         }
@@ -256,7 +275,7 @@ struct TStr {
 };
 
 template <bool BETA0>
-__global__ void k_transpose(TStr t, cplx alpha, const cplx* __restrict__ x, int conjx, cplx beta,
+__global__ void k_transpose(TStr t, cplx alpha, int ka, const cplx* __restrict__ x, int conjx, cplx beta, int kb,
                             cplx* __restrict__ y) {
     __shared__ cplx tile[32][33];
     const int64_t tiles_x = (t.nx + 31) / 32;
@@ -284,12 +303,12 @@ __global__ void k_transpose(TStr t, cplx alpha, const cplx* __restrict__ x, int 
             int64_t iy = ty0 + threadIdx.x, ix = tx0 + j;
             if (ix < t.nx && iy < t.ny) {
                 cplx v = tile[threadIdx.x][j];
-                cplx o = make_double2(alpha.x * v.x - alpha.y * v.y, alpha.x * v.y + alpha.y * v.x);
+                cplx o = cscale(alpha, ka, v);
                 cplx* yp = y + oy + iy + ix * t.syx;
                 if (!BETA0) {
-                    cplx w = *yp;
-                    o.x += beta.x * w.x - beta.y * w.y;
-                    o.y += beta.x * w.y + beta.y * w.x;
+                    const cplx w = cscale(beta, kb, *yp);
+                    o.x += w.x;
+                    o.y += w.y;
                 }
                 *yp = o;
             }
@@ -325,8 +344,9 @@ static bool try_transpose(Dev& D, cplx alpha, const ShapeStrides& ss, const cplx
     dim3 block(32, 8);
     dim3 grid((unsigned)tiles, (unsigned)std::min<int64_t>(t.nbatch, 65535));
     bool beta0 = beta.x == 0.0 && beta.y == 0.0;
-    if (beta0) k_transpose<true><<<grid, block, 0, D.st>>>(t, alpha, x, conjx, beta, y);
-    else k_transpose<false><<<grid, block, 0, D.st>>>(t, alpha, x, conjx, beta, y);
+    const int ka = ckind(alpha), kb = ckind(beta);
+    if (beta0) k_transpose<true><<<grid, block, 0, D.st>>>(t, alpha, ka, x, conjx, beta, kb, y);
+    else k_transpose<false><<<grid, block, 0, D.st>>>(t, alpha, ka, x, conjx, beta, kb, y);
     LAUNCH_CHECK(D);
     return true;
 }
@@ -341,13 +361,13 @@ void axpby(Dev& D, cplx alpha, const Tensor& x, bool conjx, cplx beta, Tensor& y
     int th = 256, g = grid_for(D, n, th);
     ShapeStrides ss = simplify(x, y);
     if (ss.nd == 1 && ss.sx[0] == 1 && ss.sy[0] == 1) {
-        if (beta0) k_axpby_contig<true><<<g, th, 0, D.st>>>(n, alpha, x.p, conjx, beta, y.p);
-        else k_axpby_contig<false><<<g, th, 0, D.st>>>(n, alpha, x.p, conjx, beta, y.p);
+        if (beta0) k_axpby_contig<true><<<g, th, 0, D.st>>>(n, alpha, ckind(alpha), x.p, conjx, beta, 0, y.p);
+        else k_axpby_contig<false><<<g, th, 0, D.st>>>(n, alpha, ckind(alpha), x.p, conjx, beta, ckind(beta), y.p);
     } else if (try_transpose(D, alpha, ss, x.p, conjx, beta, y.p)) {
         return;
     } else {
-        if (beta0) k_axpby<true><<<g, th, 0, D.st>>>(ss, n, alpha, x.p, conjx, beta, y.p);
-        else k_axpby<false><<<g, th, 0, D.st>>>(ss, n, alpha, x.p, conjx, beta, y.p);
+        if (beta0) k_axpby<true><<<g, th, 0, D.st>>>(ss, n, alpha, ckind(alpha), x.p, conjx, beta, 0, y.p);
+        else k_axpby<false><<<g, th, 0, D.st>>>(ss, n, alpha, ckind(alpha), x.p, conjx, beta, ckind(beta), y.p);
     }
     LAUNCH_CHECK(D);
 }
@@ -438,8 +458,8 @@ struct Str3 {
 };
 
 template <bool BETA0>
-__global__ void k_outer(Str3 s, int64_t n, cplx alpha, const cplx* __restrict__ a, int ca, const cplx* __restrict__ b,
-                        int cb, cplx beta, cplx* __restrict__ c) {
+__global__ void k_outer(Str3 s, int64_t n, cplx alpha, int ka, const cplx* __restrict__ a, int ca,
+                        const cplx* __restrict__ b, int cb, cplx beta, int kb, cplx* __restrict__ c) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         int64_t oa = 0, ob = 0, oc = 0;
@@ -466,9 +486,9 @@ __global__ void k_outer(Str3 s, int64_t n, cplx alpha, const cplx* __restrict__ 
         cplx u = a[oa], v = b[ob];
         if (ca) u.y = -u.y;
         if (cb) v.y = -v.y;
-        cplx p = cmul(alpha, cmul(u, v));
+        cplx p = cscale(alpha, ka, cmul(u, v));
         if (!BETA0) {
-            cplx w = cmul(beta, c[oc]);
+            cplx w = cscale(beta, kb, c[oc]);
             p.x += w.x;
             p.y += w.y;
         }
@@ -509,8 +529,9 @@ void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, 
     for (int k = 0; k < s.nd; ++k) s.fd[k] = FastDiv(s.fast ? s.d[k] : 1);
     bool beta0 = beta.x == 0.0 && beta.y == 0.0;
     int th = 256, g = grid_for(D, n, th);
-    if (beta0) k_outer<true><<<g, th, 0, D.st>>>(s, n, alpha, A.p, ca, B.p, cb, beta, C.p);
-    else k_outer<false><<<g, th, 0, D.st>>>(s, n, alpha, A.p, ca, B.p, cb, beta, C.p);
+    const int ka = ckind(alpha), kb = ckind(beta);
+    if (beta0) k_outer<true><<<g, th, 0, D.st>>>(s, n, alpha, ka, A.p, ca, B.p, cb, beta, kb, C.p);
+    else k_outer<false><<<g, th, 0, D.st>>>(s, n, alpha, ka, A.p, ca, B.p, cb, beta, kb, C.p);
     LAUNCH_CHECK(D);
 }
 
@@ -520,8 +541,8 @@ void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, 
 // y = alpha * P x + beta * y.  Each P is its own transpose.
 // ---------------------------------------------------------------------------
 template <bool BETA0>
-__global__ void k_asym(int mode, int64_t n, int64_t O, int64_t V, FastDiv fO, FastDiv fV, cplx alpha,
-                       const cplx* __restrict__ x, cplx beta, cplx* __restrict__ y) {
+__global__ void k_asym(int mode, int64_t n, int64_t O, int64_t V, FastDiv fO, FastDiv fV, cplx alpha, int ka,
+                       const cplx* __restrict__ x, cplx beta, int kb, cplx* __restrict__ y) {
     const int64_t VV = V * V, OVV = O * VV;
     const bool fast = n < FAST_INDEX_LIMIT;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
@@ -567,9 +588,9 @@ __global__ void k_asym(int mode, int64_t n, int64_t O, int64_t V, FastDiv fO, Fa
             v.x += w.x;
             v.y += w.y;
         }
-        v = cmul(alpha, v);
+        v = cscale(alpha, ka, v);
         if (!BETA0) {
-            cplx w = cmul(beta, y[idx]);
+            cplx w = cscale(beta, kb, y[idx]);
             v.x += w.x;
             v.y += w.y;
         }
@@ -588,7 +609,8 @@ void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor
     bool beta0 = beta.x == 0.0 && beta.y == 0.0;
     int th = 256, g = grid_for(D, n, th);
     FastDiv fO(O), fV(V);
-    if (beta0) k_asym<true><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, x.p, beta, y.p);
-    else k_asym<false><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, x.p, beta, y.p);
+    const int ka = ckind(alpha), kb = ckind(beta);
+    if (beta0) k_asym<true><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
+    else k_asym<false><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
     LAUNCH_CHECK(D);
 }
