@@ -77,6 +77,51 @@ Tensor copy_as(Dev& D, const Tensor& T, const std::string& lab, const std::strin
     return out;
 }
 
+// Positions in `order` where the labels stop being adjacent in T (a label of
+// extent 1 never starts a new piece).
+std::vector<int> cuts_of(const Tensor& T, const std::string& lab, const std::vector<char>& order) {
+    std::vector<int> cuts;
+    int64_t prev_s = -1;
+    bool first = true;
+    for (size_t i = 0; i < order.size(); ++i) {
+        int k = pos(lab, order[i]);
+        int64_t d = T.d[k], s = T.s[k];
+        if (d == 1) continue;
+        if (!first && prev_s != s * d) cuts.push_back((int)i);
+        prev_s = s;
+        first = false;
+    }
+    return cuts;
+}
+
+// A group (labels in `order`) shared by tensors T1 and T2 as at most two
+// pieces cut at the same label in both: index g = g1 d2 + g2 at offset
+// g1 s1 + g2 s in each.  Returns false when either tensor needs three pieces
+// or the two need different cuts.
+struct Two {
+    int64_t d2 = 0, s = 0, s1 = 0;  // d2 = 0: flat with stride s
+};
+bool two_level(const Tensor& T1, const std::string& l1, const Tensor& T2, const std::string& l2,
+               const std::vector<char>& order, Two& o1, Two& o2) {
+    std::vector<int> c1 = cuts_of(T1, l1, order), c2 = cuts_of(T2, l2, order), u = c1;
+    for (int c : c2)
+        if (std::find(u.begin(), u.end(), c) == u.end()) u.push_back(c);
+    if (u.size() > 1) return false;
+    int64_t sz;
+    if (u.empty()) {
+        o1 = Two();
+        o2 = Two();
+        return flat(T1, l1, order, sz, o1.s) && flat(T2, l2, order, sz, o2.s);
+    }
+    std::vector<char> outer(order.begin(), order.begin() + u[0]), inner(order.begin() + u[0], order.end());
+    int64_t d2a, d2b, szo;
+    if (!flat(T1, l1, inner, d2a, o1.s) || !flat(T1, l1, outer, szo, o1.s1)) return false;
+    if (!flat(T2, l2, inner, d2b, o2.s) || !flat(T2, l2, outer, szo, o2.s1)) return false;
+    o1.d2 = d2a;
+    o2.d2 = d2b;
+    return true;
+}
+
 std::string cat(const std::vector<char>& a, const std::vector<char>& b, const std::vector<char>& c) {
     std::string s;
     for (char x : a) s += x;
@@ -131,6 +176,39 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
         }
         outer_axpby(D, alpha, Av, cA, Bv, cB, beta, C);
         return;
+    }
+    const bool mixed = prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3;
+    if (mixed && gemm_tc_available()) {
+        // tensor-core GEMMs read and write strided groups of up to two pieces
+        // in place (the embedding and the epilogue decode them), so no
+        // transposed copies are made for them
+        int64_t M = 1, N = 1, K = 1, Bt = 1;
+        for (char c : gm) M *= dim_of(c);
+        for (char c : gn) N *= dim_of(c);
+        for (char c : gk) K *= dim_of(c);
+        for (char c : gb) Bt *= dim_of(c);
+        const double fl = 8.0 * double(M) * double(N) * double(K) * double(Bt);
+        if (fl >= 5e7 && K >= 48 && std::max(M, N) < FAST_INDEX_LIMIT && K < FAST_INDEX_LIMIT) {
+            std::vector<char> ob = order_by(gb, C, sp.c), om = order_by(gm, C, sp.c), on = order_by(gn, C, sp.c);
+            std::vector<char> okk = order_by(gk, A0, sp.a);
+            Two am, cm, bn, cn, ak, bk;
+            int64_t szb, sAb, sBb, sCb;
+            if (flat(A0, sp.a, ob, szb, sAb) && flat(B0, sp.b, ob, szb, sBb) && flat(C, sp.c, ob, szb, sCb) &&
+                two_level(A0, sp.a, C, sp.c, om, am, cm) && two_level(B0, sp.b, C, sp.c, on, bn, cn) &&
+                two_level(A0, sp.a, B0, sp.b, okk, ak, bk)) {
+                GemmArgs g;
+                g.M = M; g.N = N; g.K = K; g.batch = Bt;
+                g.A = A0.p; g.sAb = Bt == 1 ? 0 : sAb; g.sAm = am.s; g.sAk = ak.s; g.cA = cA;
+                g.B = B0.p; g.sBb = Bt == 1 ? 0 : sBb; g.sBk = bk.s; g.sBn = bn.s; g.cB = cB;
+                g.C = C.p; g.sCb = Bt == 1 ? 0 : sCb; g.sCm = cm.s; g.sCn = cn.s;
+                g.alpha = alpha; g.beta = beta;
+                g.dAm2 = am.d2; g.sAm1 = am.s1; g.dAk2 = ak.d2; g.sAk1 = ak.s1;
+                g.dBk2 = bk.d2; g.sBk1 = bk.s1; g.dBn2 = bn.d2; g.sBn1 = bn.s1;
+                g.dCm2 = cm.d2; g.sCm1 = cm.s1; g.dCn2 = cn.d2; g.sCn1 = cn.s1;
+                gemm_tc(D, g, prec);
+                return;
+            }
+        }
     }
     Tensor A = A0, B = B0;
     std::string la = sp.a, lb = sp.b;
@@ -197,7 +275,6 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
     double flops = 8.0 * double(g.M) * double(g.N) * double(g.K) * double(g.batch);
     // mixed mode: every contraction with real work goes to the tensor cores
     // (the O-sized contractions too: FP64 on this part is 1.25 TFLOP/s)
-    const bool mixed = prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3;
     const bool big = gemm_tc_available() && flops >= 5e7 && g.K >= 48;
     if (mixed && big) gemm_tc(D, g, prec);
     else if (mixed) gemm_f32c(D, g);

@@ -301,13 +301,16 @@ __global__ void k_dot(int64_t K, const cplx* A, int64_t sAb, int64_t sAk, int cA
     }
 }
 
-// C[b][m][n] *= beta (strided), beta == 0 -> zero
+// C[b][m][n] *= beta (strided; m and n may be two-level: g = g1 d2 + g2 at
+// offset g1 s1 + g2 s), beta == 0 -> zero
 __global__ void k_scale(int64_t M, int64_t N, int64_t batch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn,
-                        cplx beta) {
+                        int64_t dm2, int64_t sm1, int64_t dn2, int64_t sn1, cplx beta) {
     int64_t total = M * N * batch;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t n = i % N, r = i / N, m = r % M, b = r / M;
-        cplx* c = C + b * sCb + m * sCm + n * sCn;
+        const int64_t mo = dm2 ? (m / dm2) * sm1 + (m % dm2) * sCm : m * sCm;
+        const int64_t no = dn2 ? (n / dn2) * sn1 + (n % dn2) * sCn : n * sCn;
+        cplx* c = C + b * sCb + mo + no;
         if (beta.x == 0.0 && beta.y == 0.0) {
             *c = make_double2(0.0, 0.0);
         } else {
@@ -326,7 +329,8 @@ void gemm_prescale(Dev& D, const GemmArgs& g) {
     if (g.beta.x == 1.0 && g.beta.y == 0.0) return;
     int64_t total = g.M * g.N * g.batch;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, D.sm_count * 16));
-    k_scale<<<grid, 256, 0, D.st>>>(g.M, g.N, g.batch, g.C, g.sCb, g.sCm, g.sCn, g.beta);
+    k_scale<<<grid, 256, 0, D.st>>>(g.M, g.N, g.batch, g.C, g.sCb, g.sCm, g.sCn, g.dCm2, g.sCm1, g.dCn2, g.sCn1,
+                                    g.beta);
     LAUNCH_CHECK(D);
 }
 
@@ -338,6 +342,7 @@ void gemm_f32c(Dev& D, const GemmArgs& g) { gemm_simt<float>(D, g); }
 
 template <typename T>
 static void gemm_simt(Dev& D, const GemmArgs& g) {
+    REQUIRE(g.flat(), "SIMT GEMM: two-level index groups are for the tensor-core path");
     const char* kname = sizeof(T) == 8 ? "gemm_f64" : "gemm_f32";
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
     if (g.K <= 0) {

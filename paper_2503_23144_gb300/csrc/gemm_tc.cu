@@ -136,6 +136,43 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Offset of index g of a GEMM index group: g * s (flat), or with two levels
+// g = g1 d2 + g2 at g1 s1 + g2 s (an einsum group whose labels are not
+// adjacent in memory; d2 < 2^31).
+struct Lvl {
+    int64_t s = 0, s1 = 0;
+    FastDiv f2;
+    int two = 0;
+};
+__device__ __forceinline__ int64_t lvl_off(const Lvl& L, int64_t g) {
+    if (!L.two) return g * L.s;
+    const uint32_t q = L.f2.div((uint32_t)g);
+    return (int64_t)q * L.s1 + (int64_t)((uint32_t)g - q * L.f2.d) * L.s;
+}
+Lvl mk_lvl(int64_t s, int64_t d2 = 0, int64_t s1 = 0) {
+    Lvl L;
+    L.s = s;
+    if (d2 > 0) {
+        L.two = 1;
+        L.s1 = s1;
+        L.f2 = FastDiv(d2);
+    }
+    return L;
+}
+
+// FP32 -> FP64 (exact) from the bit fields with integer operations, keeping
+// conversions off the FP64 pipe; FP32 subnormals (below 1.2e-38) become zero
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = (u >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if (ex == 0) return __longlong_as_double((long long)sign);
+    if (ex == 0xFFu)
+        return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | ((u & 0x7FFFFFu) ? (1ull << 51) : 0ull)));
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(ex - 127 + 1023) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
 // FP64 work in the epilogue is kept to the adds into C (GB300 issues two FP64
 // FMAs per SM per clock): alpha scales the FP32 accumulator in FP32 unless
 // the products are exact integer chains (exact_alpha), and beta = 0 / 1 skip
@@ -143,7 +180,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 struct Epi {
     int64_t M, N;
     cplx* C;
-    int64_t sCb, sCm, sCn;
+    int64_t sCb;
+    Lvl lm, ln;  // output row and column offsets
     cplx alpha, beta;
     int conj_acc;     // use conj(accumulator): conj(A.conj(B)) = conj(A).B
     int atomic;       // split-K: accumulate alpha*acc into C with FP64 atomics (C pre-scaled)
@@ -336,7 +374,7 @@ __global__ void __launch_bounds__(192, 1)
                 tc_fence_after();
                 const int64_t m = (int64_t)tm * BM + q * 32 + lane;
                 const bool live = m < ep.M;
-                cplx* Cb = ep.C + (int64_t)bz * ep.sCb;
+                cplx* Cb = ep.C + (int64_t)bz * ep.sCb + (live ? lvl_off(ep.lm, m) : 0);
 #pragma unroll 1
                 for (int c = 0; c < BN / 32; ++c) {
                     uint32_t r[32];
@@ -345,8 +383,7 @@ __global__ void __launch_bounds__(192, 1)
                     cplx old[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
-                        old[j] = (rd && live && n0 + j < ep.N) ? Cb[m * ep.sCm + (n0 + j) * ep.sCn]
-                                                               : make_double2(0.0, 0.0);
+                        old[j] = (rd && live && n0 + j < ep.N) ? Cb[lvl_off(ep.ln, n0 + j)] : make_double2(0.0, 0.0);
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32), r);
                     if (live) {
 #pragma unroll
@@ -358,15 +395,15 @@ __global__ void __launch_bounds__(192, 1)
                                                              : __uint_as_float(r[2 * j + 1]);
                                 cplx v;
                                 if (alpha1) {
-                                    v = make_double2((double)fr, (double)fi);
+                                    v = make_double2(f32_to_f64(fr), f32_to_f64(fi));
                                 } else if (ep.exact_alpha) {
-                                    const double re = fr, im = fi;
+                                    const double re = f32_to_f64(fr), im = f32_to_f64(fi);
                                     v = make_double2(ep.alpha.x * re - ep.alpha.y * im,
                                                      ep.alpha.x * im + ep.alpha.y * re);
                                 } else {
-                                    v = make_double2((double)(afx * fr - afy * fi), (double)(afx * fi + afy * fr));
+                                    v = make_double2(f32_to_f64(afx * fr - afy * fi), f32_to_f64(afx * fi + afy * fr));
                                 }
-                                cplx* cp = Cb + m * ep.sCm + n * ep.sCn;
+                                cplx* cp = Cb + lvl_off(ep.ln, n);
                                 if (ep.atomic) {
                                     atomicAdd(&cp->x, v.x);
                                     atomicAdd(&cp->y, v.y);
@@ -480,7 +517,7 @@ __device__ __forceinline__ void embed_store(void* __restrict__ out, int64_t rows
 
 // source S[b][r][k] with strides (sb, sr, sk); k fastest across threads
 template <int KIND, bool IS_B>
-__global__ void k_embed(const cplx* __restrict__ S, int64_t sb, int64_t sr, int64_t sk, int cj, int64_t batch,
+__global__ void k_embed(const cplx* __restrict__ S, int64_t sb, Lvl lr, Lvl lk, int cj, int64_t batch,
                         int64_t Rn, int64_t K, FastDiv fR, FastDiv fK, int64_t rows_e, int64_t pitch,
                         void* __restrict__ out) {
     const int64_t total = batch * Rn * K;
@@ -499,7 +536,7 @@ __global__ void k_embed(const cplx* __restrict__ S, int64_t sb, int64_t sr, int6
             r = t % Rn;
             b = t / Rn;
         }
-        const cplx v = S[b * sb + r * sr + k * sk];
+        const cplx v = S[b * sb + lvl_off(lr, r) + lvl_off(lk, k)];
         const float vi = f64_to_f32_rz(v.y);
         embed_store<KIND, IS_B>(out, rows_e, pitch, b, r, k, f64_to_f32_rz(v.x), cj ? -vi : vi);
     }
@@ -507,7 +544,7 @@ __global__ void k_embed(const cplx* __restrict__ S, int64_t sb, int64_t sr, int6
 
 // the same for sources contiguous in r: 32x32 tiles read along r, written along k
 template <int KIND, bool IS_B>
-__global__ void __launch_bounds__(256) k_embed_t(const cplx* __restrict__ S, int64_t sb, int64_t sk, int cj,
+__global__ void __launch_bounds__(256) k_embed_t(const cplx* __restrict__ S, int64_t sb, Lvl lr, Lvl lk, int cj,
                                                  int64_t batch, int64_t Rn, int64_t K, int64_t rows_e,
                                                  int64_t pitch, void* __restrict__ out) {
     __shared__ cplx tile[32][33];
@@ -520,7 +557,7 @@ __global__ void __launch_bounds__(256) k_embed_t(const cplx* __restrict__ S, int
         for (int j = ty; j < 32; j += 8) {
             const int64_t r = r0 + tx, k = k0 + j;
             cplx v = make_double2(0.0, 0.0);
-            if (r < Rn && k < K) v = S[b * sb + r + k * sk];
+            if (r < Rn && k < K) v = S[b * sb + lvl_off(lr, r) + lvl_off(lk, k)];
             tile[j][tx] = v;
         }
         __syncthreads();
@@ -852,36 +889,46 @@ size_t tc_embed_bytes(int prec, int64_t rows, int64_t K, int64_t batch, int64_t&
     return (size_t)(batch * rows_e * pitch * es);
 }
 
-void tc_embed_a(Dev& D, int prec, const cplx* A, int64_t sAb, int64_t sAm, int64_t sAk, bool cA, int64_t batch,
-                int64_t M, int64_t K, int64_t pitch, void* out) {
-    if (batch * M * K == 0) return;
-    const bool tiled = sAm == 1 && sAk != 1;
-    const int64_t nt = batch * ((M + 31) / 32) * ((K + 31) / 32);
+// embedding of op(S)[b][r][k] (rows r, K index k); tiled when consecutive rows
+// are consecutive in memory and k is not
+static void embed_impl(Dev& D, int prec, bool is_b, const cplx* S, int64_t sb, const Lvl& lr, const Lvl& lk, bool cj,
+                       int64_t batch, int64_t Rn, int64_t K, int64_t pitch, void* out) {
+    if (batch * Rn * K == 0) return;
+    const bool tiled = lr.s == 1 && lk.s != 1;
+    const int64_t rows_e = is_b ? 2 * Rn : Rn;
+    const int64_t nt = batch * ((Rn + 31) / 32) * ((K + 31) / 32);
     const int gt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)D.sm_count * 8));
+    const int g = grid_n(D, batch * Rn * K);
+    const int c = cj ? 1 : 0;
+    const FastDiv fR(Rn), fK(K);
     if (prec == LRCC_MIXED_BF16X3) {
-        if (tiled) k_embed_t<0, false><<<gt, 256, 0, D.st>>>(A, sAb, sAk, cA, batch, M, K, M, pitch, out);
-        else k_embed<0, false><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, FastDiv(M), FastDiv(K), M, pitch, out);
+        if (is_b) {
+            if (tiled) k_embed_t<0, true><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, rows_e, pitch, out);
+            else k_embed<0, true><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, rows_e, pitch, out);
+        } else {
+            if (tiled) k_embed_t<0, false><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, rows_e, pitch, out);
+            else k_embed<0, false><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, rows_e, pitch, out);
+        }
     } else {
-        if (tiled) k_embed_t<1, false><<<gt, 256, 0, D.st>>>(A, sAb, sAk, cA, batch, M, K, M, pitch, out);
-        else k_embed<1, false><<<grid_n(D, batch * M * K), 256, 0, D.st>>>(A, sAb, sAm, sAk, cA, batch, M, K, FastDiv(M), FastDiv(K), M, pitch, out);
+        if (is_b) {
+            if (tiled) k_embed_t<1, true><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, rows_e, pitch, out);
+            else k_embed<1, true><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, rows_e, pitch, out);
+        } else {
+            if (tiled) k_embed_t<1, false><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, rows_e, pitch, out);
+            else k_embed<1, false><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, rows_e, pitch, out);
+        }
     }
     LAUNCH_CHECK(D);
 }
 
+void tc_embed_a(Dev& D, int prec, const cplx* A, int64_t sAb, int64_t sAm, int64_t sAk, bool cA, int64_t batch,
+                int64_t M, int64_t K, int64_t pitch, void* out) {
+    embed_impl(D, prec, false, A, sAb, mk_lvl(sAm), mk_lvl(sAk), cA, batch, M, K, pitch, out);
+}
+
 void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64_t sBn, bool cB, int64_t batch,
                 int64_t K, int64_t N, int64_t pitch, void* out) {
-    if (batch * N * K == 0) return;
-    const bool tiled = sBn == 1 && sBk != 1;
-    const int64_t nt = batch * ((N + 31) / 32) * ((K + 31) / 32);
-    const int gt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)D.sm_count * 8));
-    if (prec == LRCC_MIXED_BF16X3) {
-        if (tiled) k_embed_t<0, true><<<gt, 256, 0, D.st>>>(B, sBb, sBk, cB, batch, N, K, 2 * N, pitch, out);
-        else k_embed<0, true><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBn, sBk, cB, batch, N, K, FastDiv(N), FastDiv(K), 2 * N, pitch, out);
-    } else {
-        if (tiled) k_embed_t<1, true><<<gt, 256, 0, D.st>>>(B, sBb, sBk, cB, batch, N, K, 2 * N, pitch, out);
-        else k_embed<1, true><<<grid_n(D, batch * N * K), 256, 0, D.st>>>(B, sBb, sBn, sBk, cB, batch, N, K, FastDiv(N), FastDiv(K), 2 * N, pitch, out);
-    }
-    LAUNCH_CHECK(D);
+    embed_impl(D, prec, true, B, sBb, mk_lvl(sBn), mk_lvl(sBk), cB, batch, N, K, pitch, out);
 }
 
 // One persistent launch: C = alpha op(A' B'^T) + beta C on embedded operands
@@ -889,7 +936,7 @@ void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64
 // take part (kind 0: bf16, 1: tf32); FP32 accumulation chains of at most
 // kchunk k-blocks, added to C in FP64.
 static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
-                      int64_t kd, int64_t pitch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
+                      int64_t kd, int64_t pitch, cplx* C, int64_t sCb, const Lvl& lm, const Lvl& ln, cplx alpha,
                       cplx beta, bool conj_acc, int kchunk, bool exact_alpha, double useful_flops,
                       const char* name) {
     REQUIRE(D.err_flag != nullptr, "gemm_tc: no error word");
@@ -936,10 +983,11 @@ static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t 
     sc.kchunk = kchunk;
     sc.units = (long long)tiles * splits;
     REQUIRE(batch < INT32_MAX, "gemm_tc: batch too large");
-    Epi ep{M, N, C, sCb, sCm, sCn, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0, exact_alpha ? 1 : 0};
+    Epi ep{M, N, C, sCb, lm, ln, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0, exact_alpha ? 1 : 0};
     if (splits > 1) {
         GemmArgs pg{};
-        pg.M = M; pg.N = N; pg.batch = batch; pg.C = C; pg.sCb = sCb; pg.sCm = sCm; pg.sCn = sCn; pg.beta = beta;
+        pg.M = M; pg.N = N; pg.batch = batch; pg.C = C; pg.sCb = sCb; pg.sCm = lm.s; pg.sCn = ln.s; pg.beta = beta;
+        pg.dCm2 = lm.two ? lm.f2.d : 0; pg.sCm1 = lm.s1; pg.dCn2 = ln.two ? ln.f2.d : 0; pg.sCn1 = ln.s1;
         gemm_prescale(D, pg);
     }
     // host-side fault injection for the failure-detection test: the producer
@@ -970,8 +1018,8 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
                       cplx beta, bool conj_acc, double useful_flops) {
     const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
     REQUIRE(K > 0, "gemm_tc: bad embedded K");
-    tc_launch(D, kind, pa, pb, batch, M, N, slots(kind) * K, pitch, C, sCb, sCm, sCn, alpha, beta, conj_acc, KCHUNK,
-              false, useful_flops, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32");
+    tc_launch(D, kind, pa, pb, batch, M, N, slots(kind) * K, pitch, C, sCb, mk_lvl(sCm), mk_lvl(sCn), alpha, beta,
+              conj_acc, KCHUNK, false, useful_flops, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32");
 }
 
 // relative cost of running C[M][N] in this orientation: padded tensor-core
@@ -987,6 +1035,7 @@ void gemm_tc(Dev& D, const GemmArgs& g0, int prec) {
     if (g0.M <= 0 || g0.N <= 0 || g0.batch <= 0) return;
     REQUIRE(prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3, "gemm_tc: bad precision");
     if (g0.K <= 0) {
+        REQUIRE(g0.flat(), "gemm_tc: K = 0 with two-level groups");
         gemm_f64(D, g0);  // pure beta scaling
         return;
     }
@@ -997,7 +1046,11 @@ void gemm_tc(Dev& D, const GemmArgs& g0, int prec) {
         g.A = g0.B; g.sAb = g0.sBb; g.sAm = g0.sBn; g.sAk = g0.sBk; g.cA = g0.cB;
         g.B = g0.A; g.sBb = g0.sAb; g.sBk = g0.sAk; g.sBn = g0.sAm; g.cB = g0.cA;
         g.sCm = g0.sCn; g.sCn = g0.sCm;
+        g.dAm2 = g0.dBn2; g.sAm1 = g0.sBn1; g.dAk2 = g0.dBk2; g.sAk1 = g0.sBk1;
+        g.dBk2 = g0.dAk2; g.sBk1 = g0.sAk1; g.dBn2 = g0.dAm2; g.sBn1 = g0.sAm1;
+        g.dCm2 = g0.dCn2; g.sCm1 = g0.sCn1; g.dCn2 = g0.dCm2; g.sCn1 = g0.sCm1;
     }
+    REQUIRE(std::max(g.M, g.N) < FAST_INDEX_LIMIT && g.K < FAST_INDEX_LIMIT, "gemm_tc: index groups too large");
     int64_t rowsA, pitch, rowsB, pitch2;
     size_t bytesA = tc_embed_bytes(prec, g.M, g.K, g.batch, rowsA, pitch, false);
     size_t bytesB = tc_embed_bytes(prec, g.N, g.K, g.batch, rowsB, pitch2, true);
@@ -1005,10 +1058,14 @@ void gemm_tc(Dev& D, const GemmArgs& g0, int prec) {
     std::shared_ptr<DevBuf> ha(new DevBuf{&D.pool, pa, bytesA});
     void* pb = D.pool.get(bytesB);
     std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
-    tc_embed_a(D, prec, g.A, g.sAb, g.sAm, g.sAk, g.cA, g.batch, g.M, g.K, pitch, pa);
-    tc_embed_b(D, prec, g.B, g.sBb, g.sBk, g.sBn, g.cB, g.batch, g.K, g.N, pitch, pb);
-    tc_gemm_embedded(D, prec, pa, pb, g.batch, g.M, g.N, g.K, pitch, g.C, g.sCb, g.sCm, g.sCn, g.alpha, g.beta,
-                     false, 8.0 * g.M * g.N * g.K * g.batch);
+    embed_impl(D, prec, false, g.A, g.sAb, mk_lvl(g.sAm, g.dAm2, g.sAm1), mk_lvl(g.sAk, g.dAk2, g.sAk1), g.cA,
+               g.batch, g.M, g.K, pitch, pa);
+    embed_impl(D, prec, true, g.B, g.sBb, mk_lvl(g.sBn, g.dBn2, g.sBn1), mk_lvl(g.sBk, g.dBk2, g.sBk1), g.cB,
+               g.batch, g.N, g.K, pitch, pb);
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    tc_launch(D, kind, pa, pb, g.batch, g.M, g.N, slots(kind) * g.K, pitch, g.C, g.sCb,
+              mk_lvl(g.sCm, g.dCm2, g.sCm1), mk_lvl(g.sCn, g.dCn2, g.sCn1), g.alpha, g.beta, false, KCHUNK, false,
+              8.0 * g.M * g.N * g.K * g.batch, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32");
 }
 
 void tc_embed_antisym_slab(Dev& D, int prec, const cplx* GT, int64_t ldt, int64_t a0, int64_t gb0, int64_t prow0,
@@ -1087,13 +1144,14 @@ void oz_gemm_embedded(Dev& D, const void* pa, const void* pb, int64_t batch, int
     const double useful = 8.0 * M * N * K * batch, pairs = OZ_S * (OZ_S + 1) / 2.0;
     for (int d = 0; d < OZ_S; ++d) {
         const char* pbd = (const char*)pb + (size_t)((OZ_S - 1 - d) * kpad * 2);
-        tc_launch(D, 0, pa, pbd, batch, M, N, (d + 1) * kpad, OZ_S * kpad, C, sCb, sCm, sCn, alpha,
+        tc_launch(D, 0, pa, pbd, batch, M, N, (d + 1) * kpad, OZ_S * kpad, C, sCb, mk_lvl(sCm), mk_lvl(sCn), alpha,
                   d == 0 ? beta : mkc(1.0), conj_acc, OZ_KCHUNK, true, useful * (d + 1) / pairs, "gemm_tc_f64emu");
     }
 }
 
 void gemm_tc_f64(Dev& D, const GemmArgs& g0) {
     if (g0.M <= 0 || g0.N <= 0 || g0.batch <= 0) return;
+    REQUIRE(g0.flat(), "gemm_tc_f64: two-level index groups are not supported");
     if (g0.K <= 0) {
         gemm_f64(D, g0);  // pure beta scaling
         return;

@@ -209,6 +209,13 @@ struct GemmArgs {
     cplx* C;
     int64_t sCb, sCm, sCn;
     cplx alpha, beta;
+    // two-level index groups (tensor-core path only): index g of a group is
+    // split as g = g1 d2 + g2 with offset g1 s1 + g2 s, s being the stride
+    // above; d2 = 0 marks a flat group
+    int64_t dAm2 = 0, sAm1 = 0, dAk2 = 0, sAk1 = 0;
+    int64_t dBk2 = 0, sBk1 = 0, dBn2 = 0, sBn1 = 0;
+    int64_t dCm2 = 0, sCm1 = 0, dCn2 = 0, sCn1 = 0;
+    bool flat() const { return !(dAm2 | dAk2 | dBk2 | dBn2 | dCm2 | dCn2); }
 };
 void gemm_f64(Dev& D, const GemmArgs& g);
 // same GEMM with FP32 arithmetic (FP64 in and out): inner products of the
