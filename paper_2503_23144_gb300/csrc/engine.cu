@@ -174,7 +174,7 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
             Av.s[k] = pa >= 0 ? A0.s[pa] : 0;
             Bv.s[k] = pb >= 0 ? B0.s[pb] : 0;
         }
-        outer_axpby(D, alpha, Av, cA, Bv, cB, beta, C);
+        outer_axpby(D, alpha, Av, cA, Bv, cB, beta, C, prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3);
         return;
     }
     const bool mixed = prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3;
@@ -188,7 +188,7 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
         for (char c : gk) K *= dim_of(c);
         for (char c : gb) Bt *= dim_of(c);
         const double fl = 8.0 * double(M) * double(N) * double(K) * double(Bt);
-        if (fl >= 5e7 && K >= 48 && std::max(M, N) < FAST_INDEX_LIMIT && K < FAST_INDEX_LIMIT) {
+        if (fl >= 5e7 && K >= 4 && std::min(M, N) >= 8 && std::max(M, N) < FAST_INDEX_LIMIT && K < FAST_INDEX_LIMIT) {
             std::vector<char> ob = order_by(gb, C, sp.c), om = order_by(gm, C, sp.c), on = order_by(gn, C, sp.c);
             std::vector<char> okk = order_by(gk, A0, sp.a);
             Two am, cm, bn, cn, ak, bk;

@@ -160,19 +160,6 @@ Lvl mk_lvl(int64_t s, int64_t d2 = 0, int64_t s1 = 0) {
     return L;
 }
 
-// FP32 -> FP64 (exact) from the bit fields with integer operations, keeping
-// conversions off the FP64 pipe; FP32 subnormals (below 1.2e-38) become zero
-__device__ __forceinline__ double f32_to_f64(float f) {
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t ex = (u >> 23) & 0xFFu;
-    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
-    if (ex == 0) return __longlong_as_double((long long)sign);
-    if (ex == 0xFFu)
-        return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | ((u & 0x7FFFFFu) ? (1ull << 51) : 0ull)));
-    return __longlong_as_double(
-        (long long)(sign | ((unsigned long long)(ex - 127 + 1023) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
-}
-
 // FP64 work in the epilogue is kept to the adds into C (GB300 issues two FP64
 // FMAs per SM per clock): alpha scales the FP32 accumulator in FP32 unless
 // the products are exact integer chains (exact_alpha), and beta = 0 / 1 skip
@@ -455,26 +442,6 @@ __device__ __forceinline__ uint32_t bf2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// FP64 -> FP32 by truncating the significand, from the IEEE-754 bit fields with
-// integer operations only (GB300 issues two FP64 instructions per SM per clock,
-// which made FP64-side conversions the bottleneck of these memory-bound
-// kernels).  Magnitudes below the FP32 normal range flush to zero; overflow
-// gives infinity; NaN stays NaN.  The dropped bits are below 2^-23 relative,
-// far under the 2^-17 of the bf16x3 split and the 2^-11 of TF32.
-__device__ __forceinline__ float f64_to_f32_rz(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-    const int ex = (int)((b >> 52) & 0x7FF);
-    if (ex == 0x7FF)
-        return __uint_as_float(sign | 0x7F800000u | ((b & 0xFFFFFFFFFFFFFull) ? 0x400000u : 0u));
-    const int ef = ex - 1023 + 127;
-    if (ef <= 0) return __uint_as_float(sign);
-    if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
-    return __uint_as_float(sign | ((uint32_t)ef << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
-}
-
-// store the embedding of v = op(S)[b][r][k]: A rows (slots S*k..) or the B row
-// pair (2r: real output, 2r+1: imaginary output)
 template <int KIND, bool IS_B>
 __device__ __forceinline__ void embed_store(void* __restrict__ out, int64_t rows_e, int64_t pitch, int64_t b,
                                             int64_t r, int64_t k, float vr, float vi) {

@@ -457,9 +457,23 @@ struct Str3 {
     FastDiv fd[MAXD];
 };
 
-template <bool BETA0>
+// LOWP (mixed-precision products): the product and alpha in FP32 arithmetic
+// (relative error 2^-23, far below the tensor-core products it joins), only
+// the accumulation into C in FP64
+__device__ __forceinline__ float2 f2of(cplx v, int cj) {
+    const float i = f64_to_f32_rz(v.y);
+    return make_float2(f64_to_f32_rz(v.x), cj ? -i : i);
+}
+__device__ __forceinline__ float2 fscale(float2 a, int k, float2 v) {
+    if (k == 0) return v;
+    if (k == 1) return make_float2(-v.x, -v.y);
+    return make_float2(a.x * v.x - a.y * v.y, a.x * v.y + a.y * v.x);
+}
+
+template <bool BETA0, bool LOWP>
 __global__ void k_outer(Str3 s, int64_t n, cplx alpha, int ka, const cplx* __restrict__ a, int ca,
                         const cplx* __restrict__ b, int cb, cplx beta, int kb, cplx* __restrict__ c) {
+    const float2 af = make_float2((float)alpha.x, (float)alpha.y);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         int64_t oa = 0, ob = 0, oc = 0;
@@ -483,10 +497,17 @@ __global__ void k_outer(Str3 s, int64_t n, cplx alpha, int ka, const cplx* __res
                 oc += q * s.sc[k];
             }
         }
-        cplx u = a[oa], v = b[ob];
-        if (ca) u.y = -u.y;
-        if (cb) v.y = -v.y;
-        cplx p = cscale(alpha, ka, cmul(u, v));
+        cplx p;
+        if (LOWP) {
+            const float2 u = f2of(a[oa], ca), v = f2of(b[ob], cb);
+            const float2 q = fscale(af, ka, make_float2(u.x * v.x - u.y * v.y, u.x * v.y + u.y * v.x));
+            p = make_double2(f32_to_f64(q.x), f32_to_f64(q.y));
+        } else {
+            cplx u = a[oa], v = b[ob];
+            if (ca) u.y = -u.y;
+            if (cb) v.y = -v.y;
+            p = cscale(alpha, ka, cmul(u, v));
+        }
         if (!BETA0) {
             cplx w = cscale(beta, kb, c[oc]);
             p.x += w.x;
@@ -497,7 +518,8 @@ __global__ void k_outer(Str3 s, int64_t n, cplx alpha, int ka, const cplx* __res
 }
 
 // A, B given as views over C's dimensions (stride 0 where a label is absent)
-void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, bool cb, cplx beta, Tensor& C) {
+void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, bool cb, cplx beta, Tensor& C,
+                 bool lowp) {
     Str3 s;
     s.nd = 0;
     for (int k = 0; k < C.nd; ++k) {
@@ -530,8 +552,13 @@ void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, 
     bool beta0 = beta.x == 0.0 && beta.y == 0.0;
     int th = 256, g = grid_for(D, n, th);
     const int ka = ckind(alpha), kb = ckind(beta);
-    if (beta0) k_outer<true><<<g, th, 0, D.st>>>(s, n, alpha, ka, A.p, ca, B.p, cb, beta, kb, C.p);
-    else k_outer<false><<<g, th, 0, D.st>>>(s, n, alpha, ka, A.p, ca, B.p, cb, beta, kb, C.p);
+    if (lowp) {
+        if (beta0) k_outer<true, true><<<g, th, 0, D.st>>>(s, n, alpha, ka, A.p, ca, B.p, cb, beta, kb, C.p);
+        else k_outer<false, true><<<g, th, 0, D.st>>>(s, n, alpha, ka, A.p, ca, B.p, cb, beta, kb, C.p);
+    } else {
+        if (beta0) k_outer<true, false><<<g, th, 0, D.st>>>(s, n, alpha, ka, A.p, ca, B.p, cb, beta, kb, C.p);
+        else k_outer<false, false><<<g, th, 0, D.st>>>(s, n, alpha, ka, A.p, ca, B.p, cb, beta, kb, C.p);
+    }
     LAUNCH_CHECK(D);
 }
 
@@ -540,10 +567,11 @@ void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, 
 //   mode 1: x_ijab - x_jiab,  mode 2: x_ijab - x_ijba,  mode 3: both (4 terms)
 // y = alpha * P x + beta * y.  Each P is its own transpose.
 // ---------------------------------------------------------------------------
-template <bool BETA0>
+template <bool BETA0, bool LOWP>
 __global__ void k_asym(int mode, int64_t n, int64_t O, int64_t V, FastDiv fO, FastDiv fV, cplx alpha, int ka,
                        const cplx* __restrict__ x, cplx beta, int kb, cplx* __restrict__ y) {
     const int64_t VV = V * V, OVV = O * VV;
+    const float2 af = make_float2((float)alpha.x, (float)alpha.y);
     const bool fast = n < FAST_INDEX_LIMIT;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -572,23 +600,45 @@ __global__ void k_asym(int mode, int64_t n, int64_t O, int64_t V, FastDiv fO, Fa
             r = t / O;
         }
         const cplx* xr = x + r * O * OVV;
-        cplx v = xr[i * OVV + j * VV + a * V + b];
-        if (mode & 1) {
-            cplx w = xr[j * OVV + i * VV + a * V + b];
-            v.x -= w.x;
-            v.y -= w.y;
+        cplx v;
+        if (LOWP) {
+            float2 f = f2of(xr[i * OVV + j * VV + a * V + b], 0);
+            if (mode & 1) {
+                const float2 w = f2of(xr[j * OVV + i * VV + a * V + b], 0);
+                f.x -= w.x;
+                f.y -= w.y;
+            }
+            if (mode & 2) {
+                const float2 w = f2of(xr[i * OVV + j * VV + b * V + a], 0);
+                f.x -= w.x;
+                f.y -= w.y;
+            }
+            if (mode == 3) {
+                const float2 w = f2of(xr[j * OVV + i * VV + b * V + a], 0);
+                f.x += w.x;
+                f.y += w.y;
+            }
+            f = fscale(af, ka, f);
+            v = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
+        } else {
+            v = xr[i * OVV + j * VV + a * V + b];
+            if (mode & 1) {
+                cplx w = xr[j * OVV + i * VV + a * V + b];
+                v.x -= w.x;
+                v.y -= w.y;
+            }
+            if (mode & 2) {
+                cplx w = xr[i * OVV + j * VV + b * V + a];
+                v.x -= w.x;
+                v.y -= w.y;
+            }
+            if (mode == 3) {
+                cplx w = xr[j * OVV + i * VV + b * V + a];
+                v.x += w.x;
+                v.y += w.y;
+            }
+            v = cscale(alpha, ka, v);
         }
-        if (mode & 2) {
-            cplx w = xr[i * OVV + j * VV + b * V + a];
-            v.x -= w.x;
-            v.y -= w.y;
-        }
-        if (mode == 3) {
-            cplx w = xr[j * OVV + i * VV + b * V + a];
-            v.x += w.x;
-            v.y += w.y;
-        }
-        v = cscale(alpha, ka, v);
         if (!BETA0) {
             cplx w = cscale(beta, kb, y[idx]);
             v.x += w.x;
@@ -598,7 +648,7 @@ __global__ void k_asym(int mode, int64_t n, int64_t O, int64_t V, FastDiv fO, Fa
     }
 }
 
-void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor& y) {
+void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor& y, bool lowp) {
     REQUIRE(mode >= 1 && mode <= 3, "asym: bad mode");
     REQUIRE(x.contiguous() && y.contiguous() && x.numel() == y.numel() && x.nd >= 4 && y.nd >= 4,
             "asym: contiguous [..][O][O][V][V] tensors expected");
@@ -610,7 +660,12 @@ void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor
     int th = 256, g = grid_for(D, n, th);
     FastDiv fO(O), fV(V);
     const int ka = ckind(alpha), kb = ckind(beta);
-    if (beta0) k_asym<true><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
-    else k_asym<false><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
+    if (lowp) {
+        if (beta0) k_asym<true, true><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
+        else k_asym<false, true><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
+    } else {
+        if (beta0) k_asym<true, false><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
+        else k_asym<false, false><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
+    }
     LAUNCH_CHECK(D);
 }

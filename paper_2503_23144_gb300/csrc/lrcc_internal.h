@@ -123,6 +123,39 @@ struct FastDiv {
     }
     __device__ __forceinline__ uint32_t div(uint32_t n) const { return (__umulhi(n, m) + n) >> s; }
 };
+// FP64 -> FP32 by truncating the significand, from the IEEE-754 bit fields with
+// integer operations only (GB300 issues two FP64 instructions per SM per clock,
+// which made FP64-side conversions the bottleneck of these memory-bound
+// kernels).  Magnitudes below the FP32 normal range flush to zero; overflow
+// gives infinity; NaN stays NaN.  The dropped bits are below 2^-23 relative,
+// far under the 2^-17 of the bf16x3 split and the 2^-11 of TF32.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0x7FF)
+        return __uint_as_float(sign | 0x7F800000u | ((b & 0xFFFFFFFFFFFFFull) ? 0x400000u : 0u));
+    const int ef = ex - 1023 + 127;
+    if (ef <= 0) return __uint_as_float(sign);
+    if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((uint32_t)ef << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
+}
+
+// store the embedding of v = op(S)[b][r][k]: A rows (slots S*k..) or the B row
+// pair (2r: real output, 2r+1: imaginary output)
+// FP32 -> FP64 (exact) from the bit fields with integer operations, keeping
+// conversions off the FP64 pipe; FP32 subnormals (below 1.2e-38) become zero
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = (u >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if (ex == 0) return __longlong_as_double((long long)sign);
+    if (ex == 0xFFu)
+        return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull | ((u & 0x7FFFFFu) ? (1ull << 51) : 0ull)));
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(ex - 127 + 1023) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
 // elementwise index spaces below 2^31 decode with FastDiv
 constexpr int64_t FAST_INDEX_LIMIT = int64_t(1) << 31;
 
@@ -186,10 +219,11 @@ void axpby(Dev& D, cplx alpha, const Tensor& x, bool conjx, cplx beta, Tensor& y
 void fill(Dev& D, Tensor& y, cplx v);
 // C = alpha op(A) op(B) + beta C elementwise; A and B are views over C's dims
 // (stride 0 along dims they do not carry)
-void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, bool cb, cplx beta, Tensor& C);
+void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, bool cb, cplx beta, Tensor& C,
+                 bool lowp = false);
 // y = alpha P x + beta y on contiguous [..][O][O][V][V]; P = P(ij) (mode 1),
 // P(ab) (mode 2) or P(ij)P(ab) (mode 3)
-void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor& y);
+void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor& y, bool lowp = false);
 // max |y| over all elements (host result; synchronises the stream)
 double max_abs(Dev& D, const Tensor& y);
 // per-leading-index max |y| into dev out[R] (double), no sync
