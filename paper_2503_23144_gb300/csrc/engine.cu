@@ -178,17 +178,19 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
         return;
     }
     const bool mixed = prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3;
-    if (mixed && gemm_tc_available()) {
-        // tensor-core GEMMs read and write strided groups of up to two pieces
-        // in place (the embedding and the epilogue decode them), so no
-        // transposed copies are made for them
+    {
+        // GEMMs read and write index groups of up to two strided pieces in
+        // place (the tensor-core embedding and epilogue and the SIMT kernels
+        // decode them), so no transposed copies are made for them
         int64_t M = 1, N = 1, K = 1, Bt = 1;
         for (char c : gm) M *= dim_of(c);
         for (char c : gn) N *= dim_of(c);
         for (char c : gk) K *= dim_of(c);
         for (char c : gb) Bt *= dim_of(c);
         const double fl = 8.0 * double(M) * double(N) * double(K) * double(Bt);
-        if (fl >= 5e7 && K >= 4 && std::min(M, N) >= 8 && std::max(M, N) < FAST_INDEX_LIMIT && K < FAST_INDEX_LIMIT) {
+        const bool big = gemm_tc_available() && fl >= 5e7 && K >= 48;
+        const bool emu_tc = prec == LRCC_FP64_EMULATED && big && std::min(M, N) >= 8;  // sliced path: flat only
+        if (!emu_tc && std::max(M, N) < FAST_INDEX_LIMIT && K < FAST_INDEX_LIMIT && Bt <= 65535) {
             std::vector<char> ob = order_by(gb, C, sp.c), om = order_by(gm, C, sp.c), on = order_by(gn, C, sp.c);
             std::vector<char> okk = order_by(gk, A0, sp.a);
             Two am, cm, bn, cn, ak, bk;
@@ -205,7 +207,9 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
                 g.dAm2 = am.d2; g.sAm1 = am.s1; g.dAk2 = ak.d2; g.sAk1 = ak.s1;
                 g.dBk2 = bk.d2; g.sBk1 = bk.s1; g.dBn2 = bn.d2; g.sBn1 = bn.s1;
                 g.dCm2 = cm.d2; g.sCm1 = cm.s1; g.dCn2 = cn.d2; g.sCn1 = cn.s1;
-                gemm_tc(D, g, prec);
+                if (mixed && big) gemm_tc(D, g, prec);
+                else if (mixed) gemm_f32c(D, g);
+                else gemm_f64(D, g);
                 return;
             }
         }

@@ -64,6 +64,7 @@ struct GemmK {
     int64_t kper;  // K range per split
     int atomic;    // 1: accumulate alpha*acc with atomics (C pre-scaled by beta)
     int a_kfast, b_nfast;
+    Lvl am, ak, bk, bn, cm, cn;  // index group offsets (two-level groups of an einsum in place)
 };
 
 template <typename T>
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
             if (g.a_kfast) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
             int64_t m = m0 + mm, k = k0 + kk;
             cplx v = make_double2(0.0, 0.0);
-            if (m < g.M && k < kend) v = A[m * g.sAm + k * g.sAk];
+            if (m < g.M && k < kend) v = A[lvl_off(g.am, m) + lvl_off(g.ak, k)];
             if (g.cA) v.y = -v.y;
             ra[r] = CT<T>::cvt(v);
             int nn;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
             int64_t n = n0 + nn;
             k = k0 + kk;
             cplx w = make_double2(0.0, 0.0);
-            if (n < g.N && k < kend) w = B[k * g.sBk + n * g.sBn];
+            if (n < g.N && k < kend) w = B[lvl_off(g.bk, k) + lvl_off(g.bn, n)];
             if (g.cB) w.y = -w.y;
             rb[r] = CT<T>::cvt(w);
         }
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int64_t m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
-            old[i][j] = (rd && m < g.M && n < g.N) ? C[m * g.sCm + n * g.sCn] : make_double2(0.0, 0.0);
+            old[i][j] = (rd && m < g.M && n < g.N) ? C[lvl_off(g.cm, m) + lvl_off(g.cn, n)] : make_double2(0.0, 0.0);
         }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(TH) k_gemm(GemmK g) {
             int64_t n = n0 + tx + 16 * j;
             if (n >= g.N) continue;
             cplx r = CT<T>::scale(acc[i][j], g.alpha);
-            cplx* c = C + m * g.sCm + n * g.sCn;
+            cplx* c = C + lvl_off(g.cm, m) + lvl_off(g.cn, n);
             if (g.atomic) {
                 atomicAdd(&c->x, r.x);
                 atomicAdd(&c->y, r.y);
@@ -213,14 +214,14 @@ __global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
             int kk = g.b_nfast ? e / NMAX : e % SK_KC;
             int nn = g.b_nfast ? e % NMAX : e / SK_KC;
             cplx w = make_double2(0.0, 0.0);
-            if (kk < kc && nn < N) w = B[(k0 + kk) * g.sBk + nn * g.sBn];
+            if (kk < kc && nn < N) w = B[lvl_off(g.bk, k0 + kk) + lvl_off(g.bn, nn)];
             if (g.cB) w.y = -w.y;
             Bs[kk][nn] = CT<T>::cvt(w);
         }
         __syncthreads();
         if (m < g.M) {
             for (int kk = 0; kk < kc; ++kk) {
-                cplx a0 = A[m * g.sAm + (k0 + kk) * g.sAk];
+                cplx a0 = A[lvl_off(g.am, m) + lvl_off(g.ak, k0 + kk)];
                 if (g.cA) a0.y = -a0.y;
                 cT a = CT<T>::cvt(a0);
 #pragma unroll
@@ -236,12 +237,12 @@ __global__ void __launch_bounds__(SK_TH) k_gemm_skinny(GemmK g) {
     cplx old[NMAX];
 #pragma unroll
     for (int n = 0; n < NMAX; ++n)
-        old[n] = (rd && n < N) ? C[m * g.sCm + n * g.sCn] : make_double2(0.0, 0.0);
+        old[n] = (rd && n < N) ? C[lvl_off(g.cm, m) + lvl_off(g.cn, n)] : make_double2(0.0, 0.0);
 #pragma unroll
     for (int n = 0; n < NMAX; ++n) {
         if (n >= N) break;
         cplx r = CT<T>::scale(acc[n], g.alpha);
-        cplx* c = C + m * g.sCm + n * g.sCn;
+        cplx* c = C + lvl_off(g.cm, m) + lvl_off(g.cn, n);
         if (g.atomic) {
             atomicAdd(&c->x, r.x);
             atomicAdd(&c->y, r.y);
@@ -342,7 +343,8 @@ void gemm_f32c(Dev& D, const GemmArgs& g) { gemm_simt<float>(D, g); }
 
 template <typename T>
 static void gemm_simt(Dev& D, const GemmArgs& g) {
-    REQUIRE(g.flat(), "SIMT GEMM: two-level index groups are for the tensor-core path");
+    REQUIRE(g.flat() || (std::max(g.M, g.N) < FAST_INDEX_LIMIT && g.K < FAST_INDEX_LIMIT),
+            "SIMT GEMM: two-level index groups need groups below 2^31");
     const char* kname = sizeof(T) == 8 ? "gemm_f64" : "gemm_f32";
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
     if (g.K <= 0) {
@@ -350,7 +352,7 @@ static void gemm_simt(Dev& D, const GemmArgs& g) {
         return;
     }
     if (g.batch > 65535) throw LrccError(LRCC_EINVAL, "gemm batch > 65535");
-    if (g.M == 1 && g.N == 1) {
+    if (g.M == 1 && g.N == 1 && g.flat()) {
         prescale(D, g);
         int th = 256;
         int64_t want = (g.K + th * 8 - 1) / (th * 8);
@@ -371,10 +373,16 @@ static void gemm_simt(Dev& D, const GemmArgs& g) {
             k.A = g.A; k.sAb = g.sAb; k.sAm = g.sAm; k.sAk = g.sAk; k.cA = g.cA;
             k.B = g.B; k.sBb = g.sBb; k.sBk = g.sBk; k.sBn = g.sBn; k.cB = g.cB;
             k.C = g.C; k.sCb = g.sCb; k.sCm = g.sCm; k.sCn = g.sCn;
+            k.am = mk_lvl(g.sAm, g.dAm2, g.sAm1); k.ak = mk_lvl(g.sAk, g.dAk2, g.sAk1);
+            k.bk = mk_lvl(g.sBk, g.dBk2, g.sBk1); k.bn = mk_lvl(g.sBn, g.dBn2, g.sBn1);
+            k.cm = mk_lvl(g.sCm, g.dCm2, g.sCm1); k.cn = mk_lvl(g.sCn, g.dCn2, g.sCn1);
         } else {  // C^T = B^T A^T
             k.A = g.B; k.sAb = g.sBb; k.sAm = g.sBn; k.sAk = g.sBk; k.cA = g.cB;
             k.B = g.A; k.sBb = g.sAb; k.sBk = g.sAk; k.sBn = g.sAm; k.cB = g.cA;
             k.C = g.C; k.sCb = g.sCb; k.sCm = g.sCn; k.sCn = g.sCm;
+            k.am = mk_lvl(g.sBn, g.dBn2, g.sBn1); k.ak = mk_lvl(g.sBk, g.dBk2, g.sBk1);
+            k.bk = mk_lvl(g.sAk, g.dAk2, g.sAk1); k.bn = mk_lvl(g.sAm, g.dAm2, g.sAm1);
+            k.cm = mk_lvl(g.sCn, g.dCn2, g.sCn1); k.cn = mk_lvl(g.sCm, g.dCm2, g.sCm1);
         }
         k.alpha = g.alpha;
         k.beta = g.beta;
@@ -418,6 +426,9 @@ static void gemm_simt(Dev& D, const GemmArgs& g) {
     k.A = g.A; k.sAb = g.sAb; k.sAm = g.sAm; k.sAk = g.sAk; k.cA = g.cA;
     k.B = g.B; k.sBb = g.sBb; k.sBk = g.sBk; k.sBn = g.sBn; k.cB = g.cB;
     k.C = g.C; k.sCb = g.sCb; k.sCm = g.sCm; k.sCn = g.sCn;
+    k.am = mk_lvl(g.sAm, g.dAm2, g.sAm1); k.ak = mk_lvl(g.sAk, g.dAk2, g.sAk1);
+    k.bk = mk_lvl(g.sBk, g.dBk2, g.sBk1); k.bn = mk_lvl(g.sBn, g.dBn2, g.sBn1);
+    k.cm = mk_lvl(g.sCm, g.dCm2, g.sCm1); k.cn = mk_lvl(g.sCn, g.dCn2, g.sCn1);
     k.alpha = g.alpha; k.beta = g.beta;
     k.kper = (g.K + splits - 1) / splits;
     k.kper = (k.kper + BK - 1) / BK * BK;

@@ -136,30 +136,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Offset of index g of a GEMM index group: g * s (flat), or with two levels
-// g = g1 d2 + g2 at g1 s1 + g2 s (an einsum group whose labels are not
-// adjacent in memory; d2 < 2^31).
-struct Lvl {
-    int64_t s = 0, s1 = 0;
-    FastDiv f2;
-    int two = 0;
-};
-__device__ __forceinline__ int64_t lvl_off(const Lvl& L, int64_t g) {
-    if (!L.two) return g * L.s;
-    const uint32_t q = L.f2.div((uint32_t)g);
-    return (int64_t)q * L.s1 + (int64_t)((uint32_t)g - q * L.f2.d) * L.s;
-}
-Lvl mk_lvl(int64_t s, int64_t d2 = 0, int64_t s1 = 0) {
-    Lvl L;
-    L.s = s;
-    if (d2 > 0) {
-        L.two = 1;
-        L.s1 = s1;
-        L.f2 = FastDiv(d2);
-    }
-    return L;
-}
-
 // FP64 work in the epilogue is kept to the adds into C (GB300 issues two FP64
 // FMAs per SM per clock): alpha scales the FP32 accumulator in FP32 unless
 // the products are exact integer chains (exact_alpha), and beta = 0 / 1 skip

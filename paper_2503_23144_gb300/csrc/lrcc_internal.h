@@ -159,6 +159,30 @@ __device__ __forceinline__ double f32_to_f64(float f) {
 // elementwise index spaces below 2^31 decode with FastDiv
 constexpr int64_t FAST_INDEX_LIMIT = int64_t(1) << 31;
 
+// Offset of index g of a GEMM index group: g * s (flat), or with two levels
+// g = g1 d2 + g2 at g1 s1 + g2 s (an einsum group whose labels are not
+// adjacent in memory; d2 < 2^31).
+struct Lvl {
+    int64_t s = 0, s1 = 0;
+    FastDiv f2;
+    int two = 0;
+};
+__device__ __forceinline__ int64_t lvl_off(const Lvl& L, int64_t g) {
+    if (!L.two) return g * L.s;
+    const uint32_t q = L.f2.div((uint32_t)g);
+    return (int64_t)q * L.s1 + (int64_t)((uint32_t)g - q * L.f2.d) * L.s;
+}
+inline Lvl mk_lvl(int64_t s, int64_t d2 = 0, int64_t s1 = 0) {
+    Lvl L;
+    L.s = s;
+    if (d2 > 0) {
+        L.two = 1;
+        L.s1 = s1;
+        L.f2 = FastDiv(d2);
+    }
+    return L;
+}
+
 // ---------------------------------------------------------------------------
 // strided complex tensor (row-major by default), up to 8 dimensions
 // ---------------------------------------------------------------------------
