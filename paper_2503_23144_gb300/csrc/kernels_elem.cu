@@ -159,6 +159,8 @@ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return make_double2(a.x + b.x, a.y + b.y); }
+
 // a * v with the kind of the coefficient decided once per launch (0: +1,
 // 1: -1, 2: real, 3: complex): GB300 issues two FP64 FMAs per SM per clock,
 // so these memory-bound kernels spend FP64 work only where a coefficient needs it
@@ -567,88 +569,118 @@ void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, 
 //   mode 1: x_ijab - x_jiab,  mode 2: x_ijab - x_ijba,  mode 3: both (4 terms)
 // y = alpha * P x + beta * y.  Each P is its own transpose.
 // ---------------------------------------------------------------------------
-template <bool BETA0, bool LOWP>
-__global__ void k_asym(int mode, int64_t n, int64_t O, int64_t V, FastDiv fO, FastDiv fV, cplx alpha, int ka,
-                       const cplx* __restrict__ x, cplx beta, int kb, cplx* __restrict__ y) {
+// Tiled antisymmetriser: one block handles the (i<j) pair of planes
+// x[r][i][j], x[r][j][i] and one (a-tile <= b-tile) pair of 32x32 tiles, so
+// every input is read once, coalesced, and the four outputs
+//   out(ij,ab) = x(ij,ab) - x(ji,ab) - x(ij,ba) + x(ji,ba)   (mode 3)
+//   out(ji,ab) = -out(ij,ab), out(ij,ba) = -out(ij,ab), out(ji,ba) = out(ij,ab)
+// are written from the same registers (modes 1 and 2 keep only their terms).
+// Diagonal planes (i = j) and diagonal elements (a = b) come out as the mode
+// defines them (zero where the antisymmetriser vanishes).
+template <bool BETA0>
+__global__ void __launch_bounds__(256) k_asym_t(int mode, int64_t R, int64_t O, int64_t V, cplx alpha, int ka,
+                                                const cplx* __restrict__ x, cplx beta, int kb,
+                                                cplx* __restrict__ y) {
+    // [ij,ab] [ji,ab] [ij,ba] [ji,ba] tiles, as [row a][col b] / [row b][col a] (dynamic: 66 KB)
+    extern __shared__ cplx tsm[];
     const int64_t VV = V * V, OVV = O * VV;
-    const float2 af = make_float2((float)alpha.x, (float)alpha.y);
-    const bool fast = n < FAST_INDEX_LIMIT;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t b, a, j, i, r;
-        if (fast) {
-            uint32_t u = (uint32_t)idx, q = fV.div(u);
-            b = u - q * fV.d;
-            u = q;
-            q = fV.div(u);
-            a = u - q * fV.d;
-            u = q;
-            q = fO.div(u);
-            j = u - q * fO.d;
-            u = q;
-            q = fO.div(u);
-            i = u - q * fO.d;
-            r = q;
-        } else {
-            int64_t t = idx / V;
-            b = idx % V;
-            a = t % V;
-            t /= V;
-            j = t % O;
-            t /= O;
-            i = t % O;
-            r = t / O;
+    const int64_t T = (V + 31) / 32, tpairs = T * (T + 1) / 2, opairs = O * (O + 1) / 2;
+    const int64_t tasks = R * opairs * tpairs;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int64_t task = blockIdx.x; task < tasks; task += gridDim.x) {
+        int64_t rem = task % tpairs, ta = 0;
+        const int64_t u = task / tpairs;
+        while (rem >= T - ta) {
+            rem -= T - ta;
+            ++ta;
         }
-        const cplx* xr = x + r * O * OVV;
-        cplx v;
-        if (LOWP) {
-            float2 f = f2of(xr[i * OVV + j * VV + a * V + b], 0);
-            if (mode & 1) {
-                const float2 w = f2of(xr[j * OVV + i * VV + a * V + b], 0);
-                f.x -= w.x;
-                f.y -= w.y;
-            }
-            if (mode & 2) {
-                const float2 w = f2of(xr[i * OVV + j * VV + b * V + a], 0);
-                f.x -= w.x;
-                f.y -= w.y;
-            }
-            if (mode == 3) {
-                const float2 w = f2of(xr[j * OVV + i * VV + b * V + a], 0);
-                f.x += w.x;
-                f.y += w.y;
-            }
-            f = fscale(af, ka, f);
-            v = make_double2(f32_to_f64(f.x), f32_to_f64(f.y));
-        } else {
-            v = xr[i * OVV + j * VV + a * V + b];
-            if (mode & 1) {
-                cplx w = xr[j * OVV + i * VV + a * V + b];
-                v.x -= w.x;
-                v.y -= w.y;
-            }
-            if (mode & 2) {
-                cplx w = xr[i * OVV + j * VV + b * V + a];
-                v.x -= w.x;
-                v.y -= w.y;
-            }
-            if (mode == 3) {
-                cplx w = xr[j * OVV + i * VV + b * V + a];
-                v.x += w.x;
-                v.y += w.y;
-            }
-            v = cscale(alpha, ka, v);
+        const int64_t tb = ta + rem;
+        int64_t orem = u % opairs, i = 0;
+        const int64_t r = u / opairs;
+        while (orem >= O - i) {
+            orem -= O - i;
+            ++i;
         }
-        if (!BETA0) {
-            cplx w = cscale(beta, kb, y[idx]);
-            v.x += w.x;
-            v.y += w.y;
+        const int64_t j = i + orem;  // i <= j
+        const int64_t a0 = ta * 32, b0 = tb * 32;
+        const cplx* xij = x + r * O * OVV + i * OVV + j * VV;
+        const cplx* xji = x + r * O * OVV + j * OVV + i * VV;
+        // load [ij][a][b] and [ji][a][b] tiles (rows a, cols b) and the
+        // transposed-position tiles [ij][b][a], [ji][b][a] (rows b, cols a)
+        for (int q = ty; q < 32; q += 8) {
+            const int64_t a = a0 + q, b = b0 + tx;
+            const bool in1 = a < V && b < V;
+            tsm[(0 * 32 + q) * 33 + tx] = in1 ? xij[a * V + b] : make_double2(0.0, 0.0);
+            tsm[(1 * 32 + q) * 33 + tx] = in1 ? xji[a * V + b] : make_double2(0.0, 0.0);
+            const int64_t bb = b0 + q, aa = a0 + tx;
+            const bool in2 = bb < V && aa < V;
+            tsm[(2 * 32 + q) * 33 + tx] = in2 ? xij[bb * V + aa] : make_double2(0.0, 0.0);
+            tsm[(3 * 32 + q) * 33 + tx] = in2 ? xji[bb * V + aa] : make_double2(0.0, 0.0);
         }
-        y[idx] = v;
+        __syncthreads();
+        cplx* yij = y + r * O * OVV + i * OVV + j * VV;
+        cplx* yji = y + r * O * OVV + j * OVV + i * VV;
+        // outputs at (a, b) for the (ij) and (ji) planes, rows a, cols b
+        for (int q = ty; q < 32; q += 8) {
+            const int64_t a = a0 + q, b = b0 + tx;
+            if (a < V && b < V && (ta != tb || a <= b)) {
+                const cplx p0 = tsm[(0 * 32 + q) * 33 + tx], p1 = tsm[(1 * 32 + q) * 33 + tx];
+                const cplx p2 = tsm[(2 * 32 + tx) * 33 + q], p3 = tsm[(3 * 32 + tx) * 33 + q];
+                cplx v = p0;
+                if (mode & 1) { v.x -= p1.x; v.y -= p1.y; }
+                if (mode & 2) { v.x -= p2.x; v.y -= p2.y; }
+                if (mode == 3) { v.x += p3.x; v.y += p3.y; }
+                v = cscale(alpha, ka, v);
+                // (ij,ab) and, for i < j, (ji,ab) = -(ij,ab) in modes 1, 3; mode 2 has its own value there
+                cplx w = v;
+                if (!BETA0) w = cadd(w, cscale(beta, kb, yij[a * V + b]));
+                yij[a * V + b] = w;
+                if (i != j) {
+                    cplx vj;
+                    if (mode == 2) {
+                        vj = make_double2(p1.x - p3.x, p1.y - p3.y);
+                        vj = cscale(alpha, ka, vj);
+                    } else {
+                        vj = make_double2(-v.x, -v.y);
+                    }
+                    if (!BETA0) vj = cadd(vj, cscale(beta, kb, yji[a * V + b]));
+                    yji[a * V + b] = vj;
+                }
+            }
+        }
+        // outputs at (b, a) (the transposed positions, a < b strictly), rows b, cols a
+        for (int q = ty; q < 32; q += 8) {
+            const int64_t bb = b0 + q, aa = a0 + tx;
+            if (bb < V && aa < V && (ta != tb || aa < bb)) {
+                // values at (ij,ba) built from the same four inputs
+                const cplx p0 = tsm[(2 * 32 + q) * 33 + tx], p1 = tsm[(3 * 32 + q) * 33 + tx];
+                const cplx p2 = tsm[(0 * 32 + tx) * 33 + q], p3 = tsm[(1 * 32 + tx) * 33 + q];
+                cplx v = p0;
+                if (mode & 1) { v.x -= p1.x; v.y -= p1.y; }
+                if (mode & 2) { v.x -= p2.x; v.y -= p2.y; }
+                if (mode == 3) { v.x += p3.x; v.y += p3.y; }
+                v = cscale(alpha, ka, v);
+                cplx w = v;
+                if (!BETA0) w = cadd(w, cscale(beta, kb, yij[bb * V + aa]));
+                yij[bb * V + aa] = w;
+                if (i != j) {
+                    cplx vj;
+                    if (mode == 2) {
+                        vj = make_double2(p1.x - p3.x, p1.y - p3.y);
+                        vj = cscale(alpha, ka, vj);
+                    } else {
+                        vj = make_double2(-v.x, -v.y);
+                    }
+                    if (!BETA0) vj = cadd(vj, cscale(beta, kb, yji[bb * V + aa]));
+                    yji[bb * V + aa] = vj;
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
-void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor& y, bool lowp) {
+void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor& y) {
     REQUIRE(mode >= 1 && mode <= 3, "asym: bad mode");
     REQUIRE(x.contiguous() && y.contiguous() && x.numel() == y.numel() && x.nd >= 4 && y.nd >= 4,
             "asym: contiguous [..][O][O][V][V] tensors expected");
@@ -656,16 +688,20 @@ void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor
     REQUIRE(x.d[x.nd - 3] == O && x.d[x.nd - 2] == V, "asym: [..][O][O][V][V] expected");
     int64_t n = y.numel();
     if (n == 0) return;
+    REQUIRE(x.p != y.p, "asym: in-place use is not supported");
+    const int64_t R = n / (O * O * V * V);
     bool beta0 = beta.x == 0.0 && beta.y == 0.0;
-    int th = 256, g = grid_for(D, n, th);
-    FastDiv fO(O), fV(V);
     const int ka = ckind(alpha), kb = ckind(beta);
-    if (lowp) {
-        if (beta0) k_asym<true, true><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
-        else k_asym<false, true><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
-    } else {
-        if (beta0) k_asym<true, false><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
-        else k_asym<false, false><<<g, th, 0, D.st>>>(mode, n, O, V, fO, fV, alpha, ka, x.p, beta, kb, y.p);
+    const int64_t T = (V + 31) / 32, tasks = R * (O * (O + 1) / 2) * (T * (T + 1) / 2);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)D.sm_count * 8));
+    const int smem = 4 * 32 * 33 * (int)sizeof(cplx);
+    static bool attr = false;
+    if (!attr) {
+        CK(cudaFuncSetAttribute(k_asym_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        CK(cudaFuncSetAttribute(k_asym_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
     }
+    if (beta0) k_asym_t<true><<<g, 256, smem, D.st>>>(mode, R, O, V, alpha, ka, x.p, beta, kb, y.p);
+    else k_asym_t<false><<<g, 256, smem, D.st>>>(mode, R, O, V, alpha, ka, x.p, beta, kb, y.p);
     LAUNCH_CHECK(D);
 }

@@ -169,7 +169,7 @@ Amp vjp_unique(Dev& D, CCProg& cp, const Amp& Y, double e_scale, int prec) {
         fill(D, ce, mkc(e_scale));
     }
     std::vector<Tensor> g = cp.P.vjp(D, {Y.t1, c2, ce}, {cp.R1, cp.R2, cp.E}, prec);
-    return Amp{g[0], antisym4(D, g[1], is_mixed(prec))};
+    return Amp{g[0], antisym4(D, g[1])};
 }
 
 Amp grad_energy(Dev& D, CCProg& cp, int64_t O, int64_t V, int prec) {
@@ -178,7 +178,7 @@ Amp grad_energy(Dev& D, CCProg& cp, int64_t O, int64_t V, int prec) {
     std::vector<Tensor> g = cp.P.vjp(D, {Tensor(), Tensor(), ce}, {cp.R1, cp.R2, cp.E}, prec);
     (void)O;
     (void)V;
-    return Amp{g[0], antisym4(D, g[1], is_mixed(prec))};
+    return Amp{g[0], antisym4(D, g[1])};
 }
 
 double* dev_doubles(Dev& D, const std::vector<double>& v, std::shared_ptr<DevBuf>& hold) {

@@ -247,7 +247,7 @@ void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, 
                  bool lowp = false);
 // y = alpha P x + beta y on contiguous [..][O][O][V][V]; P = P(ij) (mode 1),
 // P(ab) (mode 2) or P(ij)P(ab) (mode 3)
-void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor& y, bool lowp = false);
+void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor& y);
 // max |y| over all elements (host result; synchronises the stream)
 double max_abs(Dev& D, const Tensor& y);
 // per-leading-index max |y| into dev out[R] (double), no sync

@@ -12,10 +12,6 @@
 
 #include <algorithm>
 
-// mixed-precision sweeps: antisymmetrisers in FP32 arithmetic (their inputs
-// come from tensor-core products with far larger errors)
-static bool lowp(int prec) { return prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3; }
-
 namespace {
 std::string lhs_a(const std::string& s) { return s.substr(0, s.find(',')); }
 std::string lhs_b(const std::string& s) {
@@ -124,7 +120,7 @@ void Prog::apply_term(Dev& D, const Term& t, cplx beta, Tensor& out, int prec) {
         }
     } else if (t.kind == TK_ASYM) {
         REQUIRE(RB == 0 || active[t.a], "asym term on a constant in a batched evaluation");
-        asym_axpby(D, asym_mode(t), c, val[t.a], beta, out, lowp(prec));
+        asym_axpby(D, asym_mode(t), c, val[t.a], beta, out);
     } else {
         int64_t R = (RB > 0 && active[t.a]) ? RB : 1;
         Tensor x = as5(val[t.a], R, O, V);
@@ -197,7 +193,7 @@ std::vector<Tensor> Prog::jvp(Dev& D, const std::vector<Tensor>& tin, const std:
             } else if (t.kind == TK_PERM) {
                 if (active[t.a]) perm_axpby(D, "Z" + perm_in(t.spec) + "->Z" + rhs(t.spec), t.c, tan[t.a], beta(), out);
             } else if (t.kind == TK_ASYM) {
-                if (active[t.a]) asym_axpby(D, asym_mode(t), t.c, tan[t.a], beta(), out, lowp(prec));
+                if (active[t.a]) asym_axpby(D, asym_mode(t), t.c, tan[t.a], beta(), out);
             } else {
                 if (active[t.a]) {
                     Tensor x = as5(tan[t.a], R, O, V), z = as5(out, R, O, V);
@@ -264,7 +260,7 @@ std::vector<Tensor> Prog::vjp(Dev& D, const std::vector<Tensor>& cot, const std:
                     });
             } else if (t.kind == TK_ASYM) {
                 if (active[t.a])
-                    acc(t.a, [&](Tensor& dst, cplx b) { asym_axpby(D, asym_mode(t), t.c, cb, b, dst, lowp(prec)); });
+                    acc(t.a, [&](Tensor& dst, cplx b) { asym_axpby(D, asym_mode(t), t.c, cb, b, dst); });
             } else {
                 if (active[t.a])
                     acc(t.a, [&](Tensor& dst, cplx b) {
@@ -313,7 +309,7 @@ std::vector<Tensor> Prog::jvp_of_vjp(Dev& D, const std::vector<Tensor>& tin, con
             } else if (t.kind == TK_PERM) {
                 if (active[t.a]) perm_axpby(D, "Z" + perm_in(t.spec) + "->Z" + rhs(t.spec), t.c, tan[t.a], beta(), out);
             } else if (t.kind == TK_ASYM) {
-                if (active[t.a]) asym_axpby(D, asym_mode(t), t.c, tan[t.a], beta(), out, lowp(prec));
+                if (active[t.a]) asym_axpby(D, asym_mode(t), t.c, tan[t.a], beta(), out);
             } else if (active[t.a]) {
                 Tensor x = as5(tan[t.a], R, O, V), z = as5(out, R, O, V);
                 ladder(D, *lad, x, t.c, beta(), z, false, prec);
@@ -384,8 +380,8 @@ std::vector<Tensor> Prog::jvp_of_vjp(Dev& D, const std::vector<Tensor>& tin, con
                 }
             } else if (t.kind == TK_ASYM) {
                 if (!active[t.a]) continue;
-                if (cb.p) acc1(t.a, [&](Tensor& dst, cplx b) { asym_axpby(D, asym_mode(t), t.c, cb, b, dst, lowp(prec)); });
-                if (dcb.p) accR(t.a, [&](Tensor& dst, cplx b) { asym_axpby(D, asym_mode(t), t.c, dcb, b, dst, lowp(prec)); });
+                if (cb.p) acc1(t.a, [&](Tensor& dst, cplx b) { asym_axpby(D, asym_mode(t), t.c, cb, b, dst); });
+                if (dcb.p) accR(t.a, [&](Tensor& dst, cplx b) { asym_axpby(D, asym_mode(t), t.c, dcb, b, dst); });
             } else if (t.kind == TK_PERM) {
                 if (!active[t.a]) continue;
                 std::string lx = perm_in(t.spec), ly = rhs(t.spec);

@@ -268,9 +268,9 @@ Amp amp_copy(Dev& D, const Amp& x) {
 }
 
 // y = x - P_ij x - P_ab x + P_ij P_ab x on [R][O][O][V][V]
-Tensor antisym4(Dev& D, const Tensor& x, bool lowp) {
+Tensor antisym4(Dev& D, const Tensor& x) {
     Tensor y = empty(D, x.shape());
-    asym_axpby(D, 3, mkc(1.0), x, mkc(0.0), y, lowp);
+    asym_axpby(D, 3, mkc(1.0), x, mkc(0.0), y);
     return y;
 }
 

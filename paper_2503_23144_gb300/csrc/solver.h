@@ -25,8 +25,7 @@ Tensor amp_gram(Dev& D, const Amp& U, const Amp& W);
 // rows [r0, r0+n) of a batched amplitude set (a view)
 Amp amp_rows(const Amp& a, int64_t r0, int64_t n);
 // 4-fold antisymmetriser over the (i,j) and (a,b) pairs
-// (lowp: FP32 arithmetic, for mixed-precision products)
-Tensor antisym4(Dev& D, const Tensor& x, bool lowp = false);
+Tensor antisym4(Dev& D, const Tensor& x);
 void max_abs_amp(Dev& D, const Amp& r, std::vector<double>& out);
 
 // Pulay DIIS over R independent right-hand sides; Gram matrices, the small
