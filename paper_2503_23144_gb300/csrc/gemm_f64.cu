@@ -40,13 +40,13 @@ template <> struct CT<double> {
 template <> struct CT<float> {
     typedef float2 C;
     __device__ static C cvt(cplx v) { return make_float2((float)v.x, (float)v.y); }
-    __device__ static cplx back(C v) { return make_double2((double)v.x, (double)v.y); }
+    __device__ static cplx back(C v) { return make_double2(f32_to_f64(v.x), f32_to_f64(v.y)); }
     __device__ static C zero() { return make_float2(0.f, 0.f); }
     // alpha applied in FP32: the FP64 pipe (2 FMA per SM per clock on GB300)
     // is left to the adds into C
     __device__ static cplx scale(C v, cplx a) {
         const float ax = (float)a.x, ay = (float)a.y;
-        return make_double2((double)(ax * v.x - ay * v.y), (double)(ax * v.y + ay * v.x));
+        return make_double2(f32_to_f64(ax * v.x - ay * v.y), f32_to_f64(ax * v.y + ay * v.x));
     }
 };
 

@@ -569,8 +569,10 @@ void outer_axpby(Dev& D, cplx alpha, const Tensor& A, bool ca, const Tensor& B, 
 //   mode 1: x_ijab - x_jiab,  mode 2: x_ijab - x_ijba,  mode 3: both (4 terms)
 // y = alpha * P x + beta * y.  Each P is its own transpose.
 // ---------------------------------------------------------------------------
+constexpr int AT = 16;  // antisymmetriser tile edge
+
 // Tiled antisymmetriser: one block handles the (i<j) pair of planes
-// x[r][i][j], x[r][j][i] and one (a-tile <= b-tile) pair of 32x32 tiles, so
+// x[r][i][j], x[r][j][i] and one (a-tile <= b-tile) pair of 16x16 tiles, so
 // every input is read once, coalesced, and the four outputs
 //   out(ij,ab) = x(ij,ab) - x(ji,ab) - x(ij,ba) + x(ji,ba)   (mode 3)
 //   out(ji,ab) = -out(ij,ab), out(ij,ba) = -out(ij,ab), out(ji,ba) = out(ij,ab)
@@ -581,12 +583,12 @@ template <bool BETA0>
 __global__ void __launch_bounds__(256) k_asym_t(int mode, int64_t R, int64_t O, int64_t V, cplx alpha, int ka,
                                                 const cplx* __restrict__ x, cplx beta, int kb,
                                                 cplx* __restrict__ y) {
-    // [ij,ab] [ji,ab] [ij,ba] [ji,ba] tiles, as [row a][col b] / [row b][col a] (dynamic: 66 KB)
-    extern __shared__ cplx tsm[];
+    // [ij,ab] [ji,ab] [ij,ba] [ji,ba] tiles, as [row a][col b] / [row b][col a]
+    __shared__ cplx tsm[4 * AT * (AT + 1)];
     const int64_t VV = V * V, OVV = O * VV;
-    const int64_t T = (V + 31) / 32, tpairs = T * (T + 1) / 2, opairs = O * (O + 1) / 2;
+    const int64_t T = (V + AT - 1) / AT, tpairs = T * (T + 1) / 2, opairs = O * (O + 1) / 2;
     const int64_t tasks = R * opairs * tpairs;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int tx = threadIdx.x % AT, ty = threadIdx.x / AT;
     for (int64_t task = blockIdx.x; task < tasks; task += gridDim.x) {
         int64_t rem = task % tpairs, ta = 0;
         const int64_t u = task / tpairs;
@@ -602,30 +604,30 @@ __global__ void __launch_bounds__(256) k_asym_t(int mode, int64_t R, int64_t O, 
             ++i;
         }
         const int64_t j = i + orem;  // i <= j
-        const int64_t a0 = ta * 32, b0 = tb * 32;
+        const int64_t a0 = ta * AT, b0 = tb * AT;
         const cplx* xij = x + r * O * OVV + i * OVV + j * VV;
         const cplx* xji = x + r * O * OVV + j * OVV + i * VV;
         // load [ij][a][b] and [ji][a][b] tiles (rows a, cols b) and the
         // transposed-position tiles [ij][b][a], [ji][b][a] (rows b, cols a)
-        for (int q = ty; q < 32; q += 8) {
+        for (int q = ty; q < AT; q += 256 / AT) {
             const int64_t a = a0 + q, b = b0 + tx;
             const bool in1 = a < V && b < V;
-            tsm[(0 * 32 + q) * 33 + tx] = in1 ? xij[a * V + b] : make_double2(0.0, 0.0);
-            tsm[(1 * 32 + q) * 33 + tx] = in1 ? xji[a * V + b] : make_double2(0.0, 0.0);
+            tsm[(0 * AT + q) * (AT + 1) + tx] = in1 ? xij[a * V + b] : make_double2(0.0, 0.0);
+            tsm[(1 * AT + q) * (AT + 1) + tx] = in1 ? xji[a * V + b] : make_double2(0.0, 0.0);
             const int64_t bb = b0 + q, aa = a0 + tx;
             const bool in2 = bb < V && aa < V;
-            tsm[(2 * 32 + q) * 33 + tx] = in2 ? xij[bb * V + aa] : make_double2(0.0, 0.0);
-            tsm[(3 * 32 + q) * 33 + tx] = in2 ? xji[bb * V + aa] : make_double2(0.0, 0.0);
+            tsm[(2 * AT + q) * (AT + 1) + tx] = in2 ? xij[bb * V + aa] : make_double2(0.0, 0.0);
+            tsm[(3 * AT + q) * (AT + 1) + tx] = in2 ? xji[bb * V + aa] : make_double2(0.0, 0.0);
         }
         __syncthreads();
         cplx* yij = y + r * O * OVV + i * OVV + j * VV;
         cplx* yji = y + r * O * OVV + j * OVV + i * VV;
         // outputs at (a, b) for the (ij) and (ji) planes, rows a, cols b
-        for (int q = ty; q < 32; q += 8) {
+        for (int q = ty; q < AT; q += 256 / AT) {
             const int64_t a = a0 + q, b = b0 + tx;
             if (a < V && b < V && (ta != tb || a <= b)) {
-                const cplx p0 = tsm[(0 * 32 + q) * 33 + tx], p1 = tsm[(1 * 32 + q) * 33 + tx];
-                const cplx p2 = tsm[(2 * 32 + tx) * 33 + q], p3 = tsm[(3 * 32 + tx) * 33 + q];
+                const cplx p0 = tsm[(0 * AT + q) * (AT + 1) + tx], p1 = tsm[(1 * AT + q) * (AT + 1) + tx];
+                const cplx p2 = tsm[(2 * AT + tx) * (AT + 1) + q], p3 = tsm[(3 * AT + tx) * (AT + 1) + q];
                 cplx v = p0;
                 if (mode & 1) { v.x -= p1.x; v.y -= p1.y; }
                 if (mode & 2) { v.x -= p2.x; v.y -= p2.y; }
@@ -649,12 +651,12 @@ __global__ void __launch_bounds__(256) k_asym_t(int mode, int64_t R, int64_t O, 
             }
         }
         // outputs at (b, a) (the transposed positions, a < b strictly), rows b, cols a
-        for (int q = ty; q < 32; q += 8) {
+        for (int q = ty; q < AT; q += 256 / AT) {
             const int64_t bb = b0 + q, aa = a0 + tx;
             if (bb < V && aa < V && (ta != tb || aa < bb)) {
                 // values at (ij,ba) built from the same four inputs
-                const cplx p0 = tsm[(2 * 32 + q) * 33 + tx], p1 = tsm[(3 * 32 + q) * 33 + tx];
-                const cplx p2 = tsm[(0 * 32 + tx) * 33 + q], p3 = tsm[(1 * 32 + tx) * 33 + q];
+                const cplx p0 = tsm[(2 * AT + q) * (AT + 1) + tx], p1 = tsm[(3 * AT + q) * (AT + 1) + tx];
+                const cplx p2 = tsm[(0 * AT + tx) * (AT + 1) + q], p3 = tsm[(1 * AT + tx) * (AT + 1) + q];
                 cplx v = p0;
                 if (mode & 1) { v.x -= p1.x; v.y -= p1.y; }
                 if (mode & 2) { v.x -= p2.x; v.y -= p2.y; }
@@ -692,16 +694,9 @@ void asym_axpby(Dev& D, int mode, cplx alpha, const Tensor& x, cplx beta, Tensor
     const int64_t R = n / (O * O * V * V);
     bool beta0 = beta.x == 0.0 && beta.y == 0.0;
     const int ka = ckind(alpha), kb = ckind(beta);
-    const int64_t T = (V + 31) / 32, tasks = R * (O * (O + 1) / 2) * (T * (T + 1) / 2);
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)D.sm_count * 8));
-    const int smem = 4 * 32 * 33 * (int)sizeof(cplx);
-    static bool attr = false;
-    if (!attr) {
-        CK(cudaFuncSetAttribute(k_asym_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        CK(cudaFuncSetAttribute(k_asym_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr = true;
-    }
-    if (beta0) k_asym_t<true><<<g, 256, smem, D.st>>>(mode, R, O, V, alpha, ka, x.p, beta, kb, y.p);
-    else k_asym_t<false><<<g, 256, smem, D.st>>>(mode, R, O, V, alpha, ka, x.p, beta, kb, y.p);
+    const int64_t T = (V + AT - 1) / AT, tasks = R * (O * (O + 1) / 2) * (T * (T + 1) / 2);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(tasks, (int64_t)D.sm_count * 16));
+    if (beta0) k_asym_t<true><<<g, 256, 0, D.st>>>(mode, R, O, V, alpha, ka, x.p, beta, kb, y.p);
+    else k_asym_t<false><<<g, 256, 0, D.st>>>(mode, R, O, V, alpha, ka, x.p, beta, kb, y.p);
     LAUNCH_CHECK(D);
 }
