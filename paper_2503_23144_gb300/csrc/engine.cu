@@ -5,6 +5,8 @@
 #include "lrcc_internal.h"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 namespace {
@@ -213,6 +215,12 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
                 return;
             }
         }
+    }
+    static const bool verbose = getenv("LRCC_VERBOSE") != nullptr;
+    if (verbose) {
+        fprintf(stderr, "ein with copies: %s  [", spec.c_str());
+        for (int k = 0; k < A0.nd; ++k) fprintf(stderr, "%lld%s", (long long)A0.d[k], k + 1 < A0.nd ? "," : "] [");
+        for (int k = 0; k < B0.nd; ++k) fprintf(stderr, "%lld%s", (long long)B0.d[k], k + 1 < B0.nd ? "," : "]\n");
     }
     Tensor A = A0, B = B0;
     std::string la = sp.a, lb = sp.b;

@@ -36,9 +36,7 @@ namespace {
 constexpr int BM = 128;
 constexpr int ROWB = 128;                 // bytes of K per row per stage
 constexpr int A_STAGE = BM * ROWB;        // 16 KB
-// epilogue staging: per epilogue warp 32 rows x 16 FP32 pairs (pitch 17)
-constexpr int STG_BYTES = 4 * 32 * 17 * 8;
-constexpr int smem_bytes(int bn, int stages) { return stages * (A_STAGE + bn * ROWB) + STG_BYTES + 1024 + 256; }
+constexpr int smem_bytes(int bn, int stages) { return stages * (A_STAGE + bn * ROWB) + 1024 + 256; }
 constexpr uint32_t WAIT_LIMIT = 1u << 25;  // polls (with backoff) before giving up
 // k-blocks (of 128 bytes of K per row, 4 MMAs each) summed in one FP32 TMEM
 // accumulator; longer K ranges are added chunk by chunk into C in FP64, so
@@ -231,8 +229,7 @@ __global__ void __launch_bounds__(192, 1)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
     uint8_t* sB = smem + STAGES * A_STAGE;
-    float2* stg = (float2*)(sB + STAGES * B_STAGE);
-    uint64_t* full = (uint64_t*)((uint8_t*)stg + STG_BYTES);
+    uint64_t* full = (uint64_t*)(sB + STAGES * B_STAGE);
     uint64_t* empty = full + STAGES;
     uint64_t* accf = empty + STAGES;  // [2] accumulator complete
     uint64_t* acce = accf + 2;        // [2] accumulator drained
@@ -344,7 +341,6 @@ __global__ void __launch_bounds__(192, 1)
         const bool beta1 = ep.beta.x == 1.0 && ep.beta.y == 0.0;
         const bool alpha1 = ep.alpha.x == 1.0 && ep.alpha.y == 0.0;
         const float afx = (float)ep.alpha.x, afy = (float)ep.alpha.y;
-        const bool staged = ep.ln.s == 1 && !ep.ln.two && ep.lm.s != 1;
         int ti = 0;
         bool ok = true;
         for (long long u = blockIdx.x; ok && u < sc.units; u += gridDim.x) {
@@ -363,54 +359,11 @@ __global__ void __launch_bounds__(192, 1)
                 tc_fence_after();
                 const int64_t m = (int64_t)tm * BM + q * 32 + lane;
                 const bool live = m < ep.M;
-                cplx* Cb0 = ep.C + (int64_t)bz * ep.sCb;
-                cplx* Cb = Cb0 + (live ? lvl_off(ep.lm, m) : 0);
+                cplx* Cb = ep.C + (int64_t)bz * ep.sCb + (live ? lvl_off(ep.lm, m) : 0);
 #pragma unroll 1
                 for (int c = 0; c < BN / 32; ++c) {
                     uint32_t r[32];
                     const int64_t n0 = (int64_t)tn * (BN / 2) + c * 16;
-                    if (staged) {
-                        // C contiguous along n only: the warp's 32 rows x 16 columns go
-                        // through shared memory and are written two rows (2 x 256 B)
-                        // per instruction
-                        float2* ws = stg + q * (32 * 17);
-                        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32), r);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const float fi = __uint_as_float(r[2 * j + 1]);
-                            ws[lane * 17 + j] = make_float2(__uint_as_float(r[2 * j]), ep.conj_acc ? -fi : fi);
-                        }
-                        __syncwarp();
-                        const int col = lane & 15;
-                        const int64_t n = n0 + col;
-                        cplx old[16];
-#pragma unroll
-                        for (int it = 0; it < 16; ++it) {
-                            const int row = 2 * it + (lane >> 4);
-                            const int64_t mr = (int64_t)tm * BM + q * 32 + row;
-                            old[it] = (rd && mr < ep.M && n < ep.N) ? Cb0[lvl_off(ep.lm, mr) + n]
-                                                                   : make_double2(0.0, 0.0);
-                        }
-#pragma unroll
-                        for (int it = 0; it < 16; ++it) {
-                            const int row = 2 * it + (lane >> 4);
-                            const int64_t mr = (int64_t)tm * BM + q * 32 + row;
-                            if (mr < ep.M && n < ep.N) {
-                                const float2 f = ws[row * 17 + col];
-                                cplx v = out_value(ep, alpha1, afx, afy, f.x, f.y);
-                                cplx* cp = Cb0 + lvl_off(ep.lm, mr) + n;
-                                if (ep.atomic) {
-                                    atomicAdd(&cp->x, v.x);
-                                    atomicAdd(&cp->y, v.y);
-                                    continue;
-                                }
-                                add_old(v, old[it], add1, beta0, ep.beta);
-                                *cp = v;
-                            }
-                        }
-                        __syncwarp();
-                        continue;
-                    }
                     // old C values are loaded before the TMEM read, all in flight together
                     cplx old[16];
 #pragma unroll
@@ -1019,13 +972,12 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
 }
 
 // relative cost of running C[M][N] in this orientation: padded tensor-core
-// work, with a penalty when the epilogue cannot write whole segments (C
-// contiguous neither along m, where lanes run, nor along n, staged through
-// shared memory)
-static double orient_cost(int64_t M, int64_t N, int64_t sCm, int64_t sCn) {
+// work, with a penalty when the epilogue's lanes (consecutive m) do not write
+// consecutive addresses
+static double orient_cost(int64_t M, int64_t N, int64_t sCm) {
     const int bn = bn_for(2 * N);
     const double pm = double((M + BM - 1) / BM * BM), pn = double((2 * N + bn - 1) / bn * bn);
-    return pm * pn * ((sCm == 1 || sCn == 1) ? 1.0 : 1.15);
+    return pm * pn * (sCm == 1 ? 1.0 : 1.15);
 }
 
 void gemm_tc(Dev& D, const GemmArgs& g0, int prec) {
@@ -1038,7 +990,7 @@ void gemm_tc(Dev& D, const GemmArgs& g0, int prec) {
     }
     // C^T = B^T A^T: run the orientation with less padding / coalesced stores
     GemmArgs g = g0;
-    if (orient_cost(g0.N, g0.M, g0.sCn, g0.dCm2 ? 0 : g0.sCm) < orient_cost(g0.M, g0.N, g0.sCm, g0.dCn2 ? 0 : g0.sCn)) {
+    if (orient_cost(g0.N, g0.M, g0.sCn) < orient_cost(g0.M, g0.N, g0.sCm)) {
         g.M = g0.N; g.N = g0.M;
         g.A = g0.B; g.sAb = g0.sBb; g.sAm = g0.sBn; g.sAk = g0.sBk; g.cA = g0.cB;
         g.B = g0.A; g.sBb = g0.sAb; g.sBk = g0.sAk; g.sBn = g0.sAm; g.cB = g0.cA;
@@ -1154,7 +1106,7 @@ void gemm_tc_f64(Dev& D, const GemmArgs& g0) {
         return;
     }
     GemmArgs g = g0;
-    if (orient_cost(g0.N, g0.M, g0.sCn, g0.dCm2 ? 0 : g0.sCm) < orient_cost(g0.M, g0.N, g0.sCm, g0.dCn2 ? 0 : g0.sCn)) {
+    if (orient_cost(g0.N, g0.M, g0.sCn) < orient_cost(g0.M, g0.N, g0.sCm)) {
         g.M = g0.N; g.N = g0.M;
         g.A = g0.B; g.sAb = g0.sBb; g.sAm = g0.sBn; g.sAk = g0.sBk; g.cA = g0.cB;
         g.B = g0.A; g.sBb = g0.sAb; g.sBk = g0.sAk; g.sBn = g0.sAm; g.cB = g0.cA;

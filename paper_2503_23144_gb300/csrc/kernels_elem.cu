@@ -2,6 +2,8 @@
 #include "lrcc_internal.h"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 
 // ---------------------------------------------------------------------------
 // pool
@@ -320,6 +322,12 @@ __global__ void k_transpose(TStr t, cplx alpha, int ka, const cplx* __restrict__
 }
 
 static bool try_transpose(Dev& D, cplx alpha, const ShapeStrides& ss, const cplx* x, bool conjx, cplx beta, cplx* y) {
+    static const bool verbose = getenv("LRCC_VERBOSE") != nullptr;
+    if (verbose) {
+        fprintf(stderr, "transpose-axpby:");
+        for (int k = 0; k < ss.nd; ++k) fprintf(stderr, " %lld(x%lld,y%lld)", (long long)ss.d[k], (long long)ss.sx[k], (long long)ss.sy[k]);
+        fprintf(stderr, "\n");
+    }
     int kx = -1, ky = -1;
     for (int k = 0; k < ss.nd; ++k) {
         if (ss.sx[k] == 1) kx = k;
