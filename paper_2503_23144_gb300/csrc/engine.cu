@@ -613,9 +613,10 @@ static void ensure_bcache(Dev& D, LadderCtx& LC, int prec) {
     size_t bytes = tc_embed_bytes(prec, V * V, L, 1, rows_e, pitch, true);
     void* p = D.pool.get(bytes);
     LC.bcache.reset(new DevBuf{&D.pool, p, bytes});
-    tc_embed_b(D, prec, LC.Bvv.p, 0, V * V, 1, false, 1, L, V * V, pitch, p);
+    tc_embed_b(D, prec, LC.Bvv.p, 0, V * V, 1, false, 1, L, V * V, pitch, rows_e, p);
     LC.bcache_prec = prec;
     LC.b_pitch = pitch;
+    LC.b_rows = rows_e;
 }
 
 // Assemble the rows of slab sl: FP64 into W [nrows][PV] (prec == FP64; conj:
@@ -636,7 +637,7 @@ struct SlabScratch {
 };
 
 static void assemble_slab(Dev& D, LadderCtx& LC, const Slab& sl, int prec, bool conj, cplx* W, void* Wemb,
-                          int64_t pitch_w, SlabScratch& sc) {
+                          int64_t pitch_w, int64_t rows_w, SlabScratch& sc) {
     const int64_t L = LC.Bvv.d[0], V = LC.Bvv.d[1];
     const int64_t M = (sl.a1 - sl.a0) * V, N = (sl.b1 - sl.gb0) * V;
     REQUIRE(sc.gt && M * N <= sc.gt_el, "ladder: slab product buffer too small");
@@ -660,7 +661,7 @@ static void assemble_slab(Dev& D, LadderCtx& LC, const Slab& sl, int prec, bool 
         size_t bytes = tc_embed_bytes(prec, M, L, 1, rows_e, pitch, false);
         void* p = D.pool.get(bytes);
         sc.aemb.reset(new DevBuf{&D.pool, p, bytes});
-        tc_embed_a(D, prec, LC.Bvv.p + sl.a0 * V, 0, 1, V * V, false, 1, M, L, pitch, p);
+        tc_embed_a(D, prec, LC.Bvv.p + sl.a0 * V, 0, 1, V * V, false, 1, M, L, pitch, M, p);
         sc.a0 = sl.a0;
         sc.a1 = sl.a1;
         sc.a_pitch = pitch;
@@ -668,9 +669,10 @@ static void assemble_slab(Dev& D, LadderCtx& LC, const Slab& sl, int prec, bool 
     REQUIRE(sc.a_pitch == LC.b_pitch, "ladder: embedded K pitch mismatch");
     const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
     const char* pb = (const char*)LC.bcache->p + (size_t)(2 * sl.gb0 * V) * (size_t)(LC.b_pitch * es);
-    tc_gemm_embedded(D, prec, sc.aemb->p, pb, 1, M, N, L, LC.b_pitch, GT.p, 0, 1, M, mkc(1.0), mkc(0.0), false,
+    tc_gemm_embedded(D, prec, sc.aemb->p, pb, 1, M, N, L, LC.b_pitch, M, LC.b_rows, GT.p, 0, 1, M, mkc(1.0),
+                     mkc(0.0), false,
                      8.0 * M * N * L);
-    tc_embed_antisym_slab(D, prec, GT.p, M, sl.a0, sl.gb0, sl.prow0, sl.nrows, V, pitch_w, Wemb);
+    tc_embed_antisym_slab(D, prec, GT.p, M, sl.a0, sl.gb0, sl.prow0, sl.nrows, V, pitch_w, rows_w, Wemb);
 }
 
 // Build the embedded <ab||ef> matrix W' (rows a<b, K over e<f) once for a
@@ -690,12 +692,13 @@ static bool ensure_wcache(Dev& D, LadderCtx& LC, int64_t V, int prec) {
     LC.wcache.reset();
     void* p = D.pool.get(bytes);
     LC.wcache.reset(new DevBuf{&D.pool, p, bytes});
+    tc_zero_tail(D, prec, p, PV, PV, PV);
     const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
     ensure_bcache(D, LC, prec);  // before sizing the slabs on the memory left
     const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), 0);
     SlabScratch sc(D, plan, V);
     for (const Slab& sl : plan)
-        assemble_slab(D, LC, sl, prec, false, nullptr, (char*)p + (size_t)(sl.prow0 * pitch * es), pitch, sc);
+        assemble_slab(D, LC, sl, prec, false, nullptr, (char*)p + (size_t)(sl.prow0 * pitch * es), pitch, PV, sc);
     LC.bcache.reset();  // the cache replaces per-call assembly
     LC.bcache_prec = -1;
     LC.wcache_prec = prec;
@@ -720,7 +723,7 @@ static bool ensure_w64(Dev& D, LadderCtx& LC, int64_t V, int builder) {
     Tensor W = empty(D, {PV, PV});
     const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), 0);
     SlabScratch sc(D, plan, V);
-    for (const Slab& sl : plan) assemble_slab(D, LC, sl, builder, false, W.p + sl.prow0 * PV, nullptr, 0, sc);
+    for (const Slab& sl : plan) assemble_slab(D, LC, sl, builder, false, W.p + sl.prow0 * PV, nullptr, 0, 0, sc);
     LC.w64 = W;
     LC.w64_prec = builder;
     return true;
@@ -782,7 +785,8 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
         Tensor W = empty(D, {wrows, PV});
         for (const SlabGroup& gr : groups) {
             for (size_t c = gr.c0; c < gr.c1; ++c)
-                assemble_slab(D, LC, plan[c], prec, transpose, W.p + (plan[c].prow0 - gr.prow0) * PV, nullptr, 0, sc);
+                assemble_slab(D, LC, plan[c], prec, transpose, W.p + (plan[c].prow0 - gr.prow0) * PV, nullptr, 0, 0,
+                              sc);
             g2.M = gr.nrows; g2.K = PV;
             g2.A = W.p; g2.sAb = 0; g2.sAm = PV; g2.sAk = 1; g2.cA = false;
             g2.C = Zt + gr.prow0;
@@ -795,11 +799,11 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
     size_t bytesB = tc_embed_bytes(prec, ncol, PV, 1, rows_e, pitch, true);
     void* pb = D.pool.get(bytesB);
     std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
-    tc_embed_b(D, prec, Xt, 0, 1, PV, transpose, 1, PV, ncol, pitch, pb);
+    tc_embed_b(D, prec, Xt, 0, 1, PV, transpose, 1, PV, ncol, pitch, rows_e, pb);
     if (ensure_wcache(D, LC, V, prec)) {
         REQUIRE(pitch == LC.w_pitch, "ladder cache: K pitch mismatch");
-        tc_gemm_embedded(D, prec, LC.wcache->p, pb, 1, PV, ncol, PV, pitch, Zt, 0, 1, PV, mkc(1.0), mkc(0.0),
-                         transpose, 8.0 * PV * PV * ncol);
+        tc_gemm_embedded(D, prec, LC.wcache->p, pb, 1, PV, ncol, PV, pitch, PV, rows_e, Zt, 0, 1, PV, mkc(1.0),
+                         mkc(0.0), transpose, 8.0 * PV * PV * ncol);
         return;
     }
     const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
@@ -811,15 +815,18 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
     SlabScratch sc(D, plan, V);
     int64_t wrows = 0;
     for (const SlabGroup& gr : groups) wrows = std::max(wrows, gr.nrows);
-    const size_t wb = (size_t)(wrows * pitch * es);
+    int64_t wr_e, wpitch;
+    const size_t wb = tc_embed_bytes(prec, wrows, PV, 1, wr_e, wpitch, false);
+    REQUIRE(wpitch == pitch, "ladder: W' and X' pitch mismatch");
     void* pw = D.pool.get(wb);
     std::shared_ptr<DevBuf> hw(new DevBuf{&D.pool, pw, wb});
+    tc_zero_tail(D, prec, pw, wrows, PV, wrows);
     for (const SlabGroup& gr : groups) {
         for (size_t c = gr.c0; c < gr.c1; ++c)
             assemble_slab(D, LC, plan[c], prec, false, nullptr,
-                          (char*)pw + (size_t)((plan[c].prow0 - gr.prow0) * pitch * es), pitch, sc);
-        tc_gemm_embedded(D, prec, pw, pb, 1, gr.nrows, ncol, PV, pitch, Zt + gr.prow0, 0, 1, PV, mkc(1.0),
-                         mkc(0.0), transpose, 8.0 * gr.nrows * PV * ncol);
+                          (char*)pw + (size_t)((plan[c].prow0 - gr.prow0) * pitch * es), pitch, wrows, sc);
+        tc_gemm_embedded(D, prec, pw, pb, 1, gr.nrows, ncol, PV, pitch, wrows, rows_e, Zt + gr.prow0, 0, 1, PV,
+                         mkc(1.0), mkc(0.0), transpose, 8.0 * gr.nrows * PV * ncol);
     }
 }
 

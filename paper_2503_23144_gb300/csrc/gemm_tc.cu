@@ -179,6 +179,7 @@ __device__ __forceinline__ void add_old(cplx& v, const cplx& old, bool add1, boo
 struct Sched {
     int tiles_m, tiles_n, batch, splits, kps, num_kb, group;
     int kchunk;  // k-blocks accumulated in FP32 before the epilogue adds them to C in FP64
+    int kpb;     // k-blocks per K panel of the operands (0: rows stored whole)
     long long units;
 };
 
@@ -280,8 +281,10 @@ __global__ void __launch_bounds__(192, 1)
                     mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
                     ++it;
                     if (skip_tma) continue;  // fault injection: the stage's bytes never arrive
-                    tma_load_3d(sA + s * A_STAGE, &ta, &full[s], kb * KELEM, tm * BM, bz);
-                    tma_load_3d(sB + s * B_STAGE, &tb, &full[s], kb * KELEM, tn * BN, bz);
+                    const int kx = sc.kpb ? (kb % sc.kpb) * KELEM : kb * KELEM;
+                    const int kz = sc.kpb ? kb / sc.kpb : bz;
+                    tma_load_3d(sA + s * A_STAGE, &ta, &full[s], kx, tm * BM, kz);
+                    tma_load_3d(sB + s * B_STAGE, &tb, &full[s], kx, tn * BN, kz);
                 }
             }
             // copies still in flight land before the CTA exits: wait for the
@@ -424,42 +427,53 @@ __device__ __forceinline__ uint32_t bf2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
+// Embedded-operand layout.  Rows of up to 16 KB are stored whole:
+// [batch][rows][pw].  Longer rows are cut into panels of pw = 16 KB
+// (power-of-two elements, batch 1): [panel][rows][pw], so that one TMA box
+// (rows x 128 bytes of K) reads from a few pages instead of one page per row
+// (rows of megabytes otherwise miss the TLB on every row).  `rows` is the row
+// count of the whole buffer (the panel stride); pointers may be offset by whole
+// rows inside panel 0.
+struct EL {
+    int64_t rows = 0, pw = 0;
+    int np = 1, lg = 0;
+};
+__device__ __forceinline__ int64_t el_off(const EL& L, int64_t b, int64_t row, int64_t col) {
+    if (L.np == 1) return (b * L.rows + row) * L.pw + col;
+    return ((((int64_t)(col >> L.lg)) * L.rows + row) << L.lg) + (col & (L.pw - 1));
+}
+
 template <int KIND, bool IS_B>
-__device__ __forceinline__ void embed_store(void* __restrict__ out, int64_t rows_e, int64_t pitch, int64_t b,
-                                            int64_t r, int64_t k, float vr, float vi) {
+__device__ __forceinline__ void embed_store(void* __restrict__ out, const EL& L, int64_t b, int64_t r, int64_t k,
+                                            float vr, float vi) {
     if (KIND == 0) {
         const __nv_bfloat16 rh = __float2bfloat16(vr), ih = __float2bfloat16(vi);
         const __nv_bfloat16 rl = __float2bfloat16(vr - __bfloat162float(rh));
         const __nv_bfloat16 il = __float2bfloat16(vi - __bfloat162float(ih));
+        __nv_bfloat16* o = (__nv_bfloat16*)out;
         if (!IS_B) {
-            uint32_t* o = (uint32_t*)((__nv_bfloat16*)out + (b * rows_e + r) * pitch + 6 * k);
             const uint32_t hh = bf2(rh, ih);
-            o[0] = hh;
-            o[1] = hh;
-            o[2] = bf2(rl, il);
+            *(uint32_t*)(o + el_off(L, b, r, 6 * k)) = hh;
+            *(uint32_t*)(o + el_off(L, b, r, 6 * k + 2)) = hh;
+            *(uint32_t*)(o + el_off(L, b, r, 6 * k + 4)) = bf2(rl, il);
         } else {
             const __nv_bfloat16 nih = __hneg(ih), nil = __hneg(il);
-            uint32_t* o = (uint32_t*)((__nv_bfloat16*)out + (b * rows_e + 2 * r) * pitch + 6 * k);
-            const uint32_t re_h = bf2(rh, nih);
-            o[0] = re_h;
-            o[1] = bf2(rl, nil);
-            o[2] = re_h;
-            o = (uint32_t*)((char*)o + pitch * 2);
-            const uint32_t im_h = bf2(ih, rh);
-            o[0] = im_h;
-            o[1] = bf2(il, rl);
-            o[2] = im_h;
+            const uint32_t re_h = bf2(rh, nih), im_h = bf2(ih, rh);
+            *(uint32_t*)(o + el_off(L, b, 2 * r, 6 * k)) = re_h;
+            *(uint32_t*)(o + el_off(L, b, 2 * r, 6 * k + 2)) = bf2(rl, nil);
+            *(uint32_t*)(o + el_off(L, b, 2 * r, 6 * k + 4)) = re_h;
+            *(uint32_t*)(o + el_off(L, b, 2 * r + 1, 6 * k)) = im_h;
+            *(uint32_t*)(o + el_off(L, b, 2 * r + 1, 6 * k + 2)) = bf2(il, rl);
+            *(uint32_t*)(o + el_off(L, b, 2 * r + 1, 6 * k + 4)) = im_h;
         }
     } else {
         const uint32_t br = to_tf32(vr), bi = to_tf32(vi);
+        uint32_t* o = (uint32_t*)out;
         if (!IS_B) {
-            uint2* o = (uint2*)((uint32_t*)out + (b * rows_e + r) * pitch + 2 * k);
-            *o = make_uint2(br, bi);
+            *(uint2*)(o + el_off(L, b, r, 2 * k)) = make_uint2(br, bi);
         } else {
-            uint2* o = (uint2*)((uint32_t*)out + (b * rows_e + 2 * r) * pitch + 2 * k);
-            *o = make_uint2(br, bi ^ 0x80000000u);
-            o = (uint2*)((char*)o + pitch * 4);
-            *o = make_uint2(bi, br);
+            *(uint2*)(o + el_off(L, b, 2 * r, 2 * k)) = make_uint2(br, bi ^ 0x80000000u);
+            *(uint2*)(o + el_off(L, b, 2 * r + 1, 2 * k)) = make_uint2(bi, br);
         }
     }
 }
@@ -467,8 +481,7 @@ __device__ __forceinline__ void embed_store(void* __restrict__ out, int64_t rows
 // source S[b][r][k] with strides (sb, sr, sk); k fastest across threads
 template <int KIND, bool IS_B>
 __global__ void k_embed(const cplx* __restrict__ S, int64_t sb, Lvl lr, Lvl lk, int cj, int64_t batch,
-                        int64_t Rn, int64_t K, FastDiv fR, FastDiv fK, int64_t rows_e, int64_t pitch,
-                        void* __restrict__ out) {
+                        int64_t Rn, int64_t K, FastDiv fR, FastDiv fK, EL L, void* __restrict__ out) {
     const int64_t total = batch * Rn * K;
     const bool fast = total < FAST_INDEX_LIMIT;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -487,15 +500,15 @@ __global__ void k_embed(const cplx* __restrict__ S, int64_t sb, Lvl lr, Lvl lk, 
         }
         const cplx v = S[b * sb + lvl_off(lr, r) + lvl_off(lk, k)];
         const float vi = f64_to_f32_rz(v.y);
-        embed_store<KIND, IS_B>(out, rows_e, pitch, b, r, k, f64_to_f32_rz(v.x), cj ? -vi : vi);
+        embed_store<KIND, IS_B>(out, L, b, r, k, f64_to_f32_rz(v.x), cj ? -vi : vi);
     }
 }
 
 // the same for sources contiguous in r: 32x32 tiles read along r, written along k
 template <int KIND, bool IS_B>
 __global__ void __launch_bounds__(256) k_embed_t(const cplx* __restrict__ S, int64_t sb, Lvl lr, Lvl lk, int cj,
-                                                 int64_t batch, int64_t Rn, int64_t K, int64_t rows_e,
-                                                 int64_t pitch, void* __restrict__ out) {
+                                                 int64_t batch, int64_t Rn, int64_t K, EL L,
+                                                 void* __restrict__ out) {
     __shared__ cplx tile[32][33];
     const int64_t tr_n = (Rn + 31) / 32, tk_n = (K + 31) / 32;
     const int64_t ntiles = batch * tr_n * tk_n;
@@ -515,7 +528,7 @@ __global__ void __launch_bounds__(256) k_embed_t(const cplx* __restrict__ S, int
             if (r < Rn && k < K) {
                 const cplx v = tile[tx][j];
                 const float vi = f64_to_f32_rz(v.y);
-                embed_store<KIND, IS_B>(out, rows_e, pitch, b, r, k, f64_to_f32_rz(v.x), cj ? -vi : vi);
+                embed_store<KIND, IS_B>(out, L, b, r, k, f64_to_f32_rz(v.x), cj ? -vi : vi);
             }
         }
         __syncthreads();
@@ -717,8 +730,8 @@ __device__ __forceinline__ void pair_of(int64_t k, int64_t n, int64_t& p, int64_
 // along their contiguous (a,e) index and transposed through shared memory.
 template <int KIND>
 __global__ void __launch_bounds__(256) k_embed_antisym(const cplx* __restrict__ GT, int64_t ldt, int64_t a0,
-                                                       int64_t gb0, int64_t prow0, int64_t nrows, int64_t V,
-                                                       int64_t pitch, void* __restrict__ out) {
+                                                       int64_t gb0, int64_t prow0, int64_t nrows, int64_t V, EL L,
+                                                       void* __restrict__ out) {
     __shared__ cplx t1[32][33];
     __shared__ cplx t2[32][33];
     const int64_t T = (V + 31) / 32, npair = T * (T + 1) / 2;
@@ -749,8 +762,7 @@ __global__ void __launch_bounds__(256) k_embed_antisym(const cplx* __restrict__ 
             if (e < f && f < V) {
                 const cplx u = t1[tx][j], w = t2[j][tx];
                 const int64_t ef = e * (2 * V - e - 1) / 2 + (f - e - 1);
-                embed_store<KIND, false>(out, nrows, pitch, 0, row, ef, f64_to_f32_rz(u.x - w.x),
-                                         f64_to_f32_rz(u.y - w.y));
+                embed_store<KIND, false>(out, L, 0, row, ef, f64_to_f32_rz(u.x - w.x), f64_to_f32_rz(u.y - w.y));
             }
         }
         __syncthreads();
@@ -777,12 +789,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-void encode(CUtensorMap* map, const void* base, int kind, uint64_t kd, uint64_t pitch, uint64_t rows,
-            uint64_t batch, uint32_t box_rows) {
+// dims: x = K extent (the true K, or a whole panel), y = rows of this operand
+// view, z = batch or panel; strides: row pitch and batch/panel stride (the
+// buffer's full row count times the pitch)
+void encode(CUtensorMap* map, const void* base, int kind, uint64_t dx, uint64_t pitch, uint64_t rows,
+            uint64_t rows_tot, uint64_t dz, uint32_t box_rows) {
     CUtensorMapDataType dt = kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const uint64_t es = kind == 0 ? 2 : 4;
-    cuuint64_t dims[3] = {kd, rows, batch};
-    cuuint64_t strides[2] = {pitch * es, pitch * rows * es};
+    cuuint64_t dims[3] = {dx, rows, dz};
+    cuuint64_t strides[2] = {pitch * es, pitch * rows_tot * es};
     cuuint32_t box[3] = {(cuuint32_t)(ROWB / es), box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode_fn()(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
@@ -830,21 +845,58 @@ int64_t slots(int kind) { return kind == 0 ? 6 : 2; }
 
 bool gemm_tc_available() { return true; }
 
+constexpr int64_t PANEL_BYTES = 16384;
+
+// layout of an embedded operand with rows_tot rows and complex K
+static EL make_el(int kind, int64_t K, int64_t rows_tot, int64_t batch) {
+    const int64_t es = kind == 0 ? 2 : 4, q = 16 / es, kd = slots(kind) * K, full = (kd + q - 1) / q * q;
+    const int64_t pmax = PANEL_BYTES / es;
+    EL L;
+    L.rows = rows_tot;
+    if (batch == 1 && full > pmax) {
+        L.pw = pmax;
+        L.np = (int)((kd + pmax - 1) / pmax);
+        while ((int64_t(1) << L.lg) < pmax) ++L.lg;
+    } else {
+        L.pw = full;
+    }
+    return L;
+}
+
 size_t tc_embed_bytes(int prec, int64_t rows, int64_t K, int64_t batch, int64_t& rows_e, int64_t& pitch, bool is_b) {
     const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
-    const int64_t es = kind == 0 ? 2 : 4, q = 16 / es;
-    pitch = (slots(kind) * K + q - 1) / q * q;
+    const int64_t es = kind == 0 ? 2 : 4;
     rows_e = is_b ? 2 * rows : rows;
-    return (size_t)(batch * rows_e * pitch * es);
+    const EL L = make_el(kind, K, rows_e, batch);
+    pitch = L.pw;
+    return (size_t)(batch * rows_e * L.np * L.pw * es);
+}
+
+// zeros in the last panel beyond the S K used columns, for rows [0, nrows) of
+// the view at `out` (panelled layouts only: TMA reads whole panels)
+static void zero_tail(Dev& D, int kind, void* out, const EL& L, int64_t K, int64_t nrows) {
+    if (L.np == 1 || nrows <= 0) return;
+    const int64_t es = kind == 0 ? 2 : 4, kd = slots(kind) * K, used = kd - (int64_t)(L.np - 1) * L.pw;
+    if (used >= L.pw) return;
+    char* p = (char*)out + (size_t)(((int64_t)(L.np - 1) * L.rows * L.pw + used) * es);
+    CK(cudaMemset2DAsync(p, (size_t)(L.pw * es), 0, (size_t)((L.pw - used) * es), (size_t)nrows, D.st));
+}
+
+void tc_zero_tail(Dev& D, int prec, void* out, int64_t rows_tot, int64_t K, int64_t nrows) {
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    zero_tail(D, kind, out, make_el(kind, K, rows_tot, 1), K, nrows);
 }
 
 // embedding of op(S)[b][r][k] (rows r, K index k); tiled when consecutive rows
 // are consecutive in memory and k is not
 static void embed_impl(Dev& D, int prec, bool is_b, const cplx* S, int64_t sb, const Lvl& lr, const Lvl& lk, bool cj,
-                       int64_t batch, int64_t Rn, int64_t K, int64_t pitch, void* out) {
+                       int64_t batch, int64_t Rn, int64_t K, int64_t pitch, int64_t rows_tot, void* out) {
     if (batch * Rn * K == 0) return;
     const bool tiled = lr.s == 1 && lk.s != 1;
-    const int64_t rows_e = is_b ? 2 * Rn : Rn;
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    const EL L = make_el(kind, K, rows_tot, batch);
+    REQUIRE(L.pw == pitch, "embed: pitch does not match the layout");
+    zero_tail(D, kind, out, L, K, is_b ? 2 * Rn : Rn);
     const int64_t nt = batch * ((Rn + 31) / 32) * ((K + 31) / 32);
     const int gt = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)D.sm_count * 8));
     const int g = grid_n(D, batch * Rn * K);
@@ -852,32 +904,32 @@ static void embed_impl(Dev& D, int prec, bool is_b, const cplx* S, int64_t sb, c
     const FastDiv fR(Rn), fK(K);
     if (prec == LRCC_MIXED_BF16X3) {
         if (is_b) {
-            if (tiled) k_embed_t<0, true><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, rows_e, pitch, out);
-            else k_embed<0, true><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, rows_e, pitch, out);
+            if (tiled) k_embed_t<0, true><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, L, out);
+            else k_embed<0, true><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, L, out);
         } else {
-            if (tiled) k_embed_t<0, false><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, rows_e, pitch, out);
-            else k_embed<0, false><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, rows_e, pitch, out);
+            if (tiled) k_embed_t<0, false><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, L, out);
+            else k_embed<0, false><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, L, out);
         }
     } else {
         if (is_b) {
-            if (tiled) k_embed_t<1, true><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, rows_e, pitch, out);
-            else k_embed<1, true><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, rows_e, pitch, out);
+            if (tiled) k_embed_t<1, true><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, L, out);
+            else k_embed<1, true><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, L, out);
         } else {
-            if (tiled) k_embed_t<1, false><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, rows_e, pitch, out);
-            else k_embed<1, false><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, rows_e, pitch, out);
+            if (tiled) k_embed_t<1, false><<<gt, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, L, out);
+            else k_embed<1, false><<<g, 256, 0, D.st>>>(S, sb, lr, lk, c, batch, Rn, K, fR, fK, L, out);
         }
     }
     LAUNCH_CHECK(D);
 }
 
 void tc_embed_a(Dev& D, int prec, const cplx* A, int64_t sAb, int64_t sAm, int64_t sAk, bool cA, int64_t batch,
-                int64_t M, int64_t K, int64_t pitch, void* out) {
-    embed_impl(D, prec, false, A, sAb, mk_lvl(sAm), mk_lvl(sAk), cA, batch, M, K, pitch, out);
+                int64_t M, int64_t K, int64_t pitch, int64_t rows_tot, void* out) {
+    embed_impl(D, prec, false, A, sAb, mk_lvl(sAm), mk_lvl(sAk), cA, batch, M, K, pitch, rows_tot, out);
 }
 
 void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64_t sBn, bool cB, int64_t batch,
-                int64_t K, int64_t N, int64_t pitch, void* out) {
-    embed_impl(D, prec, true, B, sBb, mk_lvl(sBn), mk_lvl(sBk), cB, batch, N, K, pitch, out);
+                int64_t K, int64_t N, int64_t pitch, int64_t rows_tot, void* out) {
+    embed_impl(D, prec, true, B, sBb, mk_lvl(sBn), mk_lvl(sBk), cB, batch, N, K, pitch, rows_tot, out);
 }
 
 // One persistent launch: C = alpha op(A' B'^T) + beta C on embedded operands
@@ -885,18 +937,20 @@ void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64
 // take part (kind 0: bf16, 1: tf32); FP32 accumulation chains of at most
 // kchunk k-blocks, added to C in FP64.
 static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
-                      int64_t kd, int64_t pitch, cplx* C, int64_t sCb, const Lvl& lm, const Lvl& ln, cplx alpha,
-                      cplx beta, bool conj_acc, int kchunk, bool exact_alpha, double useful_flops,
-                      const char* name) {
+                      int64_t kd, int64_t pitch, int64_t rows_a, int64_t rows_b, int np, cplx* C, int64_t sCb,
+                      const Lvl& lm, const Lvl& ln, cplx alpha, cplx beta, bool conj_acc, int kchunk,
+                      bool exact_alpha, double useful_flops, const char* name) {
     REQUIRE(D.err_flag != nullptr, "gemm_tc: no error word");
     if (M <= 0 || N <= 0 || batch <= 0) return;
     const int64_t es = kind == 0 ? 2 : 4, kelem = ROWB / es;
-    REQUIRE(kd > 0 && pitch >= kd && (pitch * es) % 16 == 0, "gemm_tc: bad embedded K");
+    REQUIRE(kd > 0 && (np > 1 || pitch >= kd) && (pitch * es) % 16 == 0 && (np == 1 || (batch == 1 && pitch % kelem == 0)),
+            "gemm_tc: bad embedded K");
     REQUIRE(((uintptr_t)pa % 16) == 0 && ((uintptr_t)pb % 16) == 0, "gemm_tc: operands not 16-byte aligned");
     const int bn = bn_for(2 * N);
     CUtensorMap ta, tb;
-    encode(&ta, pa, kind, (uint64_t)kd, (uint64_t)pitch, (uint64_t)M, (uint64_t)batch, BM);
-    encode(&tb, pb, kind, (uint64_t)kd, (uint64_t)pitch, (uint64_t)(2 * N), (uint64_t)batch, (uint32_t)bn);
+    const uint64_t dx = np > 1 ? (uint64_t)pitch : (uint64_t)kd, dz = np > 1 ? (uint64_t)np : (uint64_t)batch;
+    encode(&ta, pa, kind, dx, (uint64_t)pitch, (uint64_t)M, (uint64_t)rows_a, dz, BM);
+    encode(&tb, pb, kind, dx, (uint64_t)pitch, (uint64_t)(2 * N), (uint64_t)rows_b, dz, (uint32_t)bn);
     const int64_t tiles_m = (M + BM - 1) / BM, tiles_n = (2 * N + bn - 1) / bn;
     const int64_t tiles = tiles_m * tiles_n * batch;
     REQUIRE(tiles_m < INT32_MAX && tiles_n < INT32_MAX && tiles < ((int64_t)1 << 40), "gemm_tc: too many tiles");
@@ -930,6 +984,7 @@ static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t 
     sc.num_kb = num_kb;
     sc.group = (int)std::min<int64_t>(tiles_m, 16);
     sc.kchunk = kchunk;
+    sc.kpb = np > 1 ? (int)(pitch / kelem) : 0;
     sc.units = (long long)tiles * splits;
     REQUIRE(batch < INT32_MAX, "gemm_tc: batch too large");
     Epi ep{M, N, C, sCb, lm, ln, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0, exact_alpha ? 1 : 0};
@@ -963,12 +1018,15 @@ static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t 
 // C = alpha * op(A' B'^T) + beta C on embedded operands A' [batch][M][pitch],
 // B' [batch][2N][pitch], complex K (S*K embedded columns)
 void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
-                      int64_t K, int64_t pitch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
-                      cplx beta, bool conj_acc, double useful_flops) {
+                      int64_t K, int64_t pitch, int64_t rows_a, int64_t rows_b, cplx* C, int64_t sCb, int64_t sCm,
+                      int64_t sCn, cplx alpha, cplx beta, bool conj_acc, double useful_flops) {
     const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
     REQUIRE(K > 0, "gemm_tc: bad embedded K");
-    tc_launch(D, kind, pa, pb, batch, M, N, slots(kind) * K, pitch, C, sCb, mk_lvl(sCm), mk_lvl(sCn), alpha, beta,
-              conj_acc, KCHUNK, false, useful_flops, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32");
+    const EL L = make_el(kind, K, rows_a, batch);
+    REQUIRE(L.pw == pitch, "gemm_tc: pitch does not match the layout");
+    tc_launch(D, kind, pa, pb, batch, M, N, slots(kind) * K, pitch, rows_a, rows_b, L.np, C, sCb, mk_lvl(sCm),
+              mk_lvl(sCn), alpha, beta, conj_acc, KCHUNK, false, useful_flops,
+              kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32");
 }
 
 // relative cost of running C[M][N] in this orientation: padded tensor-core
@@ -1008,24 +1066,28 @@ void gemm_tc(Dev& D, const GemmArgs& g0, int prec) {
     void* pb = D.pool.get(bytesB);
     std::shared_ptr<DevBuf> hb(new DevBuf{&D.pool, pb, bytesB});
     embed_impl(D, prec, false, g.A, g.sAb, mk_lvl(g.sAm, g.dAm2, g.sAm1), mk_lvl(g.sAk, g.dAk2, g.sAk1), g.cA,
-               g.batch, g.M, g.K, pitch, pa);
+               g.batch, g.M, g.K, pitch, rowsA, pa);
     embed_impl(D, prec, true, g.B, g.sBb, mk_lvl(g.sBn, g.dBn2, g.sBn1), mk_lvl(g.sBk, g.dBk2, g.sBk1), g.cB,
-               g.batch, g.N, g.K, pitch, pb);
+               g.batch, g.N, g.K, pitch, rowsB, pb);
     const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
-    tc_launch(D, kind, pa, pb, g.batch, g.M, g.N, slots(kind) * g.K, pitch, g.C, g.sCb,
+    const EL L = make_el(kind, g.K, rowsA, g.batch);
+    tc_launch(D, kind, pa, pb, g.batch, g.M, g.N, slots(kind) * g.K, pitch, rowsA, rowsB, L.np, g.C, g.sCb,
               mk_lvl(g.sCm, g.dCm2, g.sCm1), mk_lvl(g.sCn, g.dCn2, g.sCn1), g.alpha, g.beta, false, KCHUNK, false,
               8.0 * g.M * g.N * g.K * g.batch, kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32");
 }
 
 void tc_embed_antisym_slab(Dev& D, int prec, const cplx* GT, int64_t ldt, int64_t a0, int64_t gb0, int64_t prow0,
-                           int64_t nrows, int64_t V, int64_t pitch, void* out) {
+                           int64_t nrows, int64_t V, int64_t pitch, int64_t rows_tot, void* out) {
     const int64_t T = (V + 31) / 32, tasks = nrows * T * (T + 1) / 2;
     if (tasks <= 0) return;
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    const EL L = make_el(kind, V * (V - 1) / 2, rows_tot, 1);
+    REQUIRE(L.pw == pitch, "ladder: pitch does not match the layout");
     const int grid = (int)std::min<int64_t>(tasks, (int64_t)D.sm_count * 8);
     if (prec == LRCC_MIXED_BF16X3)
-        k_embed_antisym<0><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, pitch, out);
+        k_embed_antisym<0><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, L, out);
     else
-        k_embed_antisym<1><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, pitch, out);
+        k_embed_antisym<1><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, L, out);
     LAUNCH_CHECK(D);
 }
 
@@ -1093,7 +1155,8 @@ void oz_gemm_embedded(Dev& D, const void* pa, const void* pb, int64_t batch, int
     const double useful = 8.0 * M * N * K * batch, pairs = OZ_S * (OZ_S + 1) / 2.0;
     for (int d = 0; d < OZ_S; ++d) {
         const char* pbd = (const char*)pb + (size_t)((OZ_S - 1 - d) * kpad * 2);
-        tc_launch(D, 0, pa, pbd, batch, M, N, (d + 1) * kpad, OZ_S * kpad, C, sCb, mk_lvl(sCm), mk_lvl(sCn), alpha,
+        tc_launch(D, 0, pa, pbd, batch, M, N, (d + 1) * kpad, OZ_S * kpad, M, 2 * N, 1, C, sCb, mk_lvl(sCm),
+                  mk_lvl(sCn), alpha,
                   d == 0 ? beta : mkc(1.0), conj_acc, OZ_KCHUNK, true, useful * (d + 1) / pairs, "gemm_tc_f64emu");
     }
 }

@@ -290,10 +290,15 @@ void gemm_tc(Dev& D, const GemmArgs& g, int prec);
 // columns is written or read), the split/convert kernels, and the GEMM on
 // already embedded operands (complex K)
 size_t tc_embed_bytes(int prec, int64_t rows, int64_t K, int64_t batch, int64_t& rows_e, int64_t& pitch, bool is_b);
+// (rows_tot: embedded rows of the whole destination buffer, whose K panels are
+// that many rows apart; out may point at a row inside it)
 void tc_embed_a(Dev& D, int prec, const cplx* A, int64_t sAb, int64_t sAm, int64_t sAk, bool cA, int64_t batch,
-                int64_t M, int64_t K, int64_t pitch, void* out);
+                int64_t M, int64_t K, int64_t pitch, int64_t rows_tot, void* out);
 void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64_t sBn, bool cB, int64_t batch,
-                int64_t K, int64_t N, int64_t pitch, void* out);
+                int64_t K, int64_t N, int64_t pitch, int64_t rows_tot, void* out);
+// zeros beyond the used K in the last panel of rows [0, nrows) at out (buffers
+// filled by tc_embed_antisym_slab)
+void tc_zero_tail(Dev& D, int prec, void* out, int64_t rows_tot, int64_t K, int64_t nrows);
 // FP64-class complex GEMM on bf16 tensor cores (integer slices with per-row
 // exponents, exact FP32 chains, FP64 sums): gemm_tc_f64 is the whole GEMM;
 // the pieces embed operands as [batch][rows_e][7 kpad] bf16 and run the
@@ -308,8 +313,8 @@ void oz_gemm_embedded(Dev& D, const void* pa, const void* pb, int64_t batch, int
                       int64_t kpad, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha, cplx beta,
                       bool conj_acc);
 void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
-                      int64_t K, int64_t pitch, cplx* C, int64_t sCb, int64_t sCm, int64_t sCn, cplx alpha,
-                      cplx beta, bool conj_acc, double useful_flops);
+                      int64_t K, int64_t pitch, int64_t rows_a, int64_t rows_b, cplx* C, int64_t sCb, int64_t sCm,
+                      int64_t sCn, cplx alpha, cplx beta, bool conj_acc, double useful_flops);
 
 // ---------------------------------------------------------------------------
 // contraction engine (engine.cu)
@@ -338,7 +343,7 @@ struct LadderCtx {
     // embedded Bvv as the B operand (n = (b,f), k = L) of the slab assembly
     std::shared_ptr<DevBuf> bcache;
     int bcache_prec = -1;
-    int64_t b_pitch = 0;
+    int64_t b_pitch = 0, b_rows = 0;
     // cached FP64 <ab||ef> matrix [P_V][P_V] for the FP64 ladder, when it fits,
     // built with FP64 (LRCC_FP64) or FP64-class (LRCC_FP64_EMULATED) products
     Tensor w64;
@@ -356,7 +361,7 @@ void ladder_packed(Dev& D, LadderCtx& L, const cplx* Xt, cplx* Zt, int64_t ncol,
 // embedded <ab||ef> rows of one slab from GT[(b,f)][(a,e)] (leading dimension ldt),
 // rows (a,b) = pair(prow0 + row), written as A operand rows [nrows][pitch]
 void tc_embed_antisym_slab(Dev& D, int prec, const cplx* GT, int64_t ldt, int64_t a0, int64_t gb0, int64_t prow0,
-                           int64_t nrows, int64_t V, int64_t pitch, void* out);
+                           int64_t nrows, int64_t V, int64_t pitch, int64_t rows_tot, void* out);
 
 // pair index of (p<q) among n, row-major strict upper triangle
 __host__ __device__ inline int64_t pair_index(int64_t p, int64_t q, int64_t n) {
