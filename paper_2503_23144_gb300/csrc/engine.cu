@@ -809,8 +809,9 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
     const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
     ensure_bcache(D, LC, prec);
     const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), LC.slab_rows);
-    const int64_t cap = LC.slab_rows > 0 ? 3 * LC.slab_rows
-                                         : group_rows(D, 0.25 * free_bytes(D), double(pitch * es), ncol);
+    int64_t r1, p1;
+    const double row_bytes = (double)tc_embed_bytes(prec, 1, PV, 1, r1, p1, false);  // one embedded W' row
+    const int64_t cap = LC.slab_rows > 0 ? 3 * LC.slab_rows : group_rows(D, 0.25 * free_bytes(D), row_bytes, ncol);
     const std::vector<SlabGroup> groups = group_chunks(plan, cap);
     SlabScratch sc(D, plan, V);
     int64_t wrows = 0;

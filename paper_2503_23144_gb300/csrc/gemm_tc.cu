@@ -428,19 +428,21 @@ __device__ __forceinline__ uint32_t bf2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
 }
 
 // Embedded-operand layout.  Rows of up to 16 KB are stored whole:
-// [batch][rows][pw].  Longer rows are cut into panels of pw = 16 KB
-// (power-of-two elements, batch 1): [panel][rows][pw], so that one TMA box
+// [batch][rows][pw].  Longer rows are cut into np equal panels of at most
+// 16 KB (pw a multiple of 128 bytes, batch 1): [panel][rows][pw], so that one TMA box
 // (rows x 128 bytes of K) reads from a few pages instead of one page per row
 // (rows of megabytes otherwise miss the TLB on every row).  `rows` is the row
 // count of the whole buffer (the panel stride); pointers may be offset by whole
 // rows inside panel 0.
 struct EL {
     int64_t rows = 0, pw = 0;
-    int np = 1, lg = 0;
+    int np = 1;
+    FastDiv fpw;
 };
 __device__ __forceinline__ int64_t el_off(const EL& L, int64_t b, int64_t row, int64_t col) {
     if (L.np == 1) return (b * L.rows + row) * L.pw + col;
-    return ((((int64_t)(col >> L.lg)) * L.rows + row) << L.lg) + (col & (L.pw - 1));
+    const uint32_t p = L.fpw.div((uint32_t)col);
+    return ((int64_t)p * L.rows + row) * L.pw + (col - (int64_t)p * L.pw);
 }
 
 template <int KIND, bool IS_B>
@@ -850,13 +852,13 @@ constexpr int64_t PANEL_BYTES = 16384;
 // layout of an embedded operand with rows_tot rows and complex K
 static EL make_el(int kind, int64_t K, int64_t rows_tot, int64_t batch) {
     const int64_t es = kind == 0 ? 2 : 4, q = 16 / es, kd = slots(kind) * K, full = (kd + q - 1) / q * q;
-    const int64_t pmax = PANEL_BYTES / es;
+    const int64_t pmax = PANEL_BYTES / es, kel = ROWB / es;
     EL L;
     L.rows = rows_tot;
     if (batch == 1 && full > pmax) {
-        L.pw = pmax;
         L.np = (int)((kd + pmax - 1) / pmax);
-        while ((int64_t(1) << L.lg) < pmax) ++L.lg;
+        L.pw = ((kd + L.np - 1) / L.np + kel - 1) / kel * kel;  // equal panels, whole k-blocks
+        L.fpw = FastDiv(L.pw);
     } else {
         L.pw = full;
     }
