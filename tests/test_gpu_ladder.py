@@ -120,3 +120,19 @@ def test_packed_matches_full_layout(L, sys19):
         zf = L.lrcc_ladder_dev(ctx, torch.as_tensor(x).cuda(), prec=prec).cpu().numpy()
         zp = L.lrcc_ladder_packed_dev(ctx, torch.as_tensor(xt).cuda(), prec=prec).cpu().numpy()
         assert np.abs(zf[:, iu, ju][:, :, au, bu].reshape(zp.shape) - zp).max() < 1e-12 * np.abs(zp).max()
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 3e-3), (2, 1e-4)])
+@pytest.mark.parametrize("slab_rows", [0, 13])
+def test_packed_long_rows_in_panels(L, prec, tol, slab_rows):
+    """V = 60: the embedded rows (6 P_V bf16 = 10 620 elements, 2 P_V TF32) are
+    longer than one 16 KB panel, so <ab||ef> and X' are stored in K panels."""
+    s = synth.make_system(3, 60, 40, seed=14)
+    ctx = _ctx(L, s, slab_rows=slab_rows)
+    pv = 60 * 59 // 2
+    for ncol in (5, 48):
+        xd = torch.as_tensor(_xt(ncol, pv, 300 + ncol)).cuda()
+        for tr in (False, True):
+            z64 = L.lrcc_ladder_packed_dev(ctx, xd, transpose=tr)
+            z = L.lrcc_ladder_packed_dev(ctx, xd, transpose=tr, prec=prec)
+            assert (z - z64).abs().max().item() < tol * z64.abs().max().item(), (ncol, tr)
