@@ -19,6 +19,9 @@ Plain numpy, complex128, following Sec. II.B-C of the paper:
 8. rotate B^L and mu into the new virtual basis; new virtual energies are the
    semicanonical eigenvalues.
 
+Plain FNS (Eq. 40) replaces step 2-5 by the ground-state MP2 virtual density
+D_ab = 1/2 sum_ijc t_ij^ac conj(t_ij^bc) and keeps steps 6-8.
+
 Readings where the paper is ambiguous (the project's readings): Eq. 40/45 are
 taken with the complex conjugate on the second amplitude (Hermitian density);
 the three directions are averaged at the level of densities; the denominator
@@ -62,20 +65,33 @@ def hbar_diagonals(eps, B, O, t2):
     return Hii, Haa
 
 
-def first_order_amplitudes(eps, B, mu_c, O, t2, Hii, Haa, omega=0.0, plus_omega=False):
-    """Abar over (Dbar -/+ omega) for one perturbation A = mu_c (Eq. 46-48)."""
-    N = eps.shape[0]
+def perturbed_moments(eps, B, mu_c, O, t2):
+    """Abar for one perturbation A = mu_c (Eq. 48 for the doubles; singles
+    A_ai + sum_me A_me t_im^ae).  Returns ([O, V], [O, O, V, V])."""
     A = np.asarray(mu_c)
     Aoo, Aov, Avo, Avv = A[:O, :O], A[:O, O:], A[O:, :O], A[O:, O:]
     X = np.einsum('ijae,be->ijab', t2, Avv)
     Yy = np.einsum('imab,mj->ijab', t2, Aoo)
     A2 = (X - X.transpose(0, 1, 3, 2)) - (Yy - Yy.transpose(1, 0, 2, 3))
     A1 = Avo.T + np.einsum('me,imae->ia', Aov, t2)
-    s = 1.0 if plus_omega else -1.0
+    return A1, A2
+
+
+def hbar_denominators(Hii, Haa):
+    """Dbar of Eq. 47: Hbar_aa - Hbar_ii (singles), Hbar_aa + Hbar_bb -
+    Hbar_ii - Hbar_jj (doubles)."""
     D2 = (Haa[None, None, :, None] + Haa[None, None, None, :]
-          - Hii[:, None, None, None] - Hii[None, :, None, None]) + s * omega
-    D1 = Haa[None, :] - Hii[:, None] + s * omega
-    return A1 / D1, A2 / D2
+          - Hii[:, None, None, None] - Hii[None, :, None, None])
+    D1 = Haa[None, :] - Hii[:, None]
+    return D1, D2
+
+
+def first_order_amplitudes(eps, B, mu_c, O, t2, Hii, Haa, omega=0.0, plus_omega=False):
+    """Abar over (Dbar -/+ omega) for one perturbation A = mu_c (Eq. 46-48)."""
+    A1, A2 = perturbed_moments(eps, B, mu_c, O, t2)
+    s = 1.0 if plus_omega else -1.0
+    D1, D2 = hbar_denominators(Hii, Haa)
+    return A1 / (D1 + s * omega), A2 / (D2 + s * omega)
 
 
 def fnspp_density(eps, B, mu, O, omega=0.0, plus_omega=False):
@@ -88,6 +104,47 @@ def fnspp_density(eps, B, mu, O, omega=0.0, plus_omega=False):
         t1p, t2p = first_order_amplitudes(eps, B, mu[c], O, t2, Hii, Haa, omega, plus_omega)
         M += 0.5 * np.einsum('ijac,ijbc->ab', t2p, t2p.conj()) + np.einsum('ia,ib->ab', t1p, t1p.conj())
     return M / 3.0
+
+
+def mp2_density(eps, B, O):
+    """Ground-state MP2 virtual density [V, V] of plain FNS (Eq. 40)."""
+    t2 = mp2_doubles(eps, B, O)
+    return 0.5 * np.einsum('ijac,ijbc->ab', t2, t2.conj())
+
+
+def mp2_polarizability(system, comps, omegas):
+    """MP2-level polarisability (the ingredient of the Delta alpha_MP2
+    correction, Eq. 53-54), in the system's own virtual basis.
+
+    Reading: the sum-over-states response function (Eq. 18, alpha =
+    -<<A;B>>) over the singly and doubly excited determinants mu, with the
+    MP2-dressed transition moments Abar_mu of Eq. 48 and the diagonal
+    excitation energies Dbar_mu of Eq. 47 (Hbar of Eq. 49-50):
+
+        alpha_AB(w) = sum_mu conj(Abar_mu) Bbar_mu / (Dbar_mu - w)
+                             + Abar_mu conj(Bbar_mu) / (Dbar_mu + w)
+
+    i.e. sum_mu conj(Abar_mu) t^(1)_mu(B; w) + Abar_mu conj(t^(1)_mu(B; -w))
+    with the Eq. 46 amplitudes t^(1) = Bbar / (Dbar - w); the doubles run over
+    unique (i<j, a<b), a quarter of the full-array sum.
+    Returns [n_w, n_c, n_c] complex."""
+    eps = np.asarray(system["eps"], dtype=np.float64)
+    B = np.asarray(system["B"])
+    mu = np.asarray(system["mu"])
+    O = system["O"]
+    t2 = mp2_doubles(eps, B, O)
+    Hii, Haa = hbar_diagonals(eps, B, O, t2)
+    D1, D2 = hbar_denominators(Hii, Haa)
+    mom = {c: perturbed_moments(eps, B, mu[c], O, t2) for c in comps}
+    out = np.zeros((len(omegas), len(comps), len(comps)), dtype=np.complex128)
+    for wi, w in enumerate(omegas):
+        for a, A in enumerate(comps):
+            for b, Bc in enumerate(comps):
+                (a1, a2), (b1, b2) = mom[A], mom[Bc]
+                s1 = np.sum(a1.conj() * b1 / (D1 - w) + a1 * b1.conj() / (D1 + w))
+                s2 = np.sum(a2.conj() * b2 / (D2 - w) + a2 * b2.conj() / (D2 + w))
+                out[wi, a, b] = s1 + 0.25 * s2
+    return out
 
 
 def select(n: np.ndarray, by_count: bool, value: float) -> np.ndarray:
@@ -106,13 +163,20 @@ def select(n: np.ndarray, by_count: bool, value: float) -> np.ndarray:
     return keep
 
 
-def truncate(system, by_count=True, value=None, omega=0.0, plus_omega=False):
-    """FNS++ truncation.  Returns (new_system, occupations sorted by |n| desc)."""
+def truncate(system, by_count=True, value=None, omega=0.0, plus_omega=False, density="fnspp"):
+    """FNS++ (``density="fnspp"``, Eq. 45) or plain FNS (``density="mp2"``,
+    Eq. 40) truncation.  Returns (new_system, occupations sorted by |n| desc,
+    details)."""
     eps = np.asarray(system["eps"], dtype=np.float64)
     B = np.asarray(system["B"])
     mu = np.asarray(system["mu"])
     O = system["O"]
-    M = fnspp_density(eps, B, mu, O, omega, plus_omega)
+    if density == "fnspp":
+        M = fnspp_density(eps, B, mu, O, omega, plus_omega)
+    elif density == "mp2":
+        M = mp2_density(eps, B, O)
+    else:
+        raise ValueError("density must be 'fnspp' or 'mp2'")
     n, Vn = np.linalg.eigh(M)
     keep = select(n, by_count, value)
     Vt = Vn[:, keep]

@@ -302,3 +302,143 @@ def test_fnspp_density_properties():
     assert new["V"] == 4 and new["B"].shape == (12, O + 4, O + 4)
     Bn = new["B"]
     assert np.abs(Bn - Bn.conj().transpose(0, 2, 1)).max() < 1e-15
+
+
+# --- FNS (Eq. 37-41) and FNS++ (Eq. 45) densities from the wave function ----
+
+def _vv_density_bruteforce(psi, O, V, dets, index):
+    """D_ab = <psi| a_b^+ a_a |psi>: the virtual block of the one-particle
+    density whose eigenvectors are natural-spinor coefficients (columns)."""
+    N = O + V
+    D = np.zeros((V, V), dtype=np.complex128)
+    for a in range(V):
+        for b in range(V):
+            h = np.zeros((N, N))
+            h[O + b, O + a] = 1.0
+            G = fci.one_body_matrix(h, dets, index)
+            D[a, b] = psi.conj() @ (G @ psi)
+    return D
+
+
+@pytest.mark.parametrize("O,V,seed", [(2, 5, 3), (3, 4, 6)])
+def test_fns_densities_equal_wavefunction_densities(O, V, seed):
+    """Plain FNS: |Psi1> = 1/4 sum t_ij^ab |Phi_ij^ab> with MP2 doubles
+    (Eq. 38-39); FNS++: |Psi1^A> = (T1^(1) + T2^(1))|Phi_0> with the Eq. 46
+    amplitudes.  Their virtual densities, evaluated in the determinant space,
+    equal the contracted forms of Eq. 40 and Eq. 45 (conjugate on the second
+    amplitude)."""
+    s = synth.make_system(O, V, 6, seed=seed)
+    N = O + V
+    dets, index = fci.determinants(N, O)
+    ref = index[(1 << O) - 1]
+    phi0 = np.zeros(len(dets), dtype=np.complex128)
+    phi0[ref] = 1.0
+    t2 = fns.mp2_doubles(s["eps"], s["B"], O)
+    assert np.abs(t2).max() > 1e-3                        # a non-trivial check
+    T = fci.cluster_matrix(np.zeros((O, V)), t2, O, dets, index)
+    D = _vv_density_bruteforce(T @ phi0, O, V, dets, index)
+    M = fns.mp2_density(s["eps"], s["B"], O)
+    assert np.abs(M - D).max() < 1e-14 * np.abs(D).max() * 10
+    assert np.abs(M - M.T).max() > 1e-6 * np.abs(M).max()  # complex: M differs from its transpose
+    # FNS++ (Eq. 45): singles and doubles of each component, averaged
+    Hii, Haa = fns.hbar_diagonals(s["eps"], s["B"], O, t2)
+    Dpp = np.zeros((V, V), dtype=np.complex128)
+    for c in range(3):
+        t1p, t2p = fns.first_order_amplitudes(s["eps"], s["B"], s["mu"][c], O, t2, Hii, Haa, 0.03)
+        Tp = fci.cluster_matrix(t1p, t2p, O, dets, index)
+        Dpp += _vv_density_bruteforce(Tp @ phi0, O, V, dets, index) / 3.0
+    Mpp = fns.fnspp_density(s["eps"], s["B"], s["mu"], O, 0.03)
+    assert np.abs(Mpp - Dpp).max() < 1e-14 * np.abs(Dpp).max() * 10
+
+
+def test_plain_fns_exact_when_doubles_span_a_subspace():
+    """If only the virtuals in S couple to the occupied space (B^L_ai = 0 for
+    a outside S), the MP2 doubles vanish outside S, the plain-FNS density has
+    exactly |S| non-zero occupations, and keeping them reproduces the
+    full-space MP2 energy (Eq. 51-52: Delta E_MP2 = 0)."""
+    O, V, L = 3, 9, 10
+    s = synth.make_system(O, V, L, seed=17)
+    S = [0, 2, 3, 7]
+    out = [a for a in range(V) if a not in S]
+    B = s["B"].copy()
+    for a in out:
+        B[:, O + a, :O] = 0.0
+        B[:, :O, O + a] = 0.0
+    s = dict(s, B=B)
+    new, occ, info = fns.truncate(s, True, len(S), density="mp2")
+    assert occ[len(S) - 1] > 1e-8 and occ[len(S):].max() < 1e-15 * occ[0]
+    e_full = fns.mp2_energy(s["eps"], B, O)
+    e_tr = fns.mp2_energy(new["eps"], new["B"], O)
+    assert abs(e_full) > 1e-4
+    assert abs(e_full - e_tr) < 1e-13 * abs(e_full)
+    assert np.allclose(np.sort(new["eps"][O:]), np.sort(s["eps"][O:][S]), rtol=0, atol=1e-13)
+    # the FNS++ density also sees mu_vv, which mixes in virtuals outside S
+    _, occ_pp, _ = fns.truncate(s, True, len(S))
+    assert occ_pp[len(S):].max() > 1e-10
+
+
+def test_plain_fns_untruncated_reproduces_full_alpha():
+    O, V = 3, 6
+    s = synth.make_system(O, V, 12, seed=4)
+    oms = [0.0, 0.04]
+    a_full = ccsd.polarizability(s, (0, 1, 2), oms)
+    new, occ, _ = fns.truncate(s, True, V, density="mp2")
+    a_tr = ccsd.polarizability(new, (0, 1, 2), oms)
+    assert np.abs(a_full - a_tr).max() < 1e-10 * np.abs(a_full).max()
+
+
+# --- MP2-level polarisability (Delta alpha_MP2 ingredient, Eq. 53-54) -------
+
+def test_mp2_polarizability_is_determinant_sum_over_states():
+    """The contracted form equals the sum over excited determinants k of
+    conj(<k|Abar>) <k|Bbar> / (Dbar_k - w) + <k|Abar> conj(<k|Bbar>) / (Dbar_k + w),
+    with |Abar> = (Abar_1 + Abar_2)|Phi_0> built in the determinant space and
+    Dbar_k = sum of Hbar over the particles minus the holes of k."""
+    O, V = 3, 4
+    s = synth.make_system(O, V, 7, seed=19)
+    comps, oms = (0, 2), [0.0, 0.07]
+    got = fns.mp2_polarizability(s, comps, oms)
+    N = O + V
+    dets, index = fci.determinants(N, O)
+    ref_det = (1 << O) - 1
+    phi0 = np.zeros(len(dets), dtype=np.complex128)
+    phi0[index[ref_det]] = 1.0
+    t2 = fns.mp2_doubles(s["eps"], s["B"], O)
+    Hii, Haa = fns.hbar_diagonals(s["eps"], s["B"], O, t2)
+    H = np.concatenate([Hii, Haa])
+    dk = np.array([sum(H[p] for p in range(N) if (d >> p) & 1 and p >= O)
+                   - sum(H[p] for p in range(O) if not (d >> p) & 1) for d in dets])
+    vec = {}
+    for c in comps:
+        a1, a2 = fns.perturbed_moments(s["eps"], s["B"], s["mu"][c], O, t2)
+        vec[c] = fci.cluster_matrix(a1, a2, O, dets, index) @ phi0
+    exc = np.arange(len(dets)) != index[ref_det]
+    ref = np.zeros_like(got)
+    for wi, w in enumerate(oms):
+        for a, A in enumerate(comps):
+            for b, Bc in enumerate(comps):
+                x, y = vec[A][exc], vec[Bc][exc]
+                ref[wi, a, b] = np.sum(x.conj() * y / (dk[exc] - w) + x * y.conj() / (dk[exc] + w))
+    assert np.abs(ref).max() > 1e-2
+    assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+    assert np.abs(got - got.conj().transpose(0, 2, 1)).max() < 1e-14 * np.abs(got).max()
+
+
+def test_mp2_polarizability_noninteracting_limit_and_untruncated_basis():
+    """Without two-electron terms it is the exact independent-particle alpha
+    (determinant-space SOS); with every natural spinor kept the FNS rotation
+    leaves it unchanged (Delta alpha_MP2 = 0)."""
+    O, V = 2, 5
+    s = synth.make_system(O, V, 4, seed=6)
+    s0 = dict(s, B=np.zeros_like(s["B"]))
+    comps, oms = (0, 1, 2), [0.0, 0.1]
+    sos, _, _ = fci.sos_polarizability(ccsd.fock_of(s), s0["B"], s["mu"], O, comps, oms)
+    got = fns.mp2_polarizability(s0, comps, oms)
+    assert np.abs(got - sos).max() < 1e-12 * np.abs(sos).max()
+    s2 = synth.make_system(3, 6, 9, seed=2)
+    full = fns.mp2_polarizability(s2, comps, oms)
+    for density in ("fnspp", "mp2"):
+        new, _, _ = fns.truncate(s2, True, 6, density=density)
+        assert np.abs(fns.mp2_polarizability(new, comps, oms) - full).max() < 1e-12 * np.abs(full).max()
+        new, _, _ = fns.truncate(s2, True, 3, density=density)
+        assert np.abs(fns.mp2_polarizability(new, comps, oms) - full).max() > 1e-6 * np.abs(full).max()
