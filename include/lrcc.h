@@ -77,6 +77,10 @@ typedef struct {
                               F X, ground-state polish) use 1 (default): integer-slice
                               products on the tensor cores (as LRCC_FP64_EMULATED),
                               0: FP64 SIMT products                                  */
+    int fns_density;       /* lrcc_fns_truncate: 0 (default) FNS++, the component-averaged
+                              density of the dipole-perturbed first-order amplitudes
+                              (Eq. 45); 1: plain FNS, the ground-state MP2 virtual
+                              density (Eq. 40)                                      */
 } lrcc_options;
 
 /* Fill *opt with the defaults above. */
@@ -123,6 +127,8 @@ lrcc_status lrcc_ccsd_ground(lrcc_ctx* ctx, double e_corr[2], int* iters_T, int*
  * virtual density (Eq. 45), its eigenvectors (natural spinors, Eq. 41), keeps
  * them by |occupation| descending, semicanonicalises (Eq. 42-44), and
  * replaces the context's virtual space, B, mu and eps by the rotated ones.
+ * With opt.fns_density = 1 the density is the ground-state MP2 one of plain
+ * FNS (Eq. 40, 1/2 sum_ijc t_ij^ac conj t_ij^bc) and omega is not used.
  *   by_count       1: keep the first round(value) natural spinors;
  *                  0: keep every one with |n| >= value.
  *   omega          frequency of the perturbed amplitudes.
@@ -141,6 +147,28 @@ lrcc_status lrcc_fns_truncate(lrcc_ctx* ctx, int by_count, double value, double 
  * NULL.  LRCC_ESTATE if no truncation was made on this context.
  */
 lrcc_status lrcc_mp2_correction(const lrcc_ctx* ctx, double e_full[2], double e_trunc[2], double delta[2]);
+
+/*
+ * lrcc_mp2_alpha -- MP2-level polarisability in the context's current virtual
+ * basis, the ingredient of the Delta alpha_MP2 correction (Eq. 53-54): call
+ * it before lrcc_fns_truncate (canonical full space) and after it (truncated
+ * semicanonical space); Delta alpha = alpha_full - alpha_truncated is added to
+ * the truncated LR-CCSD alpha.  The paper names the ingredients (MP2 doubles,
+ * the Eq. 46 first-order amplitudes) but prints no expression; this library
+ * evaluates the sum-over-states response function (Eq. 18) over the singly
+ * and doubly excited determinants mu with the MP2-dressed transition moments
+ * Abar_mu of Eq. 48 (singles: A_ai + sum_me A_me t_im^ae) and the excitation
+ * energies Dbar_mu of Eq. 47 (Hbar of Eq. 49-50):
+ *   alpha_AB(w) = sum_mu conj(Abar_mu) Bbar_mu / (Dbar_mu - w)
+ *                      + Abar_mu conj(Bbar_mu) / (Dbar_mu + w),
+ * unique mu (i<j, a<b).  Needs only lrcc_setup.
+ *   omegas [n_w]                 host, real frequencies; every |w| must lie
+ *                                below the lowest Dbar (else LRCC_EINVAL).
+ *   comps  [n_c]                 host, component indices into mu.
+ *   alpha  [n_w][n_c][n_c] cplx  out, host.
+ */
+lrcc_status lrcc_mp2_alpha(lrcc_ctx* ctx, const double* omegas, int n_w, const int* comps, int n_c,
+                           double* alpha);
 
 /*
  * lrcc_solve -- polarisabilities alpha_AB(omega) = -<<A;B>>_omega (Eq. 35):

@@ -11,6 +11,9 @@
 //  5. natural spinors = eigenvectors of M (Eq. 41); keep by |n| descending
 //  6. Ftilde = Vt^H F_vv Vt, its eigenvectors Z (Eq. 42-43), U = Vt Z (Eq. 44)
 //  7. rotate B^L and mu with diag(1_O, U); virtual energies = eig(Ftilde).
+//
+// Plain FNS (options.fns_density = 1) takes the ground-state MP2 virtual
+// density M_ab = 1/2 sum_ijc t_ij^ac conj t_ij^bc (Eq. 40) in place of 3-4.
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -127,6 +130,38 @@ static void one_body_program(lrcc_ctx* c, int k, CCProg& cp) {
     build_ccsd(cp, h, nullptr);
 }
 
+// MP2 doubles t_ij^ab = -<ab||ij> / (e_a + e_b - e_i - e_j) (Eq. 39) as one
+// amplitude set with t1 = 0; eo/ev: device orbital energies
+static Amp mp2_doubles_dev(Dev& D, const Tensor& B, int64_t O, int64_t V, const double* eo, const double* ev) {
+    Amp t = amp_zeros(D, 1, O, V);
+    Tensor vvoo = anti_block(D, B, O, V, O, V, 0, O, 0, O);
+    Amp r = amp_zeros(D, 1, O, V);
+    Tensor r2 = r.t2.index(0);
+    perm_axpby(D, "abij->ijab", mkc(1.0), vvoo, mkc(0.0), r2);
+    std::vector<double> zero(1, 0.0);
+    DevDoubles z0 = dev_doubles(D, zero);
+    precond(D, nullptr, r, t, eo, ev, z0.p);
+    return t;
+}
+
+// Hbar diagonals of Eq. 49-50 (real parts) into the device arrays Hii [O] and
+// Haa [V], and the MP2 energy 1/4 sum <ij||ab> t_ij^ab (Eq. 51) into *e_mp2
+// (host; the copy is complete when this returns)
+static void hbar_diagonals_dev(Dev& D, const Tensor& B, int64_t O, int64_t V, const Amp& t, const double* eo,
+                               const double* ev, double* Hii, double* Haa, cplx* e_mp2) {
+    Tensor oovv = anti_block(D, B, 0, O, 0, O, O, V, O, V);
+    Tensor t2 = t.t2.index(0);
+    Tensor ef = ein_new(D, "ijab,ijab->", mkc(0.25), oovv, false, t2, false);
+    CK(cudaMemcpyAsync(e_mp2, ef.p, sizeof(cplx), cudaMemcpyDeviceToHost, D.st));
+    Tensor si = ein_new(D, "inef,inef->i", mkc(1.0), t2, false, oovv, false);
+    Tensor sa = ein_new(D, "mnfa,mnfa->a", mkc(1.0), t2, false, oovv, false);
+    k_real_axpy<<<grid_n(D, O), 256, 0, D.st>>>(O, eo, 0.5, si.p, Hii);
+    LAUNCH_CHECK(D);
+    k_real_axpy<<<grid_n(D, V), 256, 0, D.st>>>(V, ev, -0.5, sa.p, Haa);
+    LAUNCH_CHECK(D);
+    CK(cudaStreamSynchronize(D.st));
+}
+
 void fns_truncate_impl(lrcc_ctx* c, int by_count, double value, double omega, int* v_kept, double* occ_out) {
     Dev& D = c->D;
     const int64_t O = c->O, V = c->V, L = c->L, N = O + V;
@@ -137,35 +172,19 @@ void fns_truncate_impl(lrcc_ctx* c, int by_count, double value, double omega, in
     std::vector<double> eo(c->eps.begin(), c->eps.begin() + O), ev(c->eps.begin() + O, c->eps.end());
     DevDoubles deo = dev_doubles(D, eo), dev = dev_doubles(D, ev);
 
-    // 1. MP2 doubles: t = -<ab||ij> / (e_a + e_b - e_i - e_j)
-    Amp t = amp_zeros(D, 1, O, V);
-    {
-        Tensor vvoo = anti_block(D, B, O, V, O, V, 0, O, 0, O);
-        Amp r = amp_zeros(D, 1, O, V);
-        Tensor r2 = r.t2.index(0);
-        perm_axpby(D, "abij->ijab", mkc(1.0), vvoo, mkc(0.0), r2);
-        std::vector<double> zero(1, 0.0);
-        DevDoubles z0 = dev_doubles(D, zero);
-        precond(D, nullptr, r, t, deo.p, dev.p, z0.p);
-    }
-    // 2. Hbar diagonals (and the full-space MP2 energy 1/4 sum <ij||ab> t_ij^ab, Eq. 51)
+    // 1. MP2 doubles
+    Amp t = mp2_doubles_dev(D, B, O, V, deo.p, dev.p);
+    // 2. Hbar diagonals (and the full-space MP2 energy, Eq. 51)
     DevDoubles Hii = dev_doubles(D, eo), Haa = dev_doubles(D, ev);
     cplx e_full = mkc(0.0);
-    {
-        Tensor oovv = anti_block(D, B, 0, O, 0, O, O, V, O, V);
-        Tensor t2 = t.t2.index(0);
-        Tensor ef = ein_new(D, "ijab,ijab->", mkc(0.25), oovv, false, t2, false);
-        CK(cudaMemcpyAsync(&e_full, ef.p, sizeof(cplx), cudaMemcpyDeviceToHost, D.st));
-        Tensor si = ein_new(D, "inef,inef->i", mkc(1.0), t2, false, oovv, false);
-        Tensor sa = ein_new(D, "mnfa,mnfa->a", mkc(1.0), t2, false, oovv, false);
-        k_real_axpy<<<grid_n(D, O), 256, 0, D.st>>>(O, deo.p, 0.5, si.p, Hii.p);
-        LAUNCH_CHECK(D);
-        k_real_axpy<<<grid_n(D, V), 256, 0, D.st>>>(V, dev.p, -0.5, sa.p, Haa.p);
-        LAUNCH_CHECK(D);
-    }
+    hbar_diagonals_dev(D, B, O, V, t, deo.p, dev.p, Hii.p, Haa.p, &e_full);
     // 3-4. first-order amplitudes per component and the averaged density
+    // (plain FNS: the MP2 density of the doubles of step 1)
     Tensor M = zeros(D, {V, V});
-    {
+    if (c->opt.fns_density == 1) {
+        Tensor t2 = t.t2.index(0);
+        ein(D, "ijac,ijbc->ab", mkc(0.5), t2, false, t2, true, mkc(1.0), M);
+    } else {
         std::vector<double> sh(1, omega * (c->opt.plus_omega ? 1.0 : -1.0));
         DevDoubles dsh = dev_doubles(D, sh);
         for (int k = 0; k < c->ncomp; ++k) {
@@ -281,6 +300,91 @@ void fns_truncate_impl(lrcc_ctx* c, int by_count, double value, double omega, in
     if (v_kept) *v_kept = (int)Vk;
     (void)L;
     (void)N;
+}
+
+// MP2-level polarisability in the context's current virtual basis (the
+// ingredient of Delta alpha_MP2, Eq. 53-54): the sum over the singly and doubly
+// excited determinants mu of the response function of Eq. 18 with the Eq. 48
+// transition moments Abar_mu (one-body residual at T1 = 0, T2 = MP2) and the
+// Eq. 47 excitation energies Dbar_mu:
+//   alpha_AB(w) = P_AB(w) + conj P_AB(-w),
+//   P_AB(w) = sum_mu conj(Abar_mu) Bbar_mu / (Dbar_mu - w)      (unique mu)
+static void mp2_alpha_impl(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int n_c, double* alpha) {
+    Dev& D = c->D;
+    const int64_t O = c->O, V = c->V;
+    REQUIRE(omegas && comps && alpha && n_w >= 1 && n_c >= 1, "mp2_alpha: null array or empty list");
+    for (int k = 0; k < n_c; ++k) REQUIRE(comps[k] >= 0 && comps[k] < c->ncomp, "mp2_alpha: component out of range");
+    for (int w = 0; w < n_w; ++w) REQUIRE(std::isfinite(omegas[w]), "mp2_alpha: frequency not finite");
+    std::vector<double> eo(c->eps.begin(), c->eps.begin() + O), ev(c->eps.begin() + O, c->eps.end());
+    DevDoubles deo = dev_doubles(D, eo), dev = dev_doubles(D, ev);
+    Amp t = mp2_doubles_dev(D, c->B, O, V, deo.p, dev.p);
+    DevDoubles Hii = dev_doubles(D, eo), Haa = dev_doubles(D, ev);
+    cplx e_mp2 = mkc(0.0);
+    hbar_diagonals_dev(D, c->B, O, V, t, deo.p, dev.p, Hii.p, Haa.p, &e_mp2);
+    // every |w| must stay below the lowest Dbar (singles: min Haa - max Hii;
+    // doubles: the two lowest Haa minus the two highest Hii)
+    {
+        std::vector<double> hi(O), ha(V);
+        CK(cudaMemcpyAsync(hi.data(), Hii.p, sizeof(double) * O, cudaMemcpyDeviceToHost, D.st));
+        CK(cudaMemcpyAsync(ha.data(), Haa.p, sizeof(double) * V, cudaMemcpyDeviceToHost, D.st));
+        CK(cudaStreamSynchronize(D.st));
+        std::sort(hi.begin(), hi.end());
+        std::sort(ha.begin(), ha.end());
+        double d1 = ha[0] - hi[O - 1], d2 = ha[0] + ha[1] - hi[O - 1] - hi[O - 2];
+        double lo = std::min(d1, d2);
+        for (int w = 0; w < n_w; ++w)
+            REQUIRE(std::fabs(omegas[w]) < lo, "mp2_alpha: |omega| must lie below the lowest Hbar excitation energy");
+    }
+    std::vector<Amp> mom(n_c);
+    for (int k = 0; k < n_c; ++k) {
+        CCProg cp;
+        one_body_program(c, comps[k], cp);
+        cp.P.eval(D, {t.t1.index(0), t.t2.index(0)}, LRCC_FP64);
+        Amp abar{cp.P.val[cp.R1].reshape({1, O, V}), cp.P.val[cp.R2].reshape({1, O, O, V, V})};
+        mom[k] = amp_copy(D, abar);
+    }
+    // P[w][sign][A][B], sign 0: +w, 1: -w
+    std::vector<cplx> P((size_t)n_w * 2 * n_c * n_c);
+    Amp tp = amp_empty(D, 1, O, V);
+    for (int w = 0; w < n_w; ++w)
+        for (int sg = 0; sg < 2; ++sg) {
+            std::vector<double> shv(1, sg ? omegas[w] : -omegas[w]);
+            DevDoubles sh = dev_doubles(D, shv);
+            for (int b = 0; b < n_c; ++b) {
+                precond(D, nullptr, mom[b], tp, Hii.p, Haa.p, sh.p);   // tp = -Bbar / (Dbar -/+ w)
+                for (int a = 0; a < n_c; ++a) {
+                    Tensor d = amp_dot(D, mom[a], true, tp);
+                    cplx v = mkc(0.0);
+                    CK(cudaMemcpyAsync(&v, d.p, sizeof(cplx), cudaMemcpyDeviceToHost, D.st));
+                    CK(cudaStreamSynchronize(D.st));
+                    P[(((size_t)w * 2 + sg) * n_c + a) * n_c + b] = make_double2(-v.x, -v.y);
+                }
+            }
+        }
+    for (int w = 0; w < n_w; ++w)
+        for (int a = 0; a < n_c; ++a)
+            for (int b = 0; b < n_c; ++b) {
+                const cplx p = P[(((size_t)w * 2 + 0) * n_c + a) * n_c + b];
+                const cplx m = P[(((size_t)w * 2 + 1) * n_c + a) * n_c + b];
+                double* out = alpha + 2 * (((size_t)w * n_c + a) * n_c + b);
+                out[0] = p.x + m.x;
+                out[1] = p.y - m.y;
+            }
+}
+
+extern "C" lrcc_status lrcc_mp2_alpha(lrcc_ctx* c, const double* omegas, int n_w, const int* comps, int n_c,
+                                      double* alpha) {
+    if (!c) return LRCC_EINVAL;
+    try {
+        mp2_alpha_impl(c, omegas, n_w, comps, n_c, alpha);
+        return LRCC_OK;
+    } catch (const LrccError& e) {
+        c->err = e.what();
+        return e.st;
+    } catch (const std::exception& e) {
+        c->err = e.what();
+        return LRCC_ECUDA;
+    }
 }
 
 extern "C" lrcc_status lrcc_fns_truncate(lrcc_ctx* c, int by_count, double value, double omega, int* v_kept,

@@ -616,6 +616,7 @@ void lrcc_default_options(lrcc_options* o) {
     o->slab_rows = 0;
     o->pm_omega = 0;
     o->fp64_products = 1;
+    o->fns_density = 0;
 }
 
 const char* lrcc_last_error(const lrcc_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
@@ -658,6 +659,7 @@ lrcc_status lrcc_setup(const double* eps, const double* B, int L, const double* 
         else lrcc_default_options(&c->opt);
         REQUIRE(c->opt.prec >= LRCC_FP64 && c->opt.prec <= LRCC_FP64_EMULATED, "bad precision mode");
         REQUIRE(c->opt.max_iter >= 1 && c->opt.diis_size >= 2 && c->opt.rhs_chunk >= 1, "bad solver options");
+        REQUIRE(c->opt.fns_density == 0 || c->opt.fns_density == 1, "fns_density must be 0 (FNS++) or 1 (MP2)");
         int dev = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&c->D.sm_count, cudaDevAttrMultiProcessorCount, dev));

@@ -28,7 +28,7 @@ class lrcc_options(ctypes.Structure):
     _fields_ = [("r_tol", ctypes.c_double), ("x_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_size", ctypes.c_int), ("rhs_chunk", ctypes.c_int), ("prec", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("plus_omega", ctypes.c_int), ("slab_rows", ctypes.c_int),
-                ("pm_omega", ctypes.c_int), ("fp64_products", ctypes.c_int)]
+                ("pm_omega", ctypes.c_int), ("fp64_products", ctypes.c_int), ("fns_density", ctypes.c_int)]
 
 
 class LrccError(RuntimeError):
@@ -64,6 +64,7 @@ SIGNATURES = [
     ("lrcc_profile_dump", ctypes.c_int, [_vp, ctypes.c_char_p]),
     ("lrcc_get_amplitudes", ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     ("lrcc_mp2_correction", ctypes.c_int, [_vp, _dp, _dp, _dp]),
+    ("lrcc_mp2_alpha", ctypes.c_int, [_vp, _dp, ctypes.c_int, _ip, ctypes.c_int, _dp]),
     ("lrcc_ladder_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                            ctypes.c_int, _vp]),
     ("lrcc_solve_counts", ctypes.c_int, [_vp, _ip, _ip]),
@@ -169,6 +170,16 @@ def lrcc_mp2_correction(ctx: Context):
     a, b, d = np.zeros(2), np.zeros(2), np.zeros(2)
     ctx.check(library().lrcc_mp2_correction(ctx.h, _cd(a), _cd(b), _cd(d)))
     return complex(*a), complex(*b), complex(*d)
+
+
+def lrcc_mp2_alpha(ctx: Context, omegas, comps) -> np.ndarray:
+    """MP2-level alpha [n_w, n_c, n_c] in the context's current basis (Eq. 53-54 ingredient)."""
+    om = np.ascontiguousarray(np.asarray(omegas, dtype=np.float64).reshape(-1))
+    cp = np.ascontiguousarray(np.asarray(comps, dtype=np.int32).reshape(-1))
+    alpha = np.zeros((om.size, cp.size, cp.size), dtype=np.complex128)
+    ctx.check(library().lrcc_mp2_alpha(ctx.h, _cd(om), om.size, cp.ctypes.data_as(_ip), cp.size,
+                                       _cd(alpha.view(np.float64))))
+    return alpha
 
 
 def pack_amplitudes(t1, t2) -> np.ndarray:

@@ -79,6 +79,18 @@ def test_setup_rejects_bad_ordering_and_sizes(lib):
     assert e.value.status == lib.LRCC_EINVAL
 
 
+def test_setup_rejects_bad_options(lib):
+    """Option validation happens before any device call."""
+    s = _system()
+    for field, bad in (("fns_density", 2), ("prec", 7), ("diis_size", 1)):
+        o = lib.lrcc_default_options()
+        setattr(o, field, bad)
+        with pytest.raises(lib.LrccError) as e:
+            lib.lrcc_setup(s["eps"], s["B"], s["mu"], s["O"], s["V"], o)
+        assert e.value.status == lib.LRCC_EINVAL, field
+    assert lib.lrcc_default_options().fns_density == 0
+
+
 def test_pack_roundtrip(lib):
     rng = np.random.default_rng(0)
     t1 = rng.standard_normal((2, 3, 4)) + 0j
