@@ -214,7 +214,8 @@ int solve_loop(lrcc_ctx* c, Amp& x, F&& resid, const std::vector<double>& shift,
         Amp r = resid(x);
         max_abs_amp(D, r, rn);
         double m = *std::max_element(rn.begin(), rn.end());
-        if (getenv("LRCC_VERBOSE"))
+        static const bool verbose = getenv("LRCC_VERBOSE") != nullptr;
+        if (verbose)
             fprintf(stderr, "  iter %3d  R=%lld  max|r| = %.3e%s\n", it, (long long)R, m, throw_on_max ? "" : "  (tc)");
         if (!std::isfinite(m) || m > 1e250) {
             check_device_error(D);
