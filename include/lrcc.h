@@ -331,6 +331,38 @@ lrcc_status lrcc_kernel_stats(lrcc_ctx* ctx, int idx, const char** name, int64_t
 lrcc_status lrcc_ladder_noalloc(const double* bvv_dev, int L, int O, int V, int R, const double* x_dev,
                                 double* z_dev, int transpose, void* stream);
 
+/*
+ * Host-only planning queries (no device calls): the layout rules of the
+ * tensor-core operands and of the per-call <ab||ef> assembly, exposed so that
+ * they can be checked without a GPU.
+ *
+ * lrcc_embed_layout -- layout of one embedded operand of the tcgen05 GEMM:
+ * rows of slots * K real values (slots = 6 for LRCC_MIXED_BF16X3, 2 for
+ * LRCC_MIXED_TF32).  With batch 1 and rows longer than 16 KB the rows are
+ * stored as *n_panels equal panels of *panel_width elements
+ * ([panel][row][panel_width], panel_width a multiple of 128 bytes); otherwise
+ * one panel whose width is the row padded to 16 bytes.  LRCC_EINVAL for
+ * another precision or a size < 1.
+ */
+lrcc_status lrcc_embed_layout(int prec, int64_t K, int64_t rows, int64_t batch, int64_t* n_panels,
+                              int64_t* panel_width);
+
+/*
+ * lrcc_plan_slabs -- how the ladder cuts the P_V = V(V-1)/2 rows (a<b) of
+ * <ab||ef> into assembly chunks when it is not cached: chunk c covers the
+ * pairs (a, b) with a0 <= a < a1 and b0 <= b < b1 (b > a), which are rows
+ * [prow0, prow0 + nrows) in pair order.  budget_el bounds the elements of the
+ * chunk's GT[(b,f)][(a,e)] intermediate; row_cap > 0 forces single-a chunks of
+ * at most row_cap rows (options.slab_rows); consecutive chunks are grouped
+ * into contraction GEMMs of at most cap_rows rows (a chunk larger than
+ * cap_rows forms its own group).
+ *   out [max_slabs][7]   host, per chunk: a0, a1, b0, b1, prow0, nrows, group.
+ * Returns the number of chunks (only the first max_slabs are written), or -1
+ * for V < 2, budget_el < 1, row_cap < 0, cap_rows < 1 or a NULL out.
+ */
+int64_t lrcc_plan_slabs(int64_t V, int64_t budget_el, int64_t row_cap, int64_t cap_rows, int64_t* out,
+                        int64_t max_slabs);
+
 #ifdef __cplusplus
 }
 #endif

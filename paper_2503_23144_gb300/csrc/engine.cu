@@ -585,6 +585,26 @@ static std::vector<SlabGroup> group_chunks(const std::vector<Slab>& plan, int64_
     return out;
 }
 
+extern "C" int64_t lrcc_plan_slabs(int64_t V, int64_t budget_el, int64_t row_cap, int64_t cap_rows, int64_t* out,
+                                   int64_t max_slabs) {
+    if (V < 2 || budget_el < 1 || row_cap < 0 || cap_rows < 1 || max_slabs < 0 || (max_slabs > 0 && !out)) return -1;
+    const std::vector<Slab> plan = plan_slabs(V, budget_el, row_cap);
+    const std::vector<SlabGroup> groups = group_chunks(plan, cap_rows);
+    for (size_t g = 0; g < groups.size(); ++g)
+        for (size_t c = groups[g].c0; c < groups[g].c1 && (int64_t)c < max_slabs; ++c) {
+            const Slab& sl = plan[c];
+            int64_t* o = out + 7 * c;
+            o[0] = sl.a0;
+            o[1] = sl.a1;
+            o[2] = sl.b0;
+            o[3] = sl.b1;
+            o[4] = sl.prow0;
+            o[5] = sl.nrows;
+            o[6] = (int64_t)g;
+        }
+    return (int64_t)plan.size();
+}
+
 // rows per contraction group: the most 128-row M tiles that fit in w_bytes of
 // W rows (row_bytes each), among counts whose tile grid (x tiles_n) fills
 // whole waves of the SMs best

@@ -865,6 +865,17 @@ static EL make_el(int kind, int64_t K, int64_t rows_tot, int64_t batch) {
     return L;
 }
 
+extern "C" lrcc_status lrcc_embed_layout(int prec, int64_t K, int64_t rows, int64_t batch, int64_t* n_panels,
+                                         int64_t* panel_width) {
+    if ((prec != LRCC_MIXED_TF32 && prec != LRCC_MIXED_BF16X3) || K < 1 || rows < 1 || batch < 1 || !n_panels ||
+        !panel_width)
+        return LRCC_EINVAL;
+    const EL L = make_el(prec == LRCC_MIXED_BF16X3 ? 0 : 1, K, rows, batch);
+    *n_panels = L.np;
+    *panel_width = L.pw;
+    return LRCC_OK;
+}
+
 size_t tc_embed_bytes(int prec, int64_t rows, int64_t K, int64_t batch, int64_t& rows_e, int64_t& pitch, bool is_b) {
     const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
     const int64_t es = kind == 0 ? 2 : 4;

@@ -65,6 +65,10 @@ SIGNATURES = [
     ("lrcc_get_amplitudes", ctypes.c_int, [_vp, ctypes.c_int, _dp]),
     ("lrcc_mp2_correction", ctypes.c_int, [_vp, _dp, _dp, _dp]),
     ("lrcc_mp2_alpha", ctypes.c_int, [_vp, _dp, ctypes.c_int, _ip, ctypes.c_int, _dp]),
+    ("lrcc_embed_layout", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    ("lrcc_plan_slabs", ctypes.c_int64, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int64]),
     ("lrcc_ladder_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                            ctypes.c_int, _vp]),
     ("lrcc_solve_counts", ctypes.c_int, [_vp, _ip, _ip]),
@@ -180,6 +184,28 @@ def lrcc_mp2_alpha(ctx: Context, omegas, comps) -> np.ndarray:
     ctx.check(library().lrcc_mp2_alpha(ctx.h, _cd(om), om.size, cp.ctypes.data_as(_ip), cp.size,
                                        _cd(alpha.view(np.float64))))
     return alpha
+
+
+def lrcc_embed_layout(prec: int, K: int, rows: int, batch: int = 1):
+    """(panels, panel width in elements) of an embedded tensor-core operand (host only)."""
+    n, w = ctypes.c_int64(0), ctypes.c_int64(0)
+    st = library().lrcc_embed_layout(int(prec), int(K), int(rows), int(batch), ctypes.byref(n), ctypes.byref(w))
+    if st != LRCC_OK:
+        raise LrccError(st, "lrcc_embed_layout: bad arguments")
+    return n.value, w.value
+
+
+def lrcc_plan_slabs(V: int, budget_el: int, row_cap: int, cap_rows: int) -> np.ndarray:
+    """Assembly chunks of the uncached ladder, [n, 7] int64 rows
+    (a0, a1, b0, b1, prow0, nrows, group) (host only)."""
+    lib = library()
+    n = lib.lrcc_plan_slabs(int(V), int(budget_el), int(row_cap), int(cap_rows), None, 0)
+    if n < 0:
+        raise LrccError(LRCC_EINVAL, "lrcc_plan_slabs: bad arguments")
+    out = np.zeros((max(n, 1), 7), dtype=np.int64)
+    lib.lrcc_plan_slabs(int(V), int(budget_el), int(row_cap), int(cap_rows),
+                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n)
+    return out[:n]
 
 
 def pack_amplitudes(t1, t2) -> np.ndarray:
