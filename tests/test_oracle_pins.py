@@ -442,3 +442,75 @@ def test_mp2_polarizability_noninteracting_limit_and_untruncated_basis():
         assert np.abs(fns.mp2_polarizability(new, comps, oms) - full).max() < 1e-12 * np.abs(full).max()
         new, _, _ = fns.truncate(s2, True, 3, density=density)
         assert np.abs(fns.mp2_polarizability(new, comps, oms) - full).max() > 1e-6 * np.abs(full).max()
+
+
+def _mutated_fns(old, new):
+    """oracle.fns with one source edit (a planted mistake), as a fresh module namespace."""
+    import inspect
+    src = inspect.getsource(fns)
+    assert src.count(old) == 1, old
+    ns = {"__name__": "fns_planted"}
+    exec(compile(src.replace(old, new), "fns_planted", "exec"), ns)
+    return ns
+
+
+@pytest.mark.parametrize("old,new", [
+    ("np.einsum('ijac,ijbc->ab', t2, t2.conj())", "np.einsum('ijac,ijbc->ab', t2.conj(), t2)"),    # conj side
+    ("return 0.5 * np.einsum('ijac,ijbc->ab'", "return 1.0 * np.einsum('ijac,ijbc->ab'"),            # lost 1/2
+    ("np.einsum('ijac,ijbc->ab', t2, t2.conj())", "np.einsum('ijca,ijbc->ab', t2, t2.conj())"),    # index
+    ("+ np.einsum('ia,ib->ab', t1p, t1p.conj())", "+ np.einsum('ia,ib->ab', t1p.conj(), t1p)"),    # FNS++ singles
+])
+def test_density_pin_detects_planted_mistakes(old, new, monkeypatch):
+    ns = _mutated_fns(old, new)
+    monkeypatch.setattr(fns, "mp2_density", ns["mp2_density"])
+    monkeypatch.setattr(fns, "fnspp_density", ns["fnspp_density"])
+    with pytest.raises(AssertionError):
+        test_fns_densities_equal_wavefunction_densities(2, 5, 3)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("out[wi, a, b] = s1 + 0.25 * s2", "out[wi, a, b] = s1 + 0.5 * s2"),                 # doubles weight
+    ("np.sum(a1.conj() * b1 / (D1 - w)", "np.sum(a1 * b1.conj() / (D1 - w)"),            # conjugate side
+    ("a2 * b2.conj() / (D2 + w))", "a2 * b2.conj() / (D2 - w))"),                         # sign of omega
+    ("D1 = Haa[None, :] - Hii[:, None]", "D1 = Haa[None, :] + 0 * Hii[:, None]"),         # dropped Hbar_ii
+])
+def test_mp2_alpha_pin_detects_planted_mistakes(old, new, monkeypatch):
+    ns = _mutated_fns(old, new)
+    monkeypatch.setattr(fns, "mp2_polarizability", ns["mp2_polarizability"])
+    with pytest.raises(AssertionError):
+        test_mp2_polarizability_is_determinant_sum_over_states()
+
+
+def test_hbar_diagonals_are_one_hole_and_one_particle_energies():
+    """Eq. 49-50 from the wave function: with T = T2(MP2) and
+    Hbar = e^-T H e^T built in the determinant spaces of N-1 and N+1
+    electrons, Hbar_ii = -(<Phi_i|Hbar|Phi_i> - <Phi_0|Hbar|Phi_0>) for
+    Phi_i = a_i Phi_0 and Hbar_aa = <Phi^a|Hbar|Phi^a> - <Phi_0|Hbar|Phi_0> for
+    Phi^a = a_a^+ Phi_0 (real parts)."""
+    O, V = 3, 4
+    N = O + V
+    s = synth.make_system(O, V, 6, seed=23)
+    t2 = fns.mp2_doubles(s["eps"], s["B"], O)
+    Hii, Haa = fns.hbar_diagonals(s["eps"], s["B"], O, t2)
+    gA = fci.full_antisym(s["B"])
+    h = fci.core_hamiltonian(ccsd.fock_of(s), gA, O)
+
+    def hbar_diag(nel, det):
+        dets, index = fci.determinants(N, nel)
+        H = fci.hamiltonian_matrix(h, gA, dets, index)
+        T = fci.cluster_matrix(np.zeros((O, V)), t2, O, dets, index)
+        v = np.zeros(len(dets), dtype=np.complex128)
+        v[index[det]] = 1.0
+        ev, term = v.copy(), v.copy()
+        for k in range(1, 4):                  # e^T v (T is nilpotent)
+            term = T @ term / k
+            ev = ev + term
+        return (v.conj() @ H @ ev).real        # <v| e^-T = <v| (T only excites)
+
+    ref = (1 << O) - 1
+    e0 = hbar_diag(O, ref)
+    hi = np.array([-(hbar_diag(O - 1, ref ^ (1 << i)) - e0) for i in range(O)])
+    ha = np.array([hbar_diag(O + 1, ref | (1 << (O + a))) - e0 for a in range(V)])
+    assert np.abs(Hii - s["eps"][:O]).max() > 1e-3     # the correlation shift is not negligible
+    assert np.abs(hi - Hii).max() < 1e-12 * np.abs(Hii).max()
+    assert np.abs(ha - Haa).max() < 1e-12 * np.abs(Haa).max()
