@@ -186,6 +186,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--prec", default="bf16x3", choices=list(PREC_NAMES))
+    ap.add_argument("--solver", default="diis", choices=["diis", "subspace"],
+                    help="response/Lambda solver: per right-hand-side DIIS or one shared subspace "
+                         "(FP64-class precisions only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--fns", action="store_true",
@@ -216,6 +219,7 @@ def main():
     s = synth.make_system(O, V, Lx, cfg["seed"])
     opt = L.lrcc_default_options()
     opt.prec = prec
+    opt.solver = 1 if args.solver == "subspace" else 0
     ctx = L.lrcc_setup(s["eps"], s["B"], s["mu"], O, V, opt)
     if args.ladder_only:
         return ladder_only(args, L, ctx, O, V, Lx, R, prec, world, rank, local, pg)
@@ -317,7 +321,7 @@ def main():
             dt = float(t.item())
         n64, nmix = L.lrcc_solve_counts(ctx)
         solves = {"value": world * R / dt, "unit": "alpha(omega)/s", "seconds": dt, "rhs": R,
-                  "max_residual": float(err.max()), "precision": args.prec,
+                  "max_residual": float(err.max()), "precision": args.prec, "solver": args.solver,
                   "alpha_zz_0": float(alpha[0, -1, -1].real), "fp64_maps": n64, "mixed_maps": nmix,
                   "phase_ms": [round(x, 1) for x in L.lrcc_phase_times(ctx)]}
 

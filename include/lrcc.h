@@ -81,6 +81,15 @@ typedef struct {
                               density of the dipole-perturbed first-order amplitudes
                               (Eq. 45); 1: plain FNS, the ground-state MP2 virtual
                               density (Eq. 40)                                      */
+    int solver;            /* response and Lambda equations: 0 (default) preconditioned
+                              DIIS per right-hand side; 1: one shared subspace for every
+                              right-hand side of a batch (Galerkin projections; each
+                              product M v serves all frequencies and components).
+                              1 needs prec LRCC_FP64 or LRCC_FP64_EMULATED          */
+    int subspace_max;      /* solver 1: vectors kept before a restart from the current
+                              solutions; 0 (default) automatic (8 per right-hand side,
+                              48..400, within 30 % of free device memory); a value below
+                              2 x the right-hand sides of a batch gives LRCC_EINVAL  */
 } lrcc_options;
 
 /* Fill *opt with the defaults above. */

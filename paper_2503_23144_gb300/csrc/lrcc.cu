@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <cstdio>
 #include <cstdlib>
 #include <limits>
@@ -341,6 +342,13 @@ void response_solve(lrcc_ctx* c, Amp& z, const Amp& b, const std::vector<double>
     Dev& D = c->D;
     int64_t R = b.t1.d[0];
     int O = c->O, V = c->V;
+    if (c->opt.solver == 1) {
+        // one subspace for every right-hand side of the batch (FP64-class products only)
+        std::function<Amp(const Amp&)> ap = [&](const Amp& v) { return apply(v, p64(c)); };
+        subspace_solve(D, O, V, c->eo, c->ev, z, b, shift_dev, shift, ap, p64(c), c->opt.x_tol, c->opt.max_iter,
+                       c->opt.subspace_max, final_res, n64);
+        return;
+    }
     precond(D, nullptr, b, z, c->eo, c->ev, shift_dev);
     auto res64 = [&](const Amp& x) {
         Amp s = apply(x, p64(c));
@@ -618,6 +626,8 @@ void lrcc_default_options(lrcc_options* o) {
     o->pm_omega = 0;
     o->fp64_products = 1;
     o->fns_density = 0;
+    o->solver = 0;
+    o->subspace_max = 0;
 }
 
 const char* lrcc_last_error(const lrcc_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
@@ -661,6 +671,10 @@ lrcc_status lrcc_setup(const double* eps, const double* B, int L, const double* 
         REQUIRE(c->opt.prec >= LRCC_FP64 && c->opt.prec <= LRCC_FP64_EMULATED, "bad precision mode");
         REQUIRE(c->opt.max_iter >= 1 && c->opt.diis_size >= 2 && c->opt.rhs_chunk >= 1, "bad solver options");
         REQUIRE(c->opt.fns_density == 0 || c->opt.fns_density == 1, "fns_density must be 0 (FNS++) or 1 (MP2)");
+        REQUIRE(c->opt.solver == 0 || c->opt.solver == 1, "solver must be 0 (DIIS) or 1 (shared subspace)");
+        REQUIRE(c->opt.solver == 0 || !is_mixed(c->opt.prec),
+                "the shared-subspace solver needs FP64-class products (LRCC_FP64 or LRCC_FP64_EMULATED)");
+        REQUIRE(c->opt.subspace_max >= 0, "subspace_max must be >= 0");
         int dev = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&c->D.sm_count, cudaDevAttrMultiProcessorCount, dev));

@@ -1,5 +1,7 @@
 // Amplitude vectors and solver building blocks.
 #pragma once
+#include <functional>
+
 #include "prog.h"
 
 // amplitudes of R right-hand sides: singles [R][O][V], full antisymmetric
@@ -27,6 +29,19 @@ Amp amp_rows(const Amp& a, int64_t r0, int64_t n);
 // 4-fold antisymmetriser over the (i,j) and (a,b) pairs
 Tensor antisym4(Dev& D, const Tensor& x);
 void max_abs_amp(Dev& D, const Amp& r, std::vector<double>& out);
+
+// Shared-subspace solve of (M + shift_r) z_r = -b_r for all R right-hand sides
+// at once (one orthonormal subspace, Galerkin projections, the products M v
+// shared by every shift); apply(v) = M v on a batch of vectors; prec
+// (LRCC_FP64 or LRCC_FP64_EMULATED) for the projections.  Counts the batched
+// products in n_products.
+void subspace_solve(Dev& D, int O, int V, const double* eo, const double* ev, Amp& z, const Amp& b,
+                    const double* shift_dev, const std::vector<double>& shift,
+                    const std::function<Amp(const Amp&)>& apply, int prec, double tol, int max_iter,
+                    int requested_max, std::vector<double>& final_res, int& n_products);
+// vectors the shared subspace holds for R right-hand sides: requested (> 0) or
+// automatic (8 R within 48..400), at most what fits in 30 % of device memory
+int64_t subspace_capacity(Dev& D, int O, int V, int64_t R, int requested);
 
 // Pulay DIIS over R independent right-hand sides; Gram matrices, the small
 // linear solves and the extrapolation all run on the device.

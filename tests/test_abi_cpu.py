@@ -82,13 +82,16 @@ def test_setup_rejects_bad_ordering_and_sizes(lib):
 def test_setup_rejects_bad_options(lib):
     """Option validation happens before any device call."""
     s = _system()
-    for field, bad in (("fns_density", 2), ("prec", 7), ("diis_size", 1)):
+    for fields in ({"fns_density": 2}, {"prec": 7}, {"diis_size": 1}, {"solver": 2}, {"subspace_max": -1},
+                   {"solver": 1, "prec": lib.LRCC_MIXED_BF16X3}):
         o = lib.lrcc_default_options()
-        setattr(o, field, bad)
+        for field, bad in fields.items():
+            setattr(o, field, bad)
         with pytest.raises(lib.LrccError) as e:
             lib.lrcc_setup(s["eps"], s["B"], s["mu"], s["O"], s["V"], o)
-        assert e.value.status == lib.LRCC_EINVAL, field
-    assert lib.lrcc_default_options().fns_density == 0
+        assert e.value.status == lib.LRCC_EINVAL, fields
+    o = lib.lrcc_default_options()
+    assert o.fns_density == 0 and o.solver == 0 and o.subspace_max == 0
 
 
 def test_pack_roundtrip(lib):
