@@ -1,0 +1,49 @@
+"""Full-size parity on the benchmark workload (O=10, V=120, L=240; x, y, z at
+omega = 0, 0.02, 0.05, 0.08: 12 right-hand sides): the correlation energy and
+the 3x3 polarisability tensors from lrcc_solve against the oracle's values in
+tests/golden/c2_alpha.json (written by tests/golden/make_golden.py, which calls
+only the oracle).  FP64-class path (emulated FP64 products on the tensor
+cores) at the FP64 tolerance, the bf16x3 mixed path at 1e-6."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "c2_alpha.json")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2503_23144_gb300 import build, lrcc
+    build.build()
+    assert torch.cuda.is_available()
+    return lrcc
+
+
+@pytest.fixture(scope="module")
+def golden():
+    g = json.load(open(GOLDEN))
+    s = synth.make_system(g["O"], g["V"], g["L"], g["seed"])
+    ref = np.array(g["alpha_re"]) + 1j * np.array(g["alpha_im"])
+    return g, s, ref
+
+
+@pytest.mark.parametrize("prec,tol", [(3, 1e-9), (2, 1e-6)])
+def test_c2_energy_and_alpha_against_oracle(L, golden, prec, tol):
+    g, s, ref = golden
+    o = L.lrcc_default_options()
+    o.prec = prec
+    ctx = L.lrcc_setup(s["eps"], s["B"], s["mu"], s["O"], s["V"], o)
+    e, _, _ = L.lrcc_ccsd_ground(ctx)
+    e_ref = complex(*g["E_corr"])
+    assert abs(e - e_ref) < 1e-9 * abs(e_ref)
+    a, err = L.lrcc_solve(ctx, g["omegas"], g["comps"])
+    assert a.shape == ref.shape
+    assert np.abs(a - ref).max() < tol * np.abs(ref).max()
+    assert err.max() < 1e-8
