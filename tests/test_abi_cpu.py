@@ -101,3 +101,24 @@ def test_pack_roundtrip(lib):
     flat = lib.pack_amplitudes(t1, t2)
     a, b = lib.unpack_amplitudes(flat, 3, 4)
     assert np.array_equal(a, t1) and np.array_equal(b, t2)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built CUDA library every entry point raises ImportError:
+    there is no CPU fallback behind the binding."""
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_2503_23144_gb300 import lrcc\n"
+        "lrcc._LIB_PATH = %r\n"
+        "lrcc._lib = None\n"
+        "try:\n"
+        "    lrcc.lrcc_default_options()\n"
+        "except ImportError as e:\n"
+        "    print('ImportError', e)\n"
+        "    sys.exit(0)\n"
+        "sys.exit(3)\n" % (ROOT, str(tmp_path / "absent" / "_lrcc.so")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "not built" in r.stdout
