@@ -126,3 +126,29 @@ def random_packed(nrow: int, ncol: int, seed: int, block: int = 64) -> np.ndarra
         out[r0:r1].real = rng.standard_normal((r1 - r0, ncol))
         out[r0:r1].imag = rng.standard_normal((r1 - r0, ncol))
     return out
+
+
+def two_fragment_system(fa: dict, fb: dict) -> dict:
+    """Two systems (from make_system) side by side with no interaction: the
+    combined spinors are ordered [occ A, occ B, virt A, virt B]; B^L of A acts
+    only on A's spinors and B^L of B only on B's (L = L_A + L_B), and each
+    dipole component is the sum of the two fragments' blocks.  Every occupied
+    energy of either fragment must lie below every virtual one."""
+    OA, VA, OB, VB = fa["O"], fa["V"], fb["O"], fb["V"]
+    O, V = OA + OB, VA + VB
+    N = O + V
+    ia = np.concatenate([np.arange(OA), O + np.arange(VA)])        # A's spinors in the combined order
+    ib = np.concatenate([OA + np.arange(OB), O + VA + np.arange(VB)])
+    eps = np.empty(N)
+    eps[ia] = fa["eps"]
+    eps[ib] = fb["eps"]
+    if eps[:O].max() >= eps[O:].min():
+        raise ValueError("an occupied energy lies above a virtual one")
+    LA, LB = fa["L"], fb["L"]
+    B = np.zeros((LA + LB, N, N), dtype=np.complex128)
+    B[:LA][:, ia[:, None], ia[None, :]] = fa["B"]
+    B[LA:][:, ib[:, None], ib[None, :]] = fb["B"]
+    mu = np.zeros((3, N, N), dtype=np.complex128)
+    mu[:, ia[:, None], ia[None, :]] += fa["mu"]
+    mu[:, ib[:, None], ib[None, :]] += fb["mu"]
+    return dict(O=O, V=V, L=LA + LB, N=N, seed=(fa["seed"], fb["seed"]), eps=eps, B=B, mu=mu)

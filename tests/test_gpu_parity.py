@@ -151,6 +151,23 @@ def test_two_electron_alpha_equals_sos(L):
     assert np.abs(alpha - sos).max() < 1e-9 * np.abs(sos).max()
 
 
+def test_separable_four_electrons_alpha_equals_sos(L):
+    """Two non-interacting 2-electron fragments (4 electrons in all): E_CCSD
+    and alpha at omega != 0 are exact, for Eq. 35 and Eq. 36."""
+    fa, fb = synth.make_system(2, 4, 6, seed=31), synth.make_system(2, 4, 5, seed=32)
+    s = synth.two_fragment_system(fa, fb)
+    oms = [0.0, 0.03, 0.07]
+    f = ccsd.fock_of(s)
+    Ef, _, _, _, eref = fci.fci_states(f, s["B"], s["O"])
+    sos, _, _ = fci.sos_polarizability(f, s["B"], s["mu"], s["O"], (0, 1, 2), oms)
+    for pm in (0, 1):
+        ctx = _ctx(L, s, r_tol=1e-12, x_tol=1e-11, pm_omega=pm)
+        E, _, _ = L.lrcc_ccsd_ground(ctx)
+        assert abs(E - (Ef[0] - eref)) < 1e-10
+        alpha, _ = L.lrcc_solve(ctx, oms, [0, 1, 2])
+        assert np.abs(alpha - sos).max() < 1e-9 * np.abs(sos).max(), pm
+
+
 def test_rhs_chunking_invariance_and_state(L):
     s = synth.make_system(3, 9, 12, seed=4)
     ctx = _ctx(L, s)

@@ -114,6 +114,34 @@ def test_pm_omega_form_equals_sos_for_two_electrons():
     assert np.abs(a36 - sos).max() < 1e-9 * np.abs(sos).max()
 
 
+def test_separable_four_electrons_exact_at_every_frequency():
+    """Two non-interacting 2-electron fragments: CCSD is exact for each and
+    size-extensive, so for the 4-electron whole E_CCSD = E_FCI and the LR-CCSD
+    alpha (Eq. 35 and Eq. 36 forms) equals the exact sum over states of the
+    whole at every frequency -- an exact answer for more than two electrons at
+    omega != 0."""
+    fa, fb = synth.make_system(2, 4, 6, seed=31), synth.make_system(2, 4, 5, seed=32)
+    s = synth.two_fragment_system(fa, fb)
+    f = ccsd.fock_of(s)
+    model = ccsd.build(s)
+    t, E, _ = ccsd.solve_ccsd(model)
+    lam, _ = ccsd.solve_lambda(model, t)
+    Efci, _, _, _, eref = fci.fci_states(f, s["B"], s["O"])
+    assert abs(complex(E) - (Efci[0] - eref)) < 1e-10
+    oms = [0.0, 0.03, 0.07]
+    comps = (0, 1, 2)
+    sos, _, wmin = fci.sos_polarizability(f, s["B"], s["mu"], s["O"], comps, oms)
+    assert max(oms) < wmin
+    # the construction: the whole's exact alpha is the sum of the fragments'
+    sa, _, _ = fci.sos_polarizability(ccsd.fock_of(fa), fa["B"], fa["mu"], 2, comps, oms)
+    sb, _, _ = fci.sos_polarizability(ccsd.fock_of(fb), fb["B"], fb["mu"], 2, comps, oms)
+    assert np.abs(sos - (sa + sb)).max() < 1e-11 * np.abs(sos).max()
+    a35 = ccsd.polarizability(s, comps, oms, ground=(t, E, lam))
+    a36 = ccsd.polarizability_pm(s, comps, oms, ground=(t, E, lam))
+    assert np.abs(a35 - sos).max() < 1e-9 * np.abs(sos).max()
+    assert np.abs(a36 - sos).max() < 1e-9 * np.abs(sos).max()
+
+
 def test_pm_omega_form_close_to_eq35_for_more_electrons():
     """For more than two electrons the two forms are different approximations;
     at omega = 0 both equal d^2E/dF^2 (the same number), at omega != 0 they
