@@ -116,6 +116,12 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(mine)}
 
 
+def workload_name(workload, cfg):
+    """The workload string both arms report in config.workload."""
+    return (f"{workload}: O={cfg['O']} V={cfg['V']} L={cfg['L']}, R={len(cfg['comps']) * len(cfg['omegas'])} RHS "
+            f"({len(cfg['comps'])} comps x {len(cfg['omegas'])} omegas), sigma + A^T Y per step")
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -152,7 +158,9 @@ def run_reference(args, world, rank):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128 (f64, CPU)", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: O={cfg['O']} V={cfg['V']} L={cfg['L']}, sigma + A^T Y, 1 RHS sample"},
+            "config": {"workload": workload_name(args.workload, cfg),
+                       "flop_count": "2 x 8 R (P_O P_V^2 + O^3 V^3) per step; each timed step here is a sample of "
+                                     "R = 1 right-hand side, the rate is per the same count"},
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                              "sample": "one right-hand side of the workload (the oracle's own sigma and A^T products)"},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -356,8 +364,7 @@ def main():
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[args.prec],
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: O={O} V={V} L={Lx}, R={R} RHS (3 comps x {len(omegas)} omegas), "
-                               f"sigma + A^T Y per step",
+        "config": {"workload": workload_name(args.workload, cfg),
                    "flops_per_step": F_step, "flop_count": "2 x 8 R (P_O P_V^2 + O^3 V^3); <ab||ef> cached, not counted",
                    "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": f"replicas x{world} (RHS sharding, no collective)"},
