@@ -70,10 +70,10 @@ def perturbed_moments(eps, B, mu_c, O, t2):
     A_ai + sum_me A_me t_im^ae).  Returns ([O, V], [O, O, V, V])."""
     A = np.asarray(mu_c)
     Aoo, Aov, Avo, Avv = A[:O, :O], A[:O, O:], A[O:, :O], A[O:, O:]
-    X = np.einsum('ijae,be->ijab', t2, Avv)
-    Yy = np.einsum('imab,mj->ijab', t2, Aoo)
+    X = np.einsum('ijae,be->ijab', t2, Avv, optimize=True)
+    Yy = np.einsum('imab,mj->ijab', t2, Aoo, optimize=True)
     A2 = (X - X.transpose(0, 1, 3, 2)) - (Yy - Yy.transpose(1, 0, 2, 3))
-    A1 = Avo.T + np.einsum('me,imae->ia', Aov, t2)
+    A1 = Avo.T + np.einsum('me,imae->ia', Aov, t2, optimize=True)
     return A1, A2
 
 
@@ -145,6 +145,78 @@ def mp2_polarizability(system, comps, omegas):
                 s2 = np.sum(a2.conj() * b2 / (D2 - w) + a2 * b2.conj() / (D2 + w))
                 out[wi, a, b] = s1 + 0.25 * s2
     return out
+
+
+# --- the same steps from the virtual-occupied factor block alone ------------
+# MP2 (Eq. 39, 51), the Hbar diagonals (Eq. 49-50) and the densities need only
+# <ab||ij> and <ij||ab>, i.e. B^L_ai and B^L_ia = conj(B^L_ai) (B^L Hermitian):
+# these variants take Bvo [L, V, O] so that systems whose full factor does not
+# fit in host memory can be checked.
+
+def vvoo_from_vo(Bvo):
+    """<ab||ij> = sum_L B_ai B_bj - B_aj B_bi  -> [a, b, i, j]."""
+    d = np.einsum('lai,lbj->abij', Bvo, Bvo, optimize=True)
+    return d - d.transpose(0, 1, 3, 2)
+
+
+def oovv_from_vo(Bvo):
+    """<ij||ab> = sum_L B_ia B_jb - B_ib B_ja with B_ia = conj(B_ai)  -> [i, j, a, b]."""
+    Bov = Bvo.conj().transpose(0, 2, 1)
+    d = np.einsum('lia,ljb->ijab', Bov, Bov, optimize=True)
+    return d - d.transpose(0, 1, 3, 2)
+
+
+def mp2_doubles_vo(eps, Bvo, O):
+    eo, ev = eps[:O], eps[O:]
+    D = eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
+    return vvoo_from_vo(Bvo).transpose(2, 3, 0, 1) / D
+
+
+def mp2_energy_vo(eps, Bvo, O):
+    return 0.25 * np.einsum('ijab,ijab->', oovv_from_vo(Bvo), mp2_doubles_vo(eps, Bvo, O))
+
+
+def hbar_diagonals_vo(eps, Bvo, O, t2):
+    oovv = oovv_from_vo(Bvo)
+    Hii = eps[:O] + 0.5 * np.einsum('inef,inef->i', t2, oovv).real
+    Haa = eps[O:] - 0.5 * np.einsum('mnfa,mnfa->a', t2, oovv).real
+    return Hii, Haa
+
+
+def truncation_from_vo(eps, Bvo, mu, O, by_count, value, omega=0.0, plus_omega=False, density="fnspp"):
+    """Steps 1-7 of ``truncate`` and the MP2 energies of Eq. 51 from the
+    virtual-occupied factor block: returns dict(occ = |n| sorted descending,
+    eps_virt = semicanonical energies of the kept space, e_mp2_full,
+    e_mp2_trunc, gap = (|n_k| - |n_k+1|) / |n_k| at the cut)."""
+    eps = np.asarray(eps, dtype=np.float64)
+    N = eps.shape[0]
+    t2 = mp2_doubles_vo(eps, Bvo, O)
+    if density == "fnspp":
+        Hii, Haa = hbar_diagonals_vo(eps, Bvo, O, t2)
+        M = np.zeros((N - O, N - O), dtype=np.complex128)
+        for c in range(3):
+            t1p, t2p = first_order_amplitudes(eps, None, mu[c], O, t2, Hii, Haa, omega, plus_omega)
+            M += 0.5 * np.einsum('ijac,ijbc->ab', t2p, t2p.conj(), optimize=True)
+            M += np.einsum('ia,ib->ab', t1p, t1p.conj())
+            del t1p, t2p
+        M /= 3.0
+    elif density == "mp2":
+        M = 0.5 * np.einsum('ijac,ijbc->ab', t2, t2.conj(), optimize=True)
+    else:
+        raise ValueError("density must be 'fnspp' or 'mp2'")
+    e_full = 0.25 * np.einsum('ijab,ijab->', oovv_from_vo(Bvo), t2)
+    del t2
+    n, Vn = np.linalg.eigh(M)
+    keep = select(n, by_count, value)
+    occ = np.abs(n[np.argsort(-np.abs(n), kind='stable')])
+    k = keep.shape[0]
+    gap = (occ[k - 1] - occ[k]) / occ[k - 1] if k < occ.shape[0] else 1.0
+    Vt = Vn[:, keep]
+    et, Z = np.linalg.eigh(Vt.conj().T @ np.diag(eps[O:]) @ Vt)
+    U = Vt @ Z
+    Bvo_new = np.einsum('ar,lai->lri', U.conj(), Bvo, optimize=True)   # (Uf^H B Uf)[v', o]
+    eps_new = np.concatenate([eps[:O], et])
+    return dict(occ=occ, eps_virt=et, e_mp2_full=e_full, e_mp2_trunc=mp2_energy_vo(eps_new, Bvo_new, O), gap=gap)
 
 
 def select(n: np.ndarray, by_count: bool, value: float) -> np.ndarray:

@@ -91,6 +91,35 @@ def make_system(O: int, V: int, L: int, seed: int, *, with_B: bool = True,
     return dict(O=O, V=V, L=L, N=N, seed=seed, eps=eps, B=B, mu=mu)
 
 
+def make_system_vo(O: int, V: int, L: int, seed: int) -> dict:
+    """The same draws as ``make_system`` (same eps, B and mu), keeping of each
+    factor B^L only its virtual-occupied block B^L[O:, :O] (``Bvo`` [L, V, O]):
+    O V L numbers instead of N^2 L, for systems whose full factor does not fit
+    in host memory.  B^L is Hermitian, so B^L[:O, O:] = conj(Bvo^L)^T."""
+    if O < 1 or V < 1 or L < 1:
+        raise ValueError("O, V, L must be positive")
+    N = O + V
+    rng = np.random.default_rng(seed)
+    eps = np.empty(N)
+    eps[:O] = np.sort(rng.uniform(-3.0, -0.3, size=O))
+    eps[O:] = np.sort(rng.uniform(0.1, 5.0, size=V))
+    s = 0.3 / (1.0 + L / 16.0)
+    inv2 = 1.0 / np.sqrt(2.0)
+    Bvo = np.empty((L, V, O), dtype=np.complex128)
+    for l in range(L):
+        n1 = rng.standard_normal((N, N))
+        n2 = rng.standard_normal((N, N))
+        G = (n1 + 1j * n2) * inv2
+        Bvo[l] = (s * inv2) * (G[O:, :O] + G[:O, O:].conj().T)
+    mu = np.empty((3, N, N), dtype=np.complex128)
+    for c in range(3):
+        n1 = rng.standard_normal((N, N))
+        n2 = rng.standard_normal((N, N))
+        G = 0.5 * (n1 + 1j * n2) * inv2
+        mu[c] = inv2 * (G + G.conj().T)
+    return dict(O=O, V=V, L=L, N=N, seed=seed, eps=eps, Bvo=Bvo, mu=mu)
+
+
 def random_amplitudes(O: int, V: int, R: int, seed: int, scale: float = 0.05) -> dict:
     """Random complex amplitudes for R right-hand sides.
 

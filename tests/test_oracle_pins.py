@@ -542,3 +542,22 @@ def test_hbar_diagonals_are_one_hole_and_one_particle_energies():
     assert np.abs(Hii - s["eps"][:O]).max() > 1e-3     # the correlation shift is not negligible
     assert np.abs(hi - Hii).max() < 1e-12 * np.abs(Hii).max()
     assert np.abs(ha - Haa).max() < 1e-12 * np.abs(Haa).max()
+
+
+@pytest.mark.parametrize("density", ["fnspp", "mp2"])
+def test_truncation_from_vo_block_equals_full_factor(density):
+    """The memory-light variant (only B^L_ai, drawn by synth.make_system_vo)
+    gives the same occupations, semicanonical energies and MP2 energies as the
+    full-factor truncation."""
+    O, V, L, keep = 3, 9, 7, 4
+    s = synth.make_system(O, V, L, seed=27)
+    sv = synth.make_system_vo(O, V, L, seed=27)
+    new, occ, _ = fns.truncate(s, True, keep, omega=0.02, density=density)
+    r = fns.truncation_from_vo(sv["eps"], sv["Bvo"], sv["mu"], O, True, keep, omega=0.02, density=density)
+    assert np.abs(r["occ"] - occ).max() < 1e-13 * occ[0]
+    assert np.abs(r["eps_virt"] - new["eps"][O:]).max() < 1e-13
+    e_full = fns.mp2_energy(s["eps"], s["B"], O)
+    e_tr = fns.mp2_energy(new["eps"], new["B"], O)
+    assert abs(r["e_mp2_full"] - e_full) < 1e-13 * abs(e_full)
+    assert abs(r["e_mp2_trunc"] - e_tr) < 1e-13 * abs(e_full)
+    assert 0.0 < r["gap"] <= 1.0
