@@ -122,3 +122,40 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "not built" in r.stdout
+
+
+C_CLIENT = r"""
+#include "lrcc.h"
+#include <stdio.h>
+int main(void) {
+    lrcc_options o;
+    int64_t np = 0, pw = 0, n;
+    lrcc_status st;
+    lrcc_default_options(&o);
+    st = lrcc_embed_layout(LRCC_MIXED_BF16X3, 7140, 7140, 1, &np, &pw);
+    n = lrcc_plan_slabs(120, 1 << 20, 0, 1024, NULL, 0);
+    printf("%d %d %lld %lld %lld\n", o.max_iter, (int)st, (long long)np, (long long)pw, (long long)n);
+    return (st == LRCC_OK && o.max_iter == 200 && n > 0) ? 0 : 1;
+}
+"""
+
+
+def test_header_is_plain_c99_and_links(lib, tmp_path):
+    """include/lrcc.h compiles as strict C99 (-pedantic -Werror) and a C
+    client links against the library and calls its host-only entry points."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(lib._LIB_PATH)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe), lib._LIB_PATH,
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.split()[:2] == ["200", "0"]
