@@ -553,7 +553,7 @@ static std::vector<Slab> plan_slabs(int64_t V, int64_t budget_el, int64_t row_ca
     return out;
 }
 
-static double free_bytes(Dev& D) {
+double free_bytes(Dev& D) {
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
     return double(fr + D.pool.cached);
@@ -885,6 +885,18 @@ void ladder_pack_x(Dev& D, const cplx* X, cplx* Xp, int64_t R, int64_t O, int64_
 void ladder_antisym_slab(Dev& D, const cplx* G, int64_t ldg, cplx* W, int64_t a0, int64_t nrows, int64_t V) {
     int64_t PV = V * (V - 1) / 2;
     k_antisym_slab<<<grid_n(D, nrows * PV), 256, 0, D.st>>>(G, ldg, W, a0, nrows, V);
+    LAUNCH_CHECK(D);
+}
+
+void ladder_pack_xt(Dev& D, const cplx* X, cplx* Xt, int64_t R, int64_t O, int64_t V) {
+    k_pack_xt<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(X, Xt, R, O, V, FastDiv(O), FastDiv(V));
+    LAUNCH_CHECK(D);
+}
+
+void ladder_unpack_zt(Dev& D, const cplx* Zt, cplx* Z, int64_t R, int64_t O, int64_t V, cplx alpha, cplx beta) {
+    const bool beta0 = beta.x == 0.0 && beta.y == 0.0;
+    k_unpack_zt<<<grid_n(D, R * O * O * V * V), 256, 0, D.st>>>(Zt, Z, R, O, V, FastDiv(O), FastDiv(V), alpha, beta,
+                                                               beta0);
     LAUNCH_CHECK(D);
 }
 

@@ -94,10 +94,14 @@ void build_ham_impl(lrcc_ctx* c) {
     H.vvoo = anti_block(D, B, O, V, O, V, 0, O, 0, O);
     H.ovov = anti_block(D, B, 0, O, O, V, 0, O, O, V);
     H.ovvo = anti_block(D, B, 0, O, O, V, O, V, 0, O);
-    H.ovvv = anti_block(D, B, 0, O, O, V, O, V, O, V);
-    H.vovv = anti_block(D, B, O, V, 0, O, O, V, O, V);
-    H.vvvo = anti_block(D, B, O, V, O, V, O, V, 0, O);
+    // factor blocks for the terms with three virtual indices (no O V^3 block)
     ensure_bvv(c);
+    H.Bvv = c->lad.Bvv;
+    H.Bov = empty(D, {(int64_t)c->L, (int64_t)O, (int64_t)V});
+    axpby(D, mkc(1.0), B.slice(1, 0, O).slice(2, O, V), false, mkc(0.0), H.Bov);
+    H.Bvo = empty(D, {(int64_t)c->L, (int64_t)V, (int64_t)O});
+    axpby(D, mkc(1.0), B.slice(1, O, V).slice(2, 0, O), false, mkc(0.0), H.Bvo);
+    c->lad.Bov = H.Bov;
     c->Hmu.clear();
     for (int k = 0; k < c->ncomp; ++k) {
         Ham h;

@@ -333,6 +333,7 @@ void perm_axpby(Dev& D, const std::string& spec, cplx alpha, const Tensor& x, cp
 // <ab|ef> = sum_L Bvv^L_ae Bvv^L_bf; transpose -> Bvv conjugated.
 struct LadderCtx {
     Tensor Bvv;      // [L][V][V]
+    Tensor Bov;      // [L][O][V] (B^L_me): the occupied-virtual factor of the Q map
     int slab_rows = 0;  // > 0: no <ab||ef> cache; assemble per call in slabs of this many rows
     // cached embedded <ab||ef> matrix W' [P_V][pitch] (rows a<b, K = pairs e<f)
     // for one mixed precision, built on first use when it fits in device memory
@@ -362,6 +363,22 @@ void ladder_packed(Dev& D, LadderCtx& L, const cplx* Xt, cplx* Zt, int64_t ncol,
 // rows (a,b) = pair(prow0 + row), written as A operand rows [nrows][pitch]
 void tc_embed_antisym_slab(Dev& D, int prec, const cplx* GT, int64_t ldt, int64_t a0, int64_t gb0, int64_t prow0,
                            int64_t nrows, int64_t V, int64_t pitch, int64_t rows_tot, void* out);
+
+// Q map of the T1-weighted ladder piece: Q_amij = sum_ef <am||ef> X_ij^ef with
+// <am||ef> = sum_L (Bvv^L_ae Bov^L_mf - Bvv^L_af Bov^L_me), assembled from the
+// factor in slabs over a (never stored as an O V^3 block).  X [R][O][O][V][V]
+// antisymmetric in (i,j); Q [R][V][O][O][O] = alpha * map + beta * Q.
+// Transpose (qmap_t): Xbar_ijef = sum_am Qbar_amij <am||ef> for Qbar
+// antisymmetric in (i,j); Xbar = alpha * map + beta * Xbar.
+void qmap(Dev& D, LadderCtx& L, const Tensor& X, cplx alpha, cplx beta, Tensor& Q, int prec);
+void qmap_t(Dev& D, LadderCtx& L, const Tensor& Qb, cplx alpha, cplx beta, Tensor& Xb, int prec);
+// packed ladder layouts on caller-provided buffers:
+// Xt[r*PO + ij][ef] = 1/2 (X_ijef - X_ijfe) (i<j, e<f), and
+// Z[r][i][j][a][b] = alpha * sign * Zt[r*PO + ij][ab] + beta * Z (antisymmetric fill)
+void ladder_pack_xt(Dev& D, const cplx* X, cplx* Xt, int64_t R, int64_t O, int64_t V);
+void ladder_unpack_zt(Dev& D, const cplx* Zt, cplx* Z, int64_t R, int64_t O, int64_t V, cplx alpha, cplx beta);
+// free device memory plus the pool's cached bytes
+double free_bytes(Dev& D);
 
 // pair index of (p<q) among n, row-major strict upper triangle
 __host__ __device__ inline int64_t pair_index(int64_t p, int64_t q, int64_t n) {
