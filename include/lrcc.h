@@ -221,8 +221,9 @@ typedef enum {
  *            antisymmetric inputs), so every kind is defined for any array.
  *   t        host [O*V + O*O*V*V] complex: the amplitudes T at which
  *            SIGMA / VJP are linearised, or NULL to linearise at the
- *            converged ground state of lrcc_ccsd_ground (its primal values are
- *            reused, as in lrcc_solve; LRCC_ESTATE before the ground state).
+ *            converged ground state of lrcc_ccsd_ground or at the amplitudes
+ *            of the last lrcc_linearize (the primal values kept there are
+ *            reused, as in lrcc_solve; LRCC_ESTATE before either).
  *            Required for XI; ignored for T and ENERGY.
  *   in       host [R][O*V + O*O*V*V] complex.
  *   R        number of right-hand sides (>= 1).
@@ -232,6 +233,21 @@ typedef enum {
  */
 lrcc_status lrcc_residual(lrcc_ctx* ctx, int kind, const double* t, const double* in, int R,
                           int comp, int prec, double* out);
+
+/*
+ * lrcc_linearize -- fixes the amplitudes T at which the Jacobian maps of
+ * Eq. 30 (A = dR/dT, and its transpose) are applied by later lrcc_residual
+ * calls with t == NULL, without solving the ground state: the residual
+ * program is evaluated once at T (in precision `prec`) and its primal values
+ * are kept, exactly as lrcc_ccsd_ground keeps them at the converged T.
+ *   t     host [O*V + O*O*V*V] complex (doubles projected onto their
+ *         antisymmetric part, as in lrcc_residual).
+ *   prec  precision of that evaluation (LRCC_FP64 .. LRCC_FP64_EMULATED).
+ * The ground state (and so lrcc_solve) is invalidated: lrcc_solve returns
+ * LRCC_ESTATE until lrcc_ccsd_ground runs again.  Errors: LRCC_EINVAL (bad
+ * arguments), LRCC_ENOMEM, LRCC_ECUDA.
+ */
+lrcc_status lrcc_linearize(lrcc_ctx* ctx, const double* t, int prec);
 
 /*
  * Device-pointer variants for the PyTorch binding: same semantics, but every
@@ -333,9 +349,14 @@ lrcc_status lrcc_kernel_stats(lrcc_ctx* ctx, int idx, const char** name, int64_t
  * packed amplitudes plus one ladder slab exceed it (2 P_V R P_O complex +
  * one row of <ab|ef> slab, P_n = n(n-1)/2) return LRCC_EINVAL with a message
  * for lrcc_last_error(NULL).  The first call on a device looks up that array's
- * device address (with the device current), so make the first call before
- * any stream capture.  All calls share the array: calls whose kernels overlap
- * on the GPU race on it, so serialise them on one stream.
+ * device address (with the device current); with lazy module loading (the
+ * CUDA default) that lookup also loads this library's device code and commits
+ * the 32 MiB on that device, so make the first call as a warm-up before any
+ * stream capture and outside any region where allocation is forbidden.  The
+ * looked-up address is cached per device for the life of the process: it is
+ * not valid after cudaDeviceReset, so do not call this entry point after a
+ * device reset.  All calls share the array: calls whose kernels overlap on
+ * the GPU race on it, so serialise them on one stream.
  */
 lrcc_status lrcc_ladder_noalloc(const double* bvv_dev, int L, int O, int V, int R, const double* x_dev,
                                 double* z_dev, int transpose, void* stream);

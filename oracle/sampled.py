@@ -10,7 +10,9 @@ whose virtual indices lie in a chosen set Sv.  Every intermediate is restricted
 to the indices those rows read, and every integral block is formed from the
 factor, <pq||rs> = sum_L B^L_pr B^L_qs - B^L_ps B^L_qr (``ccsd.antisym_block``),
 only over those index ranges.  The largest pieces at O=28, V=600 are the full
-<mn||ef> block (4.5 GB) and the slices <ma||fe>, <am||ef> with a in Sv.
+<mn||ef> block (4.5 GB) and the slices <ma||fe>, <am||ef> with a in Sv; the
+sums over <mn||ef> are written as matrix products on fixed layouts of that
+block so that no extra copy of it is made (the sums themselves are unchanged).
 
 The rows of A X (Eq. 30) are the forward derivative of the restricted residual
 along X.  For a left vector lambda that is zero outside the sampled rows, the
@@ -66,6 +68,10 @@ class RowIntegrals:
         self.ooov = block(B, o, o, o, v)         # <mn||ie>
         self.oovo = block(B, o, o, v, o)         # <mn||ej>
         self.oovv = block(B, o, o, v, v)         # <mn||ef>
+        # the same block laid out [m][e][n][f], so that the sums over (n, f)
+        # below are plain matrix products of views (no hidden copies of this
+        # 4.5 GB block are made or kept by the reverse sweep)
+        self.oovv_menf = self.oovv.permute(0, 2, 1, 3).contiguous()
         self.ovov_vo = block(B, o, pv, po, v)    # <na||if>, a in Sv, i in So
         self.ovvo_vo = block(B, o, pv, v, po)    # <mb||ej>, b in Sv, j in So
         self.ovvv_v = block(B, o, pv, v, v)      # <ma||fe>, a in Sv
@@ -86,13 +92,21 @@ def residual_rows(t1, t2, H: RowIntegrals):
     tau_oo = t2o[:, o] + ein('ia,jb->ijab', t1o, t1o) - ein('ib,ja->ijab', t1o, t1o)
     tau_vv = t2[:, :, v][:, :, :, v] + ein('ia,jb->ijab', t1v, t1v) - ein('ib,ja->ijab', t1v, t1v)
 
+    O, V, no, nv = H.O, H.V, len(o), len(v)
+    W_mn_ef = H.oovv.reshape(O * O, V * V)          # <mn||ef> as [(m,n)][(e,f)]
+    W_me_nf = H.oovv_menf.reshape(O * V, O * V)     # <mn||ef> as [(m,e)][(n,f)]
+
     # one-body intermediates: F_ae for a in Sv, F_mi and F_me in full
     Fae = H.fvv[v] - 0.5 * ein('me,ma->ae', H.fov, t1v)
     Fmi = H.foo + 0.5 * ein('ie,me->mi', t1, H.fov)
     Fme = H.fov.clone()
-    Fae = Fae + ein('mf,mafe->ae', t1, H.ovvv_v) - 0.5 * ein('mnaf,mnef->ae', tau_t[:, :, v], H.oovv)
-    Fmi = Fmi + ein('ne,mnie->mi', t1, H.ooov) + 0.5 * ein('inef,mnef->mi', tau_t, H.oovv)
-    Fme = Fme + ein('nf,mnef->me', t1, H.oovv)
+    # sum_mnf tau~_mn^af <mn||ef>: for each m, [e][(n,f)] x [(n,f)][a], summed over m
+    tt_v = tau_t[:, :, v].permute(0, 1, 3, 2).reshape(O, O * V, nv)            # [m][(n,f)][a]
+    Fae = Fae + ein('mf,mafe->ae', t1, H.ovvv_v) - 0.5 * torch.bmm(H.oovv_menf.reshape(O, V, O * V), tt_v).sum(0).T
+    # sum_nef tau~_in^ef <mn||ef>: [i][(n,e,f)] x [(n,e,f)][m]
+    Fmi = Fmi + ein('ne,mnie->mi', t1, H.ooov) + 0.5 * (tau_t.reshape(O, O * V * V)
+                                                       @ H.oovv.reshape(O, O * V * V).T).T
+    Fme = Fme + (W_me_nf @ t1.reshape(O * V)).reshape(O, V)                   # sum_nf t_n^f <mn||ef>
 
     # singles rows
     R1 = H.fvo[v][:, o].T.clone()
@@ -109,11 +123,18 @@ def residual_rows(t1, t2, H: RowIntegrals):
     R2 = _Pab(ein('ijae,be->ijab', t2oov, Fbe_t)) - _Pij(ein('imab,mj->ijab', t2ovv, Fmj_t))
     R2 = R2 + H.vvoo_vvoo.permute(2, 3, 0, 1)
     X = ein('je,mnie->mnij', t1o, H.ooov[:, :, o])
-    Wmnij = H.oooo[:, :, o][:, :, :, o] + X - X.transpose(2, 3) + 0.25 * ein('ijef,mnef->mnij', tau_oo, H.oovv)
+    # sum_ef tau_ij^ef <mn||ef>: [(i,j)][(e,f)] x [(e,f)][(m,n)]
+    P_ijmn = (tau_oo.reshape(no * no, V * V) @ W_mn_ef.T).reshape(no, no, O, O)
+    Wmnij = H.oooo[:, :, o][:, :, :, o] + X - X.transpose(2, 3) + 0.25 * P_ijmn.permute(2, 3, 0, 1)
     Y = ein('mb,amef->abef', t1v, H.vovv_v)
-    Wabef = H.vvvv_vv - Y + Y.transpose(0, 1) + 0.25 * ein('mnab,mnef->abef', tau_vv, H.oovv)
+    # sum_mn tau_mn^ab <mn||ef>: [(a,b)][(m,n)] x [(m,n)][(e,f)]
+    T_abef = (tau_vv.reshape(O * O, nv * nv).T @ W_mn_ef).reshape(nv, nv, V, V)
+    Wabef = H.vvvv_vv - Y + Y.transpose(0, 1) + 0.25 * T_abef
+    # sum_nf Z_jn^fb <mn||ef>, Z = t2/2 + t1 t1: [(m,e)][(n,f)] x [(n,f)][(j,b)]
+    Zt = 0.5 * t2o[:, :, :, v] + ein('jf,nb->jnfb', t1o, t1v)                 # [j][n][f][b]
+    ZW = (W_me_nf @ Zt.permute(1, 2, 0, 3).reshape(O * V, no * nv)).reshape(O, V, no, nv)   # [m][e][j][b]
     Wmbej = (H.ovvo_vo + ein('jf,mbef->mbej', t1o, H.ovvv_v) - ein('nb,mnej->mbej', t1v, H.oovo[:, :, :, o])
-             - ein('jnfb,mnef->mbej', 0.5 * t2o[:, :, :, v] + ein('jf,nb->jnfb', t1o, t1v), H.oovv))
+             - ZW.permute(0, 3, 1, 2))
     R2 = R2 + 0.5 * ein('mnab,mnij->ijab', tau_vv, Wmnij)
     R2 = R2 + 0.5 * ein('ijef,abef->ijab', tau_oo, Wabef)
     ring = ein('imae,mbej->ijab', t2o[:, :, v], Wmbej) - ein('ie,ma,mbej->ijab', t1o, t1v, H.ovvo_vo)
@@ -125,7 +146,11 @@ def residual_rows(t1, t2, H: RowIntegrals):
 
 class RowModel:
     """The residual rows So x Sv as a function of the unique-amplitude vector
-    (``ccsd.Layout`` order) and its exact derivatives."""
+    (``ccsd.Layout`` order) and its exact derivatives.  The derivatives are
+    taken with respect to t1 and the full antisymmetric t2 (the expansion of
+    the unique doubles is linear and is applied outside the differentiation):
+    a unique coordinate x_ijab (i<j, a<b) enters t2 at [i,j,a,b] and [j,i,b,a]
+    with +1 and at [j,i,a,b] and [i,j,b,a] with -1."""
 
     def __init__(self, H: RowIntegrals):
         self.H = H
@@ -143,18 +168,32 @@ class RowModel:
              for i, j in zip(self.io.tolist(), self.jo.tolist()) for a, b in zip(self.av.tolist(), self.bv.tolist())]
         return s, d
 
-    def R(self, x):
-        t1, t2 = self.lay.full(x)
+    def _rows_of(self, t1, t2):
         R1, R2 = residual_rows(t1, t2, self.H)
         I, J = self.io[:, None], self.jo[:, None]
         A, B = self.av[None, :], self.bv[None, :]
         return torch.cat([R1.reshape(-1), R2[I, J, A, B].reshape(-1)])
 
+    def R(self, x):
+        with torch.no_grad():
+            t1, t2 = self.lay.full(x)
+            return self._rows_of(t1, t2)
+
     def jvp(self, x, dx):
         """Rows of A dx (Eq. 30)."""
-        return torch.func.jvp(self.R, (x,), (dx,))[1]
+        with torch.no_grad():
+            t1, t2 = self.lay.full(x)
+            d1, d2 = self.lay.full(dx)
+        return torch.func.jvp(self._rows_of, (t1, t2), (d1, d2))[1]
 
     def vjp(self, x, lam_rows):
         """A^T lambda (all unique coordinates) for lambda supported on the rows."""
-        _, f = torch.func.vjp(self.R, x)
-        return f(lam_rows.conj())[0].conj()
+        with torch.no_grad():
+            t1, t2 = self.lay.full(x)
+        _, f = torch.func.vjp(self._rows_of, t1, t2)
+        g1, g2 = f(lam_rows.conj())
+        del f
+        lay = self.lay
+        I, J, A, B = lay._I, lay._J, lay._A, lay._B
+        g2u = g2[I, J, A, B] - g2[J, I, A, B] - g2[I, J, B, A] + g2[J, I, B, A]
+        return lay.join(g1, g2u).conj()

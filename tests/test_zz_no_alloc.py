@@ -43,6 +43,44 @@ def test_noalloc_matches_context_ladder_twice(L):
         assert err < 1e-13 * ref.abs().max().item(), (call, err)
 
 
+def _slab_count(O, V, R):
+    """Slabs of a over which the entry point cuts <ab|ef>, by the rule stated
+    in include/lrcc.h: after the packed X and Z (2 P_V R P_O complex), the
+    32 MiB scratch holds G and W rows of as many a values as fit."""
+    cap = (32 << 20) // 16
+    po, pv = O * (O - 1) // 2, V * (V - 1) // 2
+    per_a = V * (V - 1) * V + (V - 1) * pv
+    na = min(V - 1, (cap - 2 * pv * R * po) // per_a)
+    return -(-(V - 1) // na)
+
+
+def test_noalloc_several_slabs_and_no_allocation(L):
+    """A size that needs several slabs of the scratch array (a0 > 0 offsets into
+    B_vv, W and Z), both directions, against the context ladder; and a second
+    call with the output given changes neither the device's free memory nor
+    PyTorch's allocated bytes."""
+    O, V, Lx, R = 4, 60, 40, 2
+    assert _slab_count(O, V, R) >= 5
+    s = synth.make_system(O, V, Lx, seed=23)
+    ctx = L.lrcc_setup(s["eps"], s["B"], s["mu"], O, V)
+    bvv = torch.as_tensor(np.ascontiguousarray(s["B"][:, O:, O:])).cuda()
+    for seed, transpose in [(3, False), (4, True)]:
+        x = _antisym(R, O, V, seed)
+        ref = L.lrcc_ladder_dev(ctx, x, transpose=transpose)
+        got = L.lrcc_ladder_noalloc(bvv, x, transpose=transpose)
+        torch.cuda.synchronize()
+        err = (got - ref).abs().max().item()
+        assert err < 1e-13 * ref.abs().max().item(), (transpose, err)
+    out = torch.empty_like(x)
+    L.lrcc_ladder_noalloc(bvv, x, out=out)      # warm-up: the first call may load the module
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    L.lrcc_ladder_noalloc(bvv, x, out=out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
 def test_noalloc_rejects_oversized_problem(L):
     """Sizes whose packed amplitudes alone (2 x 19900 x 8 x 435 complex) exceed
     the fixed scratch are refused before any kernel runs or pointer is read."""
