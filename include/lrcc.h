@@ -90,6 +90,10 @@ typedef struct {
                               solutions; 0 (default) automatic (8 per right-hand side,
                               48..400, within 30 % of free device memory); a value below
                               2 x the right-hand sides of a batch gives LRCC_EINVAL  */
+    int embed_budget_mb;   /* tensor-core contractions: bytes (MiB) that the transient split
+                              copies of one GEMM's two operands may take; a larger GEMM runs
+                              as sub-GEMMs over halves of N, M or K.  0 (default) automatic:
+                              min(6 GiB, 10 % of free device memory)                 */
 } lrcc_options;
 
 /* Fill *opt with the defaults above. */

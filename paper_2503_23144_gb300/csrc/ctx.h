@@ -17,6 +17,7 @@ struct lrcc_ctx {
     std::vector<std::unique_ptr<CCProg>> ccmu;  // one-body programs (xi, eta)
     std::unique_ptr<CCProg> ccfx;        // scratch program for the F.X stencil
     bool ground = false;
+    bool linearized = false;               // cc holds the primal values at a fixed T (ground state or lrcc_linearize)
     bool truncated = false;                // lrcc_fns_truncate ran
     cplx e_mp2_full = {0, 0}, e_mp2_trunc = {0, 0};  // Eq. 51 pieces
     bool ham_built = false;               // integral blocks and programs exist

@@ -605,6 +605,11 @@ extern "C" int64_t lrcc_plan_slabs(int64_t V, int64_t budget_el, int64_t row_cap
     return (int64_t)plan.size();
 }
 
+// bytes for one contraction group of assembled <ab||ef> rows: a quarter of the
+// free memory, at most 8 GiB (the residual sweeps hold many amplitude-sized
+// tensors while the ladder runs, so the group must not take what is left)
+static double group_budget(Dev& D) { return std::min(0.25 * free_bytes(D), 8.0 * double(1ull << 30)); }
+
 // rows per contraction group: the most 128-row M tiles that fit in w_bytes of
 // W rows (row_bytes each), among counts whose tile grid (x tiles_n) fills
 // whole waves of the SMs best
@@ -797,7 +802,7 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
         }
         const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), LC.slab_rows);
         const int64_t cap = LC.slab_rows > 0 ? 3 * LC.slab_rows
-                                             : group_rows(D, 0.25 * free_bytes(D), 16.0 * PV, ncol);
+                                             : group_rows(D, group_budget(D), 16.0 * PV, ncol);
         const std::vector<SlabGroup> groups = group_chunks(plan, cap);
         SlabScratch sc(D, plan, V);
         int64_t wrows = 0;
@@ -831,7 +836,7 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
     const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), LC.slab_rows);
     int64_t r1, p1;
     const double row_bytes = (double)tc_embed_bytes(prec, 1, PV, 1, r1, p1, false);  // one embedded W' row
-    const int64_t cap = LC.slab_rows > 0 ? 3 * LC.slab_rows : group_rows(D, 0.25 * free_bytes(D), row_bytes, ncol);
+    const int64_t cap = LC.slab_rows > 0 ? 3 * LC.slab_rows : group_rows(D, group_budget(D), row_bytes, ncol);
     const std::vector<SlabGroup> groups = group_chunks(plan, cap);
     SlabScratch sc(D, plan, V);
     int64_t wrows = 0;

@@ -288,6 +288,7 @@ void fns_truncate_impl(lrcc_ctx* c, int by_count, double value, double omega, in
     c->eps = eps;
     c->ham_built = false;
     c->ground = false;
+    c->linearized = false;
     c->cc.reset();
     c->ccfx.reset();
     c->ccmu.clear();

@@ -1051,8 +1051,109 @@ static double orient_cost(int64_t M, int64_t N, int64_t sCm) {
     return pm * pn * (sCm == 1 ? 1.0 : 1.15);
 }
 
+// ---------------------------------------------------------------------------
+// Operand embeddings are transient copies (bf16x3: 12 bytes per complex A
+// element, 24 per B element; integer slices: 28 and 56), so a contraction whose
+// operands are amplitude-sized at large O, V (4.5 GB per right-hand side at
+// O=28, V=600) would need tens of GB for them.  Such a GEMM runs as a sequence
+// of sub-GEMMs over halves of N, M or K until the embedded operands of each fit
+// in a bounded budget.  A half along a two-level index group (g = g1 d2 + g2)
+// is cut at a multiple of d2 when the group has several outer blocks; within a
+// single outer block the group is flat with stride s.  The second K half adds
+// to C (beta = 1).
+// ---------------------------------------------------------------------------
+namespace {
+
+// split [0, n) of one index group shared by two operands (x and y) at about
+// n/2: returns the first part's size and both operands' offsets of the second
+// part, and makes the groups of the second part consistent
+bool halve_group(int64_t n, int64_t& d2x, int64_t s1x, int64_t sx, int64_t& d2y, int64_t s1y, int64_t sy,
+                 int64_t& n1, int64_t& offx, int64_t& offy, bool& to_flat) {
+    if (n < 2) return false;
+    if (d2x > 0 && d2y > 0 && d2x != d2y) return false;  // groups cut at different labels
+    const int64_t d2 = d2x > 0 ? d2x : d2y;
+    to_flat = false;
+    if (d2 > 0 && n / d2 >= 2) {
+        const int64_t q = (n / d2) / 2;
+        n1 = q * d2;
+        offx = d2x > 0 ? q * s1x : n1 * sx;
+        offy = d2y > 0 ? q * s1y : n1 * sy;
+    } else {
+        n1 = n / 2;
+        offx = n1 * sx;
+        offy = n1 * sy;
+        to_flat = d2 > 0;  // one outer block: a flat group with stride s
+    }
+    return true;
+}
+
+// halves of g along dim 0 (M), 1 (N) or 2 (K)
+bool halve_gemm(const GemmArgs& g, int dim, GemmArgs& g1, GemmArgs& g2) {
+    g1 = g;
+    g2 = g;
+    int64_t n1 = 0, ox = 0, oy = 0;
+    bool flat = false;
+    if (dim == 0) {
+        int64_t dx = g.dAm2, dy = g.dCm2;
+        if (!halve_group(g.M, dx, g.sAm1, g.sAm, dy, g.sCm1, g.sCm, n1, ox, oy, flat)) return false;
+        g1.M = n1;
+        g2.M = g.M - n1;
+        g2.A = g.A + ox;
+        g2.C = g.C + oy;
+        if (flat) g1.dAm2 = g2.dAm2 = g1.dCm2 = g2.dCm2 = 0;
+    } else if (dim == 1) {
+        int64_t dx = g.dBn2, dy = g.dCn2;
+        if (!halve_group(g.N, dx, g.sBn1, g.sBn, dy, g.sCn1, g.sCn, n1, ox, oy, flat)) return false;
+        g1.N = n1;
+        g2.N = g.N - n1;
+        g2.B = g.B + ox;
+        g2.C = g.C + oy;
+        if (flat) g1.dBn2 = g2.dBn2 = g1.dCn2 = g2.dCn2 = 0;
+    } else {
+        int64_t dx = g.dAk2, dy = g.dBk2;
+        if (!halve_group(g.K, dx, g.sAk1, g.sAk, dy, g.sBk1, g.sBk, n1, ox, oy, flat)) return false;
+        g1.K = n1;
+        g2.K = g.K - n1;
+        g2.A = g.A + ox;
+        g2.B = g.B + oy;
+        g2.beta = mkc(1.0);
+        if (flat) g1.dAk2 = g2.dAk2 = g1.dBk2 = g2.dBk2 = 0;
+    }
+    return true;
+}
+
+// the dimension to halve: the largest of M, N, K (K halves both operands)
+bool split_gemm(const GemmArgs& g, GemmArgs& g1, GemmArgs& g2) {
+    int order[3];
+    if (g.K >= std::max(g.M, g.N)) { order[0] = 2; order[1] = g.N >= g.M ? 1 : 0; order[2] = g.N >= g.M ? 0 : 1; }
+    else if (g.N >= g.M) { order[0] = 1; order[1] = 2; order[2] = 0; }
+    else { order[0] = 0; order[1] = 2; order[2] = 1; }
+    for (int d : order)
+        if (halve_gemm(g, d, g1, g2)) return true;
+    return false;
+}
+
+// bytes the embedded operands of one GEMM may take
+double embed_budget(Dev& D) {
+    if (D.embed_budget > 0) return D.embed_budget;
+    return std::min(6.0 * double(1ull << 30), 0.1 * free_bytes(D));
+}
+
+}  // namespace
+
 void gemm_tc(Dev& D, const GemmArgs& g0, int prec) {
     if (g0.M <= 0 || g0.N <= 0 || g0.batch <= 0) return;
+    if (g0.K > 0) {
+        int64_t ra, pa_, rb, pb_;
+        const double bytes = double(tc_embed_bytes(prec, g0.M, g0.K, g0.batch, ra, pa_, false)) +
+                             double(tc_embed_bytes(prec, g0.N, g0.K, g0.batch, rb, pb_, true));
+        GemmArgs g1, g2;
+        if (bytes > embed_budget(D) && split_gemm(g0, g1, g2)) {
+            gemm_tc(D, g1, prec);
+            gemm_tc(D, g2, prec);
+            return;
+        }
+    }
     REQUIRE(prec == LRCC_MIXED_TF32 || prec == LRCC_MIXED_BF16X3, "gemm_tc: bad precision");
     if (g0.K <= 0) {
         REQUIRE(g0.flat(), "gemm_tc: K = 0 with two-level groups");
@@ -1177,6 +1278,17 @@ void oz_gemm_embedded(Dev& D, const void* pa, const void* pb, int64_t batch, int
 void gemm_tc_f64(Dev& D, const GemmArgs& g0) {
     if (g0.M <= 0 || g0.N <= 0 || g0.batch <= 0) return;
     REQUIRE(g0.flat(), "gemm_tc_f64: two-level index groups are not supported");
+    if (g0.K > 0) {
+        int64_t ra, ka, rb, kb;
+        const double bytes = double(oz_embed_bytes(g0.M, g0.K, g0.batch, ra, ka, false)) +
+                             double(oz_embed_bytes(g0.N, g0.K, g0.batch, rb, kb, true));
+        GemmArgs g1, g2;
+        if (bytes > embed_budget(D) && split_gemm(g0, g1, g2)) {
+            gemm_tc_f64(D, g1);
+            gemm_tc_f64(D, g2);
+            return;
+        }
+    }
     if (g0.K <= 0) {
         gemm_f64(D, g0);  // pure beta scaling
         return;

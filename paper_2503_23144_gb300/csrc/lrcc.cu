@@ -289,6 +289,7 @@ void do_ground(lrcc_ctx* c, cplx& E, int& itT, int& itL) {
         itT += solve_loop(c, T, res, zero, c->opt.r_tol, c->opt.max_iter);
         c->T = amp_copy(D, T);
         residual_T(D, *c->cc, c->T, 0, p64(c), &E);  // primal cached at converged T
+        c->linearized = true;
         c->phase_ms[0] = tm.stop();
     }
     {
@@ -632,6 +633,7 @@ void lrcc_default_options(lrcc_options* o) {
     o->fns_density = 0;
     o->solver = 0;
     o->subspace_max = 0;
+    o->embed_budget_mb = 0;
 }
 
 const char* lrcc_last_error(const lrcc_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
@@ -679,6 +681,8 @@ lrcc_status lrcc_setup(const double* eps, const double* B, int L, const double* 
         REQUIRE(c->opt.solver == 0 || !is_mixed(c->opt.prec),
                 "the shared-subspace solver needs FP64-class products (LRCC_FP64 or LRCC_FP64_EMULATED)");
         REQUIRE(c->opt.subspace_max >= 0, "subspace_max must be >= 0");
+        REQUIRE(c->opt.embed_budget_mb >= 0, "embed_budget_mb must be >= 0");
+        c->D.embed_budget = double(c->opt.embed_budget_mb) * double(1 << 20);
         int dev = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&c->D.sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -792,7 +796,8 @@ static lrcc_status residual_impl(lrcc_ctx* c, int kind, const double* t, const d
     if ((kind == LRCC_RES_SIGMA || kind == LRCC_RES_VJP || kind == LRCC_RES_VJP_FULL) && !t) {
         // linearised at the converged ground state: the primal values cached in
         // the solver's program are reused (exactly the maps lrcc_solve applies)
-        if (!c->ground) throw LrccError(LRCC_ESTATE, "t == NULL needs lrcc_ccsd_ground first");
+        if (!c->ground && !c->linearized)
+            throw LrccError(LRCC_ESTATE, "t == NULL needs lrcc_ccsd_ground or lrcc_linearize first");
         if (kind == LRCC_RES_SIGMA) {
             res = sigma(D, *c->cc, X, prec);
         } else if (kind == LRCC_RES_VJP) {
@@ -882,6 +887,40 @@ lrcc_status lrcc_residual(lrcc_ctx* c, int kind, const double* t, const double* 
         lrcc_status s = residual_impl(c, kind, t, in, R, comp, prec, out, false);
         check_device_error(c->D);
         return s;
+    } catch (const LrccError& e) {
+        return fail(c, e);
+    } catch (const std::exception& e) {
+        c->err = e.what();
+        return LRCC_ECUDA;
+    }
+}
+
+lrcc_status lrcc_linearize(lrcc_ctx* c, const double* t, int prec) {
+    if (!c) return LRCC_EINVAL;
+    try {
+        REQUIRE(t, "t is NULL");
+        REQUIRE(prec >= LRCC_FP64 && prec <= LRCC_FP64_EMULATED, "bad precision");
+        ensure_ham(c);
+        Dev& D = c->D;
+        const int64_t O = c->O, V = c->V, n1 = O * V, n2 = O * O * V * V;
+        c->ground = false;
+        c->linearized = false;
+        Tensor tb = dev_copy_c(D, t, {n1 + n2});
+        Amp T = amp_empty(D, 1, O, V);
+        axpby(D, mkc(1.0), tb.slice(0, 0, n1).reshape({1, O, V}), false, mkc(0.0), T.t1);
+        Tensor s2 = tb.slice(0, n1, n2).reshape({1, O, O, V, V});
+        // antisymmetric projection of the doubles block
+        perm_axpby(D, "Zijab->Zijab", mkc(0.25), s2, mkc(0.0), T.t2);
+        perm_axpby(D, "Zijab->Zjiab", mkc(-0.25), s2, mkc(1.0), T.t2);
+        perm_axpby(D, "Zijab->Zijba", mkc(-0.25), s2, mkc(1.0), T.t2);
+        perm_axpby(D, "Zijab->Zjiba", mkc(0.25), s2, mkc(1.0), T.t2);
+        tb = Tensor();
+        c->T = T;
+        residual_T(D, *c->cc, c->T, 0, prec);
+        CK(cudaStreamSynchronize(D.st));
+        check_device_error(D);
+        c->linearized = true;
+        return LRCC_OK;
     } catch (const LrccError& e) {
         return fail(c, e);
     } catch (const std::exception& e) {

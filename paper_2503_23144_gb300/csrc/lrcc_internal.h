@@ -75,6 +75,7 @@ struct Dev {
     int64_t launches = 0;
     int* err_flag = nullptr;  // device word set by kernels whose bounded waits expire
     int sm_count = 148;
+    double embed_budget = 0;  // bytes for one GEMM's embedded operands (0: automatic)
     bool timing = false;
     std::vector<KRec> recs;
 };

@@ -299,17 +299,41 @@ Diis::~Diis() {
     if (slots_dev) cudaFree(slots_dev);
 }
 
+// The history is kept in packed form: singles as they are and the doubles by
+// their unique pairs (i<j, a<b), [R][P_O P_V] -- a quarter of the full
+// antisymmetric array, exact for antisymmetric amplitudes -- so that a long
+// history of many right-hand sides fits next to the residual sweeps.
+namespace {
+Amp pack_amp(Dev& D, const Amp& x) {
+    const int64_t R = x.t1.d[0], O = x.t1.d[1], V = x.t1.d[2];
+    REQUIRE(x.t2.contiguous(), "DIIS: doubles must be contiguous");
+    Amp p;
+    p.t1 = empty(D, x.t1.shape());
+    axpby(D, mkc(1.0), x.t1, false, mkc(0.0), p.t1);
+    p.t2 = empty(D, {R, O * (O - 1) / 2 * (V * (V - 1) / 2)});
+    ladder_pack_xt(D, x.t2.p, p.t2.p, R, O, V);
+    return p;
+}
+// per-RHS dot over unique amplitudes of packed vectors (conjugated first)
+Tensor packed_dot(Dev& D, const Amp& a, const Amp& b) {
+    Tensor out = empty(D, {a.t1.d[0]});
+    ein(D, "Zia,Zia->Z", mkc(1.0), a.t1, true, b.t1, false, mkc(0.0), out);
+    ein(D, "Zk,Zk->Z", mkc(1.0), a.t2, true, b.t2, false, mkc(1.0), out);
+    return out;
+}
+}  // namespace
+
 Amp Diis::push_extrapolate(Dev& D, const Amp& x, const Amp& e) {
     int s = count % nmax;
-    xs[s] = x;
-    es[s] = e;
+    xs[s] = pack_amp(D, x);
+    es[s] = pack_amp(D, e);
     count++;
     int k = std::min(count, nmax);
     // stored slots oldest first
     std::vector<int> sl;
     for (int q = count - k; q < count; ++q) sl.push_back(q % nmax);
     for (int i : sl) {
-        Tensor d = amp_dot(D, es[i], true, es[s]);
+        Tensor d = packed_dot(D, es[i], es[s]);
         k_gram_set<<<(R + 127) / 128, 128, 0, D.st>>>(gram.p, R, nmax, i, s, d.p);
         LAUNCH_CHECK(D);
     }
@@ -317,17 +341,20 @@ Amp Diis::push_extrapolate(Dev& D, const Amp& x, const Amp& e) {
     CK(cudaMemcpyAsync(slots_dev, sl.data(), sizeof(int) * k, cudaMemcpyHostToDevice, D.st));
     k_diis_solve<<<(R + 63) / 64, 64, 0, D.st>>>(gram.p, R, nmax, slots_dev, k, coef.p);
     LAUNCH_CHECK(D);
-    Amp out = amp_empty(D, R, x.t1.d[1], x.t1.d[2]);
+    const int64_t O = x.t1.d[1], V = x.t1.d[2];
+    Amp out = amp_empty(D, R, O, V);
+    Tensor t2p = empty(D, xs[s].t2.shape());
     Ptrs p1, p2;
     for (int i = 0; i < k; ++i) {
         p1.p[i] = xs[sl[i]].t1.p;
         p2.p[i] = xs[sl[i]].t2.p;
     }
-    int64_t n1 = x.t1.numel() / R, n2 = x.t2.numel() / R;
+    int64_t n1 = x.t1.numel() / R, n2 = t2p.numel() / R;
     k_lincomb<<<grid_n(D, R * n1), 256, 0, D.st>>>(R, n1, FastDiv(n1), p1, k, nullptr, coef.p, nmax, slots_dev, out.t1.p);
     LAUNCH_CHECK(D);
-    k_lincomb<<<grid_n(D, R * n2), 256, 0, D.st>>>(R, n2, FastDiv(n2), p2, k, nullptr, coef.p, nmax, slots_dev, out.t2.p);
+    k_lincomb<<<grid_n(D, R * n2), 256, 0, D.st>>>(R, n2, FastDiv(n2), p2, k, nullptr, coef.p, nmax, slots_dev, t2p.p);
     LAUNCH_CHECK(D);
+    ladder_unpack_zt(D, t2p.p, out.t2.p, R, O, V, mkc(1.0), mkc(0.0));
     // the host copy of the slot list must outlive the async copy
     CK(cudaStreamSynchronize(D.st));
     return out;

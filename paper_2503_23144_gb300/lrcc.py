@@ -29,7 +29,7 @@ class lrcc_options(ctypes.Structure):
                 ("diis_size", ctypes.c_int), ("rhs_chunk", ctypes.c_int), ("prec", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("plus_omega", ctypes.c_int), ("slab_rows", ctypes.c_int),
                 ("pm_omega", ctypes.c_int), ("fp64_products", ctypes.c_int), ("fns_density", ctypes.c_int),
-                ("solver", ctypes.c_int), ("subspace_max", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("subspace_max", ctypes.c_int), ("embed_budget_mb", ctypes.c_int)]
 
 
 class LrccError(RuntimeError):
@@ -73,6 +73,7 @@ SIGNATURES = [
     ("lrcc_ladder_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp,
                                            ctypes.c_int, _vp]),
     ("lrcc_solve_counts", ctypes.c_int, [_vp, _ip, _ip]),
+    ("lrcc_linearize", ctypes.c_int, [_vp, _dp, ctypes.c_int]),
     ("lrcc_kernel_stats", ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                          ctypes.POINTER(ctypes.c_int64), _dp, _dp, _dp]),
 ]
@@ -240,6 +241,13 @@ def lrcc_residual(ctx: Context, kind: int, t, x, comp: int = 0, prec: int = LRCC
                                       _cd(x.view(np.float64)), R, comp, prec, _cd(out.view(np.float64))))
     del tp
     return out
+
+
+def lrcc_linearize(ctx: Context, t, prec: int = LRCC_FP64) -> None:
+    """Fix the amplitudes t (flat [n_amp], host) at which later residual maps
+    with t=None are applied (the program is evaluated once at t)."""
+    tt = _c128(t).reshape(-1)
+    ctx.check(library().lrcc_linearize(ctx.h, _cd(tt.view(np.float64)), prec))
 
 
 def _stream_ptr():

@@ -52,6 +52,9 @@ CONFIGS = {
     # dynamic spectrum: 3 components x 64 frequencies in [0, 0.15]
     "c4": dict(O=28, V=600, L=1200, seed=3, comps=(0, 1, 2),
                omegas=tuple(np.linspace(0.0, 0.15, 64).tolist())),
+    # the dynamic-spectrum system's occupied count and factor rank on a virtual
+    # space small enough for the full oracle: both ends of its frequency grid
+    "c4r": dict(O=28, V=60, L=1200, seed=3, comps=(0, 1, 2), omegas=(0.0, 0.15)),
     # ladder throughput at the largest virtual space: 12 batched right-hand sides
     "c5": dict(O=20, V=1200, L=1800, seed=4, comps=(0, 1, 2), omegas=(0.0, 0.02, 0.05, 0.08)),
 }
