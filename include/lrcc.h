@@ -90,6 +90,11 @@ typedef struct {
                               solutions; 0 (default) automatic (8 per right-hand side,
                               48..400, within 30 % of free device memory); a value below
                               2 x the right-hand sides of a batch gives LRCC_EINVAL  */
+    int ladder_hermitian;  /* per-call <ab||ef> assembly (mixed precisions): 1 assembles only the
+                              columns (ef) >= (ab) of each row group and contracts the rest
+                              through the conjugate transpose (<ef||ab> = conj <ab||ef>);
+                              -1 assembles whole rows; 0 (default) automatic: 1 when a row
+                              group holds at least 1024 rows                          */
     int embed_budget_mb;   /* tensor-core contractions: bytes (MiB) that the transient split
                               copies of one GEMM's two operands may take; a larger GEMM runs
                               as sub-GEMMs over halves of N, M or K.  0 (default) automatic:

@@ -661,8 +661,13 @@ struct SlabScratch {
     }
 };
 
+// emin > 0 (embedded path only): only the columns (pairs e<f) >= cmin of the
+// rows are needed, so the products GT are computed only for tiles that hold an
+// index e >= emin among their rows (a,e) and an f >= emin among their columns
+// (b,f) (every needed <ab||ef> has e, f >= emin), and only columns >= cmin are
+// written.
 static void assemble_slab(Dev& D, LadderCtx& LC, const Slab& sl, int prec, bool conj, cplx* W, void* Wemb,
-                          int64_t pitch_w, int64_t rows_w, SlabScratch& sc) {
+                          int64_t pitch_w, int64_t rows_w, SlabScratch& sc, int64_t emin = 0, int64_t cmin = 0) {
     const int64_t L = LC.Bvv.d[0], V = LC.Bvv.d[1];
     const int64_t M = (sl.a1 - sl.a0) * V, N = (sl.b1 - sl.gb0) * V;
     REQUIRE(sc.gt && M * N <= sc.gt_el, "ladder: slab product buffer too small");
@@ -694,10 +699,15 @@ static void assemble_slab(Dev& D, LadderCtx& LC, const Slab& sl, int prec, bool 
     REQUIRE(sc.a_pitch == LC.b_pitch, "ladder: embedded K pitch mismatch");
     const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
     const char* pb = (const char*)LC.bcache->p + (size_t)(2 * sl.gb0 * V) * (size_t)(LC.b_pitch * es);
-    tc_gemm_embedded(D, prec, sc.aemb->p, pb, 1, M, N, L, LC.b_pitch, M, LC.b_rows, GT.p, 0, 1, M, mkc(1.0),
-                     mkc(0.0), false,
-                     8.0 * M * N * L);
-    tc_embed_antisym_slab(D, prec, GT.p, M, sl.a0, sl.gb0, sl.prow0, sl.nrows, V, pitch_w, rows_w, Wemb);
+    // the B rows from (b, f) = (gb0, 0) to the end of the cached embedding
+    const int64_t rows_b = LC.b_rows - 2 * sl.gb0 * V;
+    // GT in complex FP32: it is only split into the bf16x3 / TF32 embedding
+    // (2^-17 / 2^-11 relative), so FP32 (2^-24) loses nothing and halves its traffic
+    const double frac = double(V - emin) / double(V);
+    tc_gemm_embedded_ex(D, prec, sc.aemb->p, pb, M, N, L, 0, LC.b_pitch, M, rows_b, GT.p, 1, M, mkc(1.0), mkc(0.0),
+                        false, 8.0 * M * N * L * frac * frac, emin > 0 ? (int)V : 0, (int)emin, true);
+    tc_embed_antisym_slab(D, prec, GT.p, M, sl.a0, sl.gb0, sl.prow0, sl.nrows, V, pitch_w, rows_w, Wemb, emin, cmin,
+                          true);
 }
 
 // Build the embedded <ab||ef> matrix W' (rows a<b, K over e<f) once for a
@@ -772,6 +782,18 @@ static bool ensure_ozcache(Dev& D, LadderCtx& LC, int64_t V) {
     return true;
 }
 
+// pitch of an embedded operand with K complex columns (batch 1)
+static int64_t t_pitch_for(int prec, int64_t K) {
+    int64_t r, p;
+    tc_embed_bytes(prec, 1, K, 1, r, p, false);
+    return p;
+}
+
+static void ladder_hermitian(Dev& D, LadderCtx& LC, const cplx* Xt, void* pb, int64_t pitch, int64_t rows_e,
+                             cplx* Zt, int64_t ncol, bool transpose, int prec);
+static void ladder_whole_rows(Dev& D, LadderCtx& LC, void* pb, int64_t pitch, int64_t rows_e, cplx* Zt,
+                              int64_t ncol, bool transpose, int prec);
+
 void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol, bool transpose, int prec) {
     const int64_t V = LC.Bvv.d[1], PV = V * (V - 1) / 2;
     if (ncol <= 0 || PV <= 0) return;
@@ -831,6 +853,23 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
                          mkc(0.0), transpose, 8.0 * PV * PV * ncol);
         return;
     }
+    // the Hermitian-half scheme pays when a row group is long enough for the
+    // conjugate-transpose products (K = the group's rows) to amortise their
+    // read-modify-write of Z; with very long <ab||ef> rows (V = 1200: 8.6 MB
+    // each) the groups are short and whole rows are assembled instead
+    int64_t r1, p1;
+    const double row_bytes = (double)tc_embed_bytes(prec, 1, PV, 1, r1, p1, false);
+    const int64_t hcap = LC.slab_rows > 0 ? 3 * LC.slab_rows : group_rows(D, 0.5 * group_budget(D), row_bytes, ncol);
+    const bool herm = LC.hermitian > 0 || (LC.hermitian == 0 && hcap >= 1024);
+    if (herm) ladder_hermitian(D, LC, Xt, pb, pitch, rows_e, Zt, ncol, transpose, prec);
+    else ladder_whole_rows(D, LC, pb, pitch, rows_e, Zt, ncol, transpose, prec);
+}
+
+// Per-call <ab||ef> assembled by whole rows: each contraction group of rows
+// (a<b) is assembled over every column (e<f) and multiplied by X'.
+static void ladder_whole_rows(Dev& D, LadderCtx& LC, void* pb, int64_t pitch, int64_t rows_e, cplx* Zt,
+                              int64_t ncol, bool transpose, int prec) {
+    const int64_t V = LC.Bvv.d[1], PV = V * (V - 1) / 2;
     const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
     ensure_bcache(D, LC, prec);
     const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), LC.slab_rows);
@@ -854,6 +893,76 @@ void ladder_packed(Dev& D, LadderCtx& LC, const cplx* Xt, cplx* Zt, int64_t ncol
         tc_gemm_embedded(D, prec, pw, pb, 1, gr.nrows, ncol, PV, pitch, wrows, rows_e, Zt + gr.prow0, 0, 1, PV,
                          mkc(1.0), mkc(0.0), transpose, 8.0 * gr.nrows * PV * ncol);
     }
+}
+
+// Per-call <ab||ef> on the tensor cores with its Hermitian symmetry,
+// <ef||ab> = conj <ab||ef>.  Rows (pairs a<b) are cut into contraction groups
+// G = [p0, p1).  For each group only the columns c >= p0 are assembled (about
+// half of the matrix over all groups), then
+//   GEMM 1:  Z[n][r] += sum_{c >= p0} W[r][c] X[n][c]          (r in G)
+//   GEMM 2:  Z[n][c] += sum_{r in G} conj(W[r][c]) X[n][r]      (c >= p1)
+// so every (r, c) pair enters once: the diagonal block through GEMM 1, the part
+// above it through both.  GEMM 1 starts at the k-block boundary below p0; the
+// columns between it and p0 are zeroed.  GEMM 2's A operand is the conjugate
+// transpose of the group's columns c >= p1, its B operand the group's slice of
+// X.  The transpose map is conj(W conj(X)) as in the cached path.
+static void ladder_hermitian(Dev& D, LadderCtx& LC, const cplx* Xt, void* pb, int64_t pitch, int64_t rows_e,
+                             cplx* Zt, int64_t ncol, bool transpose, int prec) {
+    const int64_t V = LC.Bvv.d[1], PV = V * (V - 1) / 2;
+    const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
+    ensure_bcache(D, LC, prec);
+    const std::vector<Slab> plan = plan_slabs(V, slab_budget_el(D), LC.slab_rows);
+    int64_t r1, p1;
+    const double row_bytes = (double)tc_embed_bytes(prec, 1, PV, 1, r1, p1, false);  // one embedded W' row
+    // W' rows and their conjugate transpose (as large again) share the group budget
+    const int64_t cap = LC.slab_rows > 0 ? 3 * LC.slab_rows : group_rows(D, 0.5 * group_budget(D), row_bytes, ncol);
+    const std::vector<SlabGroup> groups = group_chunks(plan, cap);
+    SlabScratch sc(D, plan, V);
+    int64_t wrows = 0;
+    for (const SlabGroup& gr : groups) wrows = std::max(wrows, gr.nrows);
+    int64_t wr_e, wpitch;
+    const size_t wb = tc_embed_bytes(prec, wrows, PV, 1, wr_e, wpitch, false);
+    REQUIRE(wpitch == pitch, "ladder: W' and X' pitch mismatch");
+    void* pw = D.pool.get(wb);
+    std::shared_ptr<DevBuf> hw(new DevBuf{&D.pool, pw, wb});
+    tc_zero_tail(D, prec, pw, wrows, PV, wrows);
+    // conjugate-transpose block: rows c (at most PV - p1 of the first group), K = group rows
+    int64_t t_re, t_pitch;
+    const size_t tb = tc_embed_bytes(prec, PV, wrows, 1, t_re, t_pitch, false);
+    void* pt = D.pool.get(tb);
+    std::shared_ptr<DevBuf> ht(new DevBuf{&D.pool, pt, tb});
+    int64_t g_re, g_pitch;
+    const size_t gbytes = tc_embed_bytes(prec, ncol, wrows, 1, g_re, g_pitch, true);
+    void* pg = D.pool.get(gbytes);
+    std::shared_ptr<DevBuf> hg(new DevBuf{&D.pool, pg, gbytes});
+    CK(cudaMemsetAsync(Zt, 0, sizeof(cplx) * (size_t)ncol * (size_t)PV, D.st));
+    const int64_t kal = tc_k_align(prec);
+    for (const SlabGroup& gr : groups) {
+        const int64_t q0 = gr.prow0, q1 = gr.prow0 + gr.nrows;
+        // a of the group's first pair: every column it needs has e, f >= a
+        int64_t emin = 0;
+        while (emin < V - 1 && (emin + 1) * (2 * V - (emin + 1) - 1) / 2 <= q0) ++emin;
+        for (size_t c = gr.c0; c < gr.c1; ++c)
+            assemble_slab(D, LC, plan[c], prec, false, nullptr,
+                          (char*)pw + (size_t)((plan[c].prow0 - gr.prow0) * pitch * es), pitch, wrows, sc, emin, q0);
+        const int64_t kstart = q0 / kal * kal;
+        tc_zero_cols_a(D, prec, pw, PV, wrows, gr.nrows, kstart, q0);
+        // GEMM 1: rows G, K range [kstart, PV)
+        tc_gemm_embedded_ex(D, prec, pw, pb, gr.nrows, ncol, PV, kstart, pitch, wrows, rows_e, Zt + q0, 1, PV,
+                            mkc(1.0), mkc(1.0), transpose, 8.0 * gr.nrows * double(PV - q0) * ncol, 0, 0);
+        if (q1 < PV) {
+            // GEMM 2: rows c in [q1, PV), K = the group's rows
+            const int64_t nc = PV - q1;
+            tc_transpose_conj_a(D, prec, pw, PV, wrows, gr.nrows, q1, nc, pt, nc);
+            tc_embed_b(D, prec, Xt + q0, 0, 1, PV, transpose, 1, gr.nrows, ncol, t_pitch_for(prec, gr.nrows), g_re,
+                       pg);
+            tc_gemm_embedded(D, prec, pt, pg, 1, nc, ncol, gr.nrows, t_pitch_for(prec, gr.nrows), nc, g_re, Zt + q1,
+                             0, 1, PV, mkc(1.0), mkc(1.0), transpose, 8.0 * double(nc) * gr.nrows * ncol);
+        }
+    }
+    (void)t_re;
+    (void)t_pitch;
+    (void)g_pitch;
 }
 
 void ladder(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose, int prec) {

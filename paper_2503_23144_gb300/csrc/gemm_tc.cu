@@ -149,6 +149,7 @@ struct Epi {
     int conj_acc;     // use conj(accumulator): conj(A.conj(B)) = conj(A).B
     int atomic;       // split-K: accumulate alpha*acc into C with FP64 atomics (C pre-scaled)
     int exact_alpha;  // apply alpha in FP64 (accumulators that are exact sums)
+    int f32out;       // C holds complex FP32 pairs (float2): alpha acc (+ C) in FP32, no split K
 };
 
 // alpha * accumulator (FP32 pair) as FP64: in FP32 arithmetic unless alpha must
@@ -180,8 +181,27 @@ struct Sched {
     int tiles_m, tiles_n, batch, splits, kps, num_kb, group;
     int kchunk;  // k-blocks accumulated in FP32 before the epilogue adds them to C in FP64
     int kpb;     // k-blocks per K panel of the operands (0: rows stored whole)
+    int kbase;   // k-block of the operands where this GEMM's K range starts
+    // tile mask (mv > 0): rows m and complex columns n are grouped in blocks of
+    // mv; a tile runs only if one of its rows and one of its columns have
+    // (index mod mv) >= memin
+    int mv, memin;
+    long long mrows, mcols;
     long long units;
 };
+
+// does the index range [i0, i1] contain an index with (index mod v) >= e?
+__device__ __forceinline__ bool range_live(long long i0, long long i1, int v, int e) {
+    return (i0 / v != i1 / v) || (int)(i1 % v) >= e;
+}
+
+template <int BN>
+__device__ __forceinline__ bool unit_live(const Sched& s, int tm, int tn) {
+    if (s.mv <= 0) return true;
+    const long long r0 = (long long)tm * BM, c0 = (long long)tn * (BN / 2);
+    const long long r1 = min(s.mrows, r0 + BM) - 1, c1 = min(s.mcols, c0 + BN / 2) - 1;
+    return range_live(r0, r1, s.mv, s.memin) && range_live(c0, c1, s.mv, s.memin);
+}
 
 __device__ __forceinline__ void unit_coords(const Sched& s, long long u, int& tm, int& tn, int& bz, int& kb0,
                                             int& kb1) {
@@ -271,6 +291,7 @@ __global__ void __launch_bounds__(192, 1)
             for (long long u = blockIdx.x; ok && u < sc.units; u += gridDim.x) {
                 int tm, tn, bz, kb0, kb1;
                 unit_coords(sc, u, tm, tn, bz, kb0, kb1);
+                if (!unit_live<BN>(sc, tm, tn)) continue;
                 for (int kb = kb0; kb < kb1; ++kb) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
@@ -281,8 +302,9 @@ __global__ void __launch_bounds__(192, 1)
                     mbar_expect_tx(&full[s], A_STAGE + B_STAGE);
                     ++it;
                     if (skip_tma) continue;  // fault injection: the stage's bytes never arrive
-                    const int kx = sc.kpb ? (kb % sc.kpb) * KELEM : kb * KELEM;
-                    const int kz = sc.kpb ? kb / sc.kpb : bz;
+                    const int kg = kb + sc.kbase;
+                    const int kx = sc.kpb ? (kg % sc.kpb) * KELEM : kg * KELEM;
+                    const int kz = sc.kpb ? kg / sc.kpb : bz;
                     tma_load_3d(sA + s * A_STAGE, &ta, &full[s], kx, tm * BM, kz);
                     tma_load_3d(sB + s * B_STAGE, &tb, &full[s], kx, tn * BN, kz);
                 }
@@ -302,6 +324,7 @@ __global__ void __launch_bounds__(192, 1)
             for (long long u = blockIdx.x; ok && u < sc.units; u += gridDim.x) {
                 int tm, tn, bz, kb0, kb1;
                 unit_coords(sc, u, tm, tn, bz, kb0, kb1);
+                if (!unit_live<BN>(sc, tm, tn)) continue;
                 // the unit's K range in chunks, each into the next accumulator
                 for (int c0 = kb0; ok && c0 < kb1; c0 += sc.kchunk) {
                     const int c1 = min(kb1, c0 + sc.kchunk);
@@ -349,6 +372,7 @@ __global__ void __launch_bounds__(192, 1)
         for (long long u = blockIdx.x; ok && u < sc.units; u += gridDim.x) {
             int tm, tn, bz, kb0, kb1;
             unit_coords(sc, u, tm, tn, bz, kb0, kb1);
+            if (!unit_live<BN>(sc, tm, tn)) continue;
             for (int c0 = kb0; c0 < kb1; c0 += sc.kchunk) {
                 // first chunk: C = alpha acc + beta C; later chunks: C += alpha acc
                 const bool first = c0 == kb0;
@@ -363,6 +387,42 @@ __global__ void __launch_bounds__(192, 1)
                 const int64_t m = (int64_t)tm * BM + q * 32 + lane;
                 const bool live = m < ep.M;
                 cplx* Cb = ep.C + (int64_t)bz * ep.sCb + (live ? lvl_off(ep.lm, m) : 0);
+                if (ep.f32out) {
+                    // complex FP32 output (an intermediate read only by a split/convert kernel)
+                    float2* Cf = (float2*)ep.C + (int64_t)bz * ep.sCb + (live ? lvl_off(ep.lm, m) : 0);
+#pragma unroll 1
+                    for (int c = 0; c < BN / 32; ++c) {
+                        uint32_t r[32];
+                        const int64_t n0 = (int64_t)tn * (BN / 2) + c * 16;
+                        float2 oldf[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            oldf[j] = (rd && live && n0 + j < ep.N) ? Cf[lvl_off(ep.ln, n0 + j)] : make_float2(0.f, 0.f);
+                        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32), r);
+                        if (live) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const int64_t n = n0 + j;
+                                if (n < ep.N) {
+                                    const float fr = __uint_as_float(r[2 * j]);
+                                    const float fi = ep.conj_acc ? -__uint_as_float(r[2 * j + 1]) : __uint_as_float(r[2 * j + 1]);
+                                    float vr = alpha1 ? fr : afx * fr - afy * fi;
+                                    float vi = alpha1 ? fi : afx * fi + afy * fr;
+                                    if (rd) {
+                                        vr += oldf[j].x;
+                                        vi += oldf[j].y;
+                                    }
+                                    Cf[lvl_off(ep.ln, n)] = make_float2(vr, vi);
+                                }
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acce[acc]);
+                    ++ti;
+                    continue;
+                }
 #pragma unroll 1
                 for (int c = 0; c < BN / 32; ++c) {
                     uint32_t r[32];
@@ -730,10 +790,19 @@ __device__ __forceinline__ void pair_of(int64_t k, int64_t n, int64_t& p, int64_
 // GT[(b,f)][(a,e)] = sum_L Bvv^L_ae Bvv^L_bf = <ab|ef>.  One task = one row
 // (a,b) and one 32x32 (e,f) tile pair with te <= tf; both GT blocks are read
 // along their contiguous (a,e) index and transposed through shared memory.
-template <int KIND>
-__global__ void __launch_bounds__(256) k_embed_antisym(const cplx* __restrict__ GT, int64_t ldt, int64_t a0,
+// GT holds complex FP64 or complex FP32 (GTE = float2) values.  cmin > 0: only
+// the columns (pairs e<f) >= cmin are written, and the 32x32 (e, f) tiles whose
+// e are all below emin are skipped (their GT entries were not computed).
+__device__ __forceinline__ cplx gt_load(const cplx* p, int64_t i) { return p[i]; }
+__device__ __forceinline__ cplx gt_load(const float2* p, int64_t i) {
+    const float2 v = p[i];
+    return make_double2(f32_to_f64(v.x), f32_to_f64(v.y));
+}
+
+template <int KIND, typename GTE>
+__global__ void __launch_bounds__(256) k_embed_antisym(const GTE* __restrict__ GT, int64_t ldt, int64_t a0,
                                                        int64_t gb0, int64_t prow0, int64_t nrows, int64_t V, EL L,
-                                                       void* __restrict__ out) {
+                                                       void* __restrict__ out, int64_t emin, int64_t cmin) {
     __shared__ cplx t1[32][33];
     __shared__ cplx t2[32][33];
     const int64_t T = (V + 31) / 32, npair = T * (T + 1) / 2;
@@ -748,15 +817,16 @@ __global__ void __launch_bounds__(256) k_embed_antisym(const cplx* __restrict__ 
             ++te;
         }
         const int64_t tf = te + rem;
+        if (te * 32 + 31 < emin) continue;  // uniform across the block
         int64_t a, b;
         pair_of(prow0 + row, V, a, b);
         const int64_t ra = (a - a0) * V, cb = (b - gb0) * V;
         const int64_t e0 = te * 32, f0 = tf * 32;
         for (int j = ty; j < 32; j += 8) {
             const int64_t f = f0 + j, e = e0 + tx;
-            t1[j][tx] = (f < V && e < V) ? GT[(cb + f) * ldt + ra + e] : zero;  // <ab|ef>, [f][e]
+            t1[j][tx] = (f < V && e < V) ? gt_load(GT, (cb + f) * ldt + ra + e) : zero;  // <ab|ef>, [f][e]
             const int64_t e2 = e0 + j, f2 = f0 + tx;
-            t2[j][tx] = (e2 < V && f2 < V) ? GT[(cb + e2) * ldt + ra + f2] : zero;  // <ab|fe>, [e][f]
+            t2[j][tx] = (e2 < V && f2 < V) ? gt_load(GT, (cb + e2) * ldt + ra + f2) : zero;  // <ab|fe>, [e][f]
         }
         __syncthreads();
         for (int j = ty; j < 32; j += 8) {
@@ -764,7 +834,8 @@ __global__ void __launch_bounds__(256) k_embed_antisym(const cplx* __restrict__ 
             if (e < f && f < V) {
                 const cplx u = t1[tx][j], w = t2[j][tx];
                 const int64_t ef = e * (2 * V - e - 1) / 2 + (f - e - 1);
-                embed_store<KIND, false>(out, L, 0, row, ef, f64_to_f32_rz(u.x - w.x), f64_to_f32_rz(u.y - w.y));
+                if (ef >= cmin)
+                    embed_store<KIND, false>(out, L, 0, row, ef, f64_to_f32_rz(u.x - w.x), f64_to_f32_rz(u.y - w.y));
             }
         }
         __syncthreads();
@@ -773,6 +844,59 @@ __global__ void __launch_bounds__(256) k_embed_antisym(const cplx* __restrict__ 
 
 int grid_n(Dev& D, int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)D.sm_count * 16));
+}
+
+// dst[c - c0][r] = conj(src[r][c]) for embedded A operands (rows r < nr of src
+// with layout Ls, columns c in [c0, c0 + nc); dst rows with layout Ld), the
+// embedded words moved as they are with the imaginary signs flipped (bf16x3:
+// three words (re,im) per complex element, imaginary in the high half; TF32:
+// (re, im)).  32 x 32 tiles through shared memory: reads along c, writes along r.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_transpose_conj_a(const void* __restrict__ src, EL Ls, int64_t nr,
+                                                          int64_t c0, int64_t nc, void* __restrict__ dst, EL Ld) {
+    constexpr int W = KIND == 0 ? 3 : 2;  // 32-bit words per complex element
+    __shared__ uint32_t tile[32][33][W];
+    const int64_t tr_n = (nr + 31) / 32, tc_n = (nc + 31) / 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const uint32_t* s32 = (const uint32_t*)src;
+    uint32_t* d32 = (uint32_t*)dst;
+    for (int64_t t = blockIdx.x; t < tr_n * tc_n; t += gridDim.x) {
+        const int64_t r0 = (t / tc_n) * 32, cc0 = (t % tc_n) * 32;
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t r = r0 + j, c = cc0 + tx;
+            if (r < nr && c < nc) {
+                if (KIND == 0) {
+                    // element offsets are in bf16 units: word = offset / 2
+                    for (int w = 0; w < 3; ++w)
+                        tile[j][tx][w] = s32[el_off(Ls, 0, r, 6 * (c0 + c) + 2 * w) / 2] ^ 0x80000000u;
+                } else {
+                    const uint2 v = *(const uint2*)(s32 + el_off(Ls, 0, r, 2 * (c0 + c)));
+                    tile[j][tx][0] = v.x;
+                    tile[j][tx][1] = v.y ^ 0x80000000u;
+                }
+            }
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            const int64_t c = cc0 + j, r = r0 + tx;
+            if (r < nr && c < nc) {
+                if (KIND == 0) {
+                    for (int w = 0; w < 3; ++w) d32[el_off(Ld, 0, c, 6 * r + 2 * w) / 2] = tile[tx][j][w];
+                } else {
+                    *(uint2*)(d32 + el_off(Ld, 0, c, 2 * r)) = make_uint2(tile[tx][j][0], tile[tx][j][1]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// zeros in complex columns [c_lo, c_hi) of rows [0, nr) of an embedded A operand
+template <int KIND>
+__global__ void k_zero_cols_a(void* __restrict__ out, EL L, int64_t nr, int64_t c_lo, int64_t c_hi) {
+    const int64_t w = c_hi - c_lo, total = nr * w;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        embed_store<KIND, false>(out, L, 0, i / w, c_lo + i % w, 0.0f, 0.0f);
 }
 
 // cuTensorMapEncodeTiled from the driver, resolved through the runtime so the
@@ -949,19 +1073,32 @@ void tc_embed_b(Dev& D, int prec, const cplx* B, int64_t sBb, int64_t sBk, int64
 // A' [batch][M][pitch], B' [batch][2N][pitch] of which the first kd columns
 // take part (kind 0: bf16, 1: tf32); FP32 accumulation chains of at most
 // kchunk k-blocks, added to C in FP64.
+// Options of one launch: the K range may start at k-block kbase of the
+// operands (kd then counts the embedded columns from there), and a tile mask
+// (mask_v > 0) skips the tiles whose rows and complex columns all have
+// (index mod mask_v) < mask_emin.
+struct TcExtra {
+    int kbase = 0;
+    int mask_v = 0, mask_emin = 0;
+    bool f32out = false;  // C is complex FP32 (beta must be 0 or 1)
+};
+
 static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
                       int64_t kd, int64_t pitch, int64_t rows_a, int64_t rows_b, int np, cplx* C, int64_t sCb,
                       const Lvl& lm, const Lvl& ln, cplx alpha, cplx beta, bool conj_acc, int kchunk,
-                      bool exact_alpha, double useful_flops, const char* name) {
+                      bool exact_alpha, double useful_flops, const char* name, const TcExtra& ex = TcExtra()) {
     REQUIRE(D.err_flag != nullptr, "gemm_tc: no error word");
     if (M <= 0 || N <= 0 || batch <= 0) return;
     const int64_t es = kind == 0 ? 2 : 4, kelem = ROWB / es;
-    REQUIRE(kd > 0 && (np > 1 || pitch >= kd) && (pitch * es) % 16 == 0 && (np == 1 || (batch == 1 && pitch % kelem == 0)),
+    const int64_t kext = (int64_t)ex.kbase * kelem + kd;  // embedded columns the operands hold up to the range end
+    REQUIRE(ex.kbase >= 0 && (ex.kbase == 0 || batch == 1), "gemm_tc: K offset needs batch 1");
+    REQUIRE(kd > 0 && (np > 1 || pitch >= kext) && (pitch * es) % 16 == 0 &&
+                (np == 1 || (batch == 1 && pitch % kelem == 0 && kext <= (int64_t)np * pitch)),
             "gemm_tc: bad embedded K");
     REQUIRE(((uintptr_t)pa % 16) == 0 && ((uintptr_t)pb % 16) == 0, "gemm_tc: operands not 16-byte aligned");
     const int bn = bn_for(2 * N);
     CUtensorMap ta, tb;
-    const uint64_t dx = np > 1 ? (uint64_t)pitch : (uint64_t)kd, dz = np > 1 ? (uint64_t)np : (uint64_t)batch;
+    const uint64_t dx = np > 1 ? (uint64_t)pitch : (uint64_t)kext, dz = np > 1 ? (uint64_t)np : (uint64_t)batch;
     encode(&ta, pa, kind, dx, (uint64_t)pitch, (uint64_t)M, (uint64_t)rows_a, dz, BM);
     encode(&tb, pb, kind, dx, (uint64_t)pitch, (uint64_t)(2 * N), (uint64_t)rows_b, dz, (uint32_t)bn);
     const int64_t tiles_m = (M + BM - 1) / BM, tiles_n = (2 * N + bn - 1) / bn;
@@ -973,7 +1110,7 @@ static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t 
     const int64_t sm = D.sm_count;
     int splits = 1, kps = num_kb;
     double best = 1e300;
-    for (int S = 1; S <= 96; ++S) {
+    for (int S = 1; S <= (ex.f32out ? 1 : 96); ++S) {
         if (S > 1 && num_kb / S < 8) break;
         const int k1 = (num_kb + S - 1) / S;
         const int se = (num_kb + k1 - 1) / k1;
@@ -998,9 +1135,16 @@ static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t 
     sc.group = (int)std::min<int64_t>(tiles_m, 16);
     sc.kchunk = kchunk;
     sc.kpb = np > 1 ? (int)(pitch / kelem) : 0;
+    sc.kbase = ex.kbase;
+    sc.mv = ex.mask_v;
+    sc.memin = ex.mask_emin;
+    sc.mrows = M;
+    sc.mcols = N;
     sc.units = (long long)tiles * splits;
     REQUIRE(batch < INT32_MAX, "gemm_tc: batch too large");
-    Epi ep{M, N, C, sCb, lm, ln, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0, exact_alpha ? 1 : 0};
+    REQUIRE(!ex.f32out || ((beta.x == 0.0 || beta.x == 1.0) && beta.y == 0.0), "gemm_tc: FP32 output with beta 0 or 1");
+    Epi ep{M, N, C, sCb, lm, ln, alpha, beta, conj_acc ? 1 : 0, splits > 1 ? 1 : 0, exact_alpha ? 1 : 0,
+           ex.f32out ? 1 : 0};
     if (splits > 1) {
         GemmArgs pg{};
         pg.M = M; pg.N = N; pg.batch = batch; pg.C = C; pg.sCb = sCb; pg.sCm = lm.s; pg.sCn = ln.s; pg.beta = beta;
@@ -1040,6 +1184,36 @@ void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t 
     tc_launch(D, kind, pa, pb, batch, M, N, slots(kind) * K, pitch, rows_a, rows_b, L.np, C, sCb, mk_lvl(sCm),
               mk_lvl(sCn), alpha, beta, conj_acc, KCHUNK, false, useful_flops,
               kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32");
+}
+
+void tc_gemm_embedded_ex(Dev& D, int prec, const void* pa, const void* pb, int64_t M, int64_t N, int64_t K_total,
+                         int64_t k0, int64_t pitch, int64_t rows_a, int64_t rows_b, cplx* C, int64_t sCm,
+                         int64_t sCn, cplx alpha, cplx beta, bool conj_acc, double useful_flops, int mask_v,
+                         int mask_emin, bool f32out) {
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    const int64_t es = kind == 0 ? 2 : 4, kelem = ROWB / es, S = slots(kind);
+    REQUIRE(K_total > 0 && k0 >= 0 && k0 < K_total && (S * k0) % kelem == 0,
+            "gemm_tc: K offset must start a k-block of the embedded operands");
+    const EL L = make_el(kind, K_total, rows_a, 1);
+    REQUIRE(L.pw == pitch, "gemm_tc: pitch does not match the layout");
+    TcExtra ex;
+    ex.kbase = (int)(S * k0 / kelem);
+    ex.mask_v = mask_v;
+    ex.mask_emin = mask_emin;
+    ex.f32out = f32out;
+    tc_launch(D, kind, pa, pb, 1, M, N, S * (K_total - k0), pitch, rows_a, rows_b, L.np, C, 0, mk_lvl(sCm),
+              mk_lvl(sCn), alpha, beta, conj_acc, KCHUNK, false, useful_flops,
+              kind == 0 ? "gemm_tc_bf16x3" : "gemm_tc_tf32", ex);
+}
+
+int64_t tc_k_align(int prec) {
+    // complex K indices at which a k-block of the embedded operands starts:
+    // multiples of lcm(slots, k-block) / slots
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    const int64_t es = kind == 0 ? 2 : 4, kelem = ROWB / es, S = slots(kind);
+    int64_t a = 1;
+    while ((S * a) % kelem) ++a;
+    return a;
 }
 
 // relative cost of running C[M][N] in this orientation: padded tensor-core
@@ -1191,17 +1365,45 @@ void gemm_tc(Dev& D, const GemmArgs& g0, int prec) {
 }
 
 void tc_embed_antisym_slab(Dev& D, int prec, const cplx* GT, int64_t ldt, int64_t a0, int64_t gb0, int64_t prow0,
-                           int64_t nrows, int64_t V, int64_t pitch, int64_t rows_tot, void* out) {
+                           int64_t nrows, int64_t V, int64_t pitch, int64_t rows_tot, void* out, int64_t emin,
+                           int64_t cmin, bool gt_f32) {
     const int64_t T = (V + 31) / 32, tasks = nrows * T * (T + 1) / 2;
     if (tasks <= 0) return;
     const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
     const EL L = make_el(kind, V * (V - 1) / 2, rows_tot, 1);
     REQUIRE(L.pw == pitch, "ladder: pitch does not match the layout");
     const int grid = (int)std::min<int64_t>(tasks, (int64_t)D.sm_count * 8);
-    if (prec == LRCC_MIXED_BF16X3)
-        k_embed_antisym<0><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, L, out);
-    else
-        k_embed_antisym<1><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, L, out);
+    const float2* GF = (const float2*)GT;
+    if (prec == LRCC_MIXED_BF16X3) {
+        if (gt_f32) k_embed_antisym<0, float2><<<grid, 256, 0, D.st>>>(GF, ldt, a0, gb0, prow0, nrows, V, L, out, emin, cmin);
+        else k_embed_antisym<0, cplx><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, L, out, emin, cmin);
+    } else {
+        if (gt_f32) k_embed_antisym<1, float2><<<grid, 256, 0, D.st>>>(GF, ldt, a0, gb0, prow0, nrows, V, L, out, emin, cmin);
+        else k_embed_antisym<1, cplx><<<grid, 256, 0, D.st>>>(GT, ldt, a0, gb0, prow0, nrows, V, L, out, emin, cmin);
+    }
+    LAUNCH_CHECK(D);
+}
+
+void tc_transpose_conj_a(Dev& D, int prec, const void* src, int64_t K_src, int64_t rows_src, int64_t nr, int64_t c0,
+                         int64_t nc, void* dst, int64_t rows_dst) {
+    if (nr <= 0 || nc <= 0) return;
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    const EL Ls = make_el(kind, K_src, rows_src, 1), Ld = make_el(kind, nr, rows_dst, 1);
+    const int64_t tiles = ((nr + 31) / 32) * ((nc + 31) / 32);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)D.sm_count * 8));
+    if (kind == 0) k_transpose_conj_a<0><<<grid, 256, 0, D.st>>>(src, Ls, nr, c0, nc, dst, Ld);
+    else k_transpose_conj_a<1><<<grid, 256, 0, D.st>>>(src, Ls, nr, c0, nc, dst, Ld);
+    LAUNCH_CHECK(D);
+}
+
+void tc_zero_cols_a(Dev& D, int prec, void* out, int64_t K, int64_t rows_tot, int64_t nr, int64_t c_lo,
+                    int64_t c_hi) {
+    if (nr <= 0 || c_hi <= c_lo) return;
+    const int kind = prec == LRCC_MIXED_BF16X3 ? 0 : 1;
+    const EL L = make_el(kind, K, rows_tot, 1);
+    const int grid = grid_n(D, nr * (c_hi - c_lo));
+    if (kind == 0) k_zero_cols_a<0><<<grid, 256, 0, D.st>>>(out, L, nr, c_lo, c_hi);
+    else k_zero_cols_a<1><<<grid, 256, 0, D.st>>>(out, L, nr, c_lo, c_hi);
     LAUNCH_CHECK(D);
 }
 

@@ -64,6 +64,7 @@ void ensure_bvv(lrcc_ctx* c) {
     c->lad.Bvv = empty(D, {(int64_t)c->L, (int64_t)V, (int64_t)V});
     axpby(D, mkc(1.0), c->B.slice(1, O, V).slice(2, O, V), false, mkc(0.0), c->lad.Bvv);
     c->lad.slab_rows = c->opt.slab_rows;
+    c->lad.hermitian = c->opt.ladder_hermitian;
 }
 
 void build_ham_impl(lrcc_ctx* c) {
@@ -633,6 +634,7 @@ void lrcc_default_options(lrcc_options* o) {
     o->fns_density = 0;
     o->solver = 0;
     o->subspace_max = 0;
+    o->ladder_hermitian = 0;
     o->embed_budget_mb = 0;
 }
 
@@ -682,6 +684,7 @@ lrcc_status lrcc_setup(const double* eps, const double* B, int L, const double* 
                 "the shared-subspace solver needs FP64-class products (LRCC_FP64 or LRCC_FP64_EMULATED)");
         REQUIRE(c->opt.subspace_max >= 0, "subspace_max must be >= 0");
         REQUIRE(c->opt.embed_budget_mb >= 0, "embed_budget_mb must be >= 0");
+        REQUIRE(c->opt.ladder_hermitian >= -1 && c->opt.ladder_hermitian <= 1, "ladder_hermitian must be -1, 0 or 1");
         c->D.embed_budget = double(c->opt.embed_budget_mb) * double(1 << 20);
         int dev = 0;
         CK(cudaGetDevice(&dev));

@@ -316,6 +316,15 @@ void oz_gemm_embedded(Dev& D, const void* pa, const void* pb, int64_t batch, int
 void tc_gemm_embedded(Dev& D, int prec, const void* pa, const void* pb, int64_t batch, int64_t M, int64_t N,
                       int64_t K, int64_t pitch, int64_t rows_a, int64_t rows_b, cplx* C, int64_t sCb, int64_t sCm,
                       int64_t sCn, cplx alpha, cplx beta, bool conj_acc, double useful_flops);
+// the same on the complex K range [k0, K_total) of operands embedded with K_total
+// (batch 1; k0 a multiple of tc_k_align(prec)), optionally skipping tiles: with
+// mask_v > 0 a tile runs only if one of its rows and one of its complex
+// columns have (index mod mask_v) >= mask_emin
+void tc_gemm_embedded_ex(Dev& D, int prec, const void* pa, const void* pb, int64_t M, int64_t N, int64_t K_total,
+                         int64_t k0, int64_t pitch, int64_t rows_a, int64_t rows_b, cplx* C, int64_t sCm,
+                         int64_t sCn, cplx alpha, cplx beta, bool conj_acc, double useful_flops, int mask_v,
+                         int mask_emin, bool f32out = false);
+int64_t tc_k_align(int prec);
 
 // ---------------------------------------------------------------------------
 // contraction engine (engine.cu)
@@ -335,7 +344,13 @@ void perm_axpby(Dev& D, const std::string& spec, cplx alpha, const Tensor& x, cp
 struct LadderCtx {
     Tensor Bvv;      // [L][V][V]
     Tensor Bov;      // [L][O][V] (B^L_me): the occupied-virtual factor of the Q map
+    // assembled <am||ef> rows W [V*O][P_V] (FP64 or FP64-class products), cached
+    // when they fit in a sixth of free memory; otherwise assembled per call
+    Tensor wq64;
+    int wq64_prec = -1;
+    bool wq64_disabled = false;
     int slab_rows = 0;  // > 0: no <ab||ef> cache; assemble per call in slabs of this many rows
+    int hermitian = 0;  // per-call assembly: 1 Hermitian half, -1 whole rows, 0 automatic
     // cached embedded <ab||ef> matrix W' [P_V][pitch] (rows a<b, K = pairs e<f)
     // for one mixed precision, built on first use when it fits in device memory
     std::shared_ptr<DevBuf> wcache;
@@ -363,7 +378,16 @@ void ladder_packed(Dev& D, LadderCtx& L, const cplx* Xt, cplx* Zt, int64_t ncol,
 // embedded <ab||ef> rows of one slab from GT[(b,f)][(a,e)] (leading dimension ldt),
 // rows (a,b) = pair(prow0 + row), written as A operand rows [nrows][pitch]
 void tc_embed_antisym_slab(Dev& D, int prec, const cplx* GT, int64_t ldt, int64_t a0, int64_t gb0, int64_t prow0,
-                           int64_t nrows, int64_t V, int64_t pitch, int64_t rows_tot, void* out);
+                           int64_t nrows, int64_t V, int64_t pitch, int64_t rows_tot, void* out, int64_t emin = 0,
+                           int64_t cmin = 0, bool gt_f32 = false);
+// dst[c - c0][r] = conj(src[r][c]): the conjugate transpose of columns
+// [c0, c0 + nc) of rows [0, nr) of an embedded A operand (K_src complex columns,
+// rows_src rows) into an embedded A operand with K = nr (rows_dst rows)
+void tc_transpose_conj_a(Dev& D, int prec, const void* src, int64_t K_src, int64_t rows_src, int64_t nr, int64_t c0,
+                         int64_t nc, void* dst, int64_t rows_dst);
+// zeros in complex columns [c_lo, c_hi) of rows [0, nr) of an embedded A operand
+void tc_zero_cols_a(Dev& D, int prec, void* out, int64_t K, int64_t rows_tot, int64_t nr, int64_t c_lo,
+                    int64_t c_hi);
 
 // Q map of the T1-weighted ladder piece: Q_amij = sum_ef <am||ef> X_ij^ef with
 // <am||ef> = sum_L (Bvv^L_ae Bov^L_mf - Bvv^L_af Bov^L_me), assembled from the

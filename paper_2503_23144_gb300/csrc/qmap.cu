@@ -118,6 +118,32 @@ void assemble_q(Dev& D, LadderCtx& LC, int64_t a0, int64_t na, int prec, Tensor&
     LAUNCH_CHECK(D);
 }
 
+// The whole W [V*O][P_V] once, when it fits in a sixth of the free memory,
+// built with FP64 products for the FP64 path and FP64-class (integer-slice)
+// products otherwise; a matrix built with FP64 products serves every precision.
+bool ensure_qcache(Dev& D, LadderCtx& LC, int prec) {
+    const int builder = prec == LRCC_FP64 ? LRCC_FP64 : LRCC_FP64_EMULATED;
+    if (LC.wq64.p && (LC.wq64_prec == LRCC_FP64 || LC.wq64_prec == builder)) return true;
+    if (LC.wq64_disabled) return false;
+    const int64_t O = LC.Bov.d[1], V = LC.Bov.d[2], PV = V * (V - 1) / 2;
+    if (16.0 * double(V * O) * double(PV) > free_bytes(D) / 6.0) {
+        LC.wq64_disabled = true;
+        return false;
+    }
+    LC.wq64 = Tensor();
+    Tensor W = empty(D, {V * O, PV});
+    const int64_t na = slab_a(D, O, V);
+    Tensor GT = empty(D, {O * V * na * V});
+    for (int64_t a0 = 0; a0 < V; a0 += na) {
+        const int64_t n = std::min(na, V - a0);
+        Tensor Ws = W.slice(0, a0 * O, n * O);
+        assemble_q(D, LC, a0, n, builder, GT, Ws);
+    }
+    LC.wq64 = W;
+    LC.wq64_prec = builder;
+    return true;
+}
+
 }  // namespace
 
 void qmap(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tensor& Q, int prec) {
@@ -135,6 +161,12 @@ void qmap(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tensor&
     Tensor Xt = empty(D, {R * PO, PV});
     ladder_pack_xt(D, X.p, Xt.p, R, O, V);
     Tensor Zq = empty(D, {V * O, R * PO});
+    if (ensure_qcache(D, LC, prec)) {
+        ein(D, "xk,nk->xn", mkc(2.0), LC.wq64, false, Xt, false, mkc(0.0), Zq, prec);
+        k_unpack_q<<<grid_of(D, R * V * O * O * O), 256, 0, D.st>>>(Zq.p, Q.p, R, V, O, alpha, beta, beta0);
+        LAUNCH_CHECK(D);
+        return;
+    }
     const int64_t na = slab_a(D, O, V);
     Tensor GT = empty(D, {O * V * na * V});
     Tensor W = empty(D, {na * O, PV});
@@ -165,6 +197,11 @@ void qmap_t(Dev& D, LadderCtx& LC, const Tensor& Qb, cplx alpha, cplx beta, Tens
     k_pack_q<<<grid_of(D, R * V * O * O * O), 256, 0, D.st>>>(Qb.p, Qt.p, R, V, O);
     LAUNCH_CHECK(D);
     Tensor Zt = empty(D, {R * PO, PV});
+    if (ensure_qcache(D, LC, prec)) {
+        ein(D, "xn,xk->nk", mkc(1.0), Qt, false, LC.wq64, false, mkc(0.0), Zt, prec);
+        ladder_unpack_zt(D, Zt.p, Xb.p, R, O, V, alpha, beta);
+        return;
+    }
     const int64_t na = slab_a(D, O, V);
     Tensor GT = empty(D, {O * V * na * V});
     Tensor W = empty(D, {na * O, PV});

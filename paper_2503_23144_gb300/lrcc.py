@@ -29,7 +29,8 @@ class lrcc_options(ctypes.Structure):
                 ("diis_size", ctypes.c_int), ("rhs_chunk", ctypes.c_int), ("prec", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("plus_omega", ctypes.c_int), ("slab_rows", ctypes.c_int),
                 ("pm_omega", ctypes.c_int), ("fp64_products", ctypes.c_int), ("fns_density", ctypes.c_int),
-                ("solver", ctypes.c_int), ("subspace_max", ctypes.c_int), ("embed_budget_mb", ctypes.c_int)]
+                ("solver", ctypes.c_int), ("subspace_max", ctypes.c_int), ("ladder_hermitian", ctypes.c_int),
+                ("embed_budget_mb", ctypes.c_int)]
 
 
 class LrccError(RuntimeError):

@@ -82,7 +82,7 @@ def test_setup_rejects_bad_ordering_and_sizes(lib):
 def test_setup_rejects_bad_options(lib):
     """Option validation happens before any device call."""
     s = _system()
-    for fields in ({"fns_density": 2}, {"prec": 7}, {"diis_size": 1}, {"solver": 2}, {"subspace_max": -1}, {"embed_budget_mb": -1},
+    for fields in ({"fns_density": 2}, {"prec": 7}, {"diis_size": 1}, {"solver": 2}, {"subspace_max": -1}, {"embed_budget_mb": -1}, {"ladder_hermitian": 2},
                    {"solver": 1, "prec": lib.LRCC_MIXED_BF16X3}):
         o = lib.lrcc_default_options()
         for field, bad in fields.items():
@@ -91,7 +91,7 @@ def test_setup_rejects_bad_options(lib):
             lib.lrcc_setup(s["eps"], s["B"], s["mu"], s["O"], s["V"], o)
         assert e.value.status == lib.LRCC_EINVAL, fields
     o = lib.lrcc_default_options()
-    assert o.fns_density == 0 and o.solver == 0 and o.subspace_max == 0 and o.embed_budget_mb == 0
+    assert o.fns_density == 0 and o.solver == 0 and o.subspace_max == 0 and o.embed_budget_mb == 0 and o.ladder_hermitian == 0
 
 
 def test_pack_roundtrip(lib):

@@ -71,11 +71,15 @@ def test_packed_fp64_against_oracle(L, sys19, slab_rows):
 
 
 @pytest.mark.parametrize("prec,tol", [(1, 3e-3), (2, 1e-4)])
-@pytest.mark.parametrize("slab_rows", [0, 7])
-def test_packed_tensor_core_vs_fp64(L, sys19, prec, tol, slab_rows):
+@pytest.mark.parametrize("slab_rows,herm", [(0, 0), (7, -1), (7, 1)])
+def test_packed_tensor_core_vs_fp64(L, sys19, prec, tol, slab_rows, herm):
+    """Cached <ab||ef>, and per-call assembly by whole rows (herm -1) or by the
+    Hermitian half of each row group with the conjugate-transpose products
+    (herm 1; groups of 21 rows, so the k-block boundary below each group's
+    first column and the zeroed columns up to it are exercised)."""
     s, W = sys19
     pv = W.shape[0]
-    ctx = _ctx(L, s, slab_rows=slab_rows)
+    ctx = _ctx(L, s, slab_rows=slab_rows, ladder_hermitian=herm)
     for ncol in WIDTHS:
         xd = torch.as_tensor(_xt(ncol, pv, 200 + ncol)).cuda()
         for tr in (False, True):
@@ -123,12 +127,15 @@ def test_packed_matches_full_layout(L, sys19):
 
 
 @pytest.mark.parametrize("prec,tol", [(1, 3e-3), (2, 1e-4)])
-@pytest.mark.parametrize("slab_rows", [0, 13])
-def test_packed_long_rows_in_panels(L, prec, tol, slab_rows):
+@pytest.mark.parametrize("slab_rows,herm", [(0, 0), (13, -1), (13, 1), (600, 1)])
+def test_packed_long_rows_in_panels(L, prec, tol, slab_rows, herm):
     """V = 60: the embedded rows (6 P_V bf16 = 10 620 elements, 2 P_V TF32) are
-    longer than one 16 KB panel, so <ab||ef> and X' are stored in K panels."""
+    longer than one 16 KB panel, so <ab||ef> and X' are stored in K panels; with
+    the Hermitian half (herm 1) the K ranges start inside panels, and a group of
+    all 1770 rows (slab_rows 600) gives a conjugate-transpose operand whose rows
+    (K = 1770: 21 KB in bf16x3) are stored in panels too."""
     s = synth.make_system(3, 60, 40, seed=14)
-    ctx = _ctx(L, s, slab_rows=slab_rows)
+    ctx = _ctx(L, s, slab_rows=slab_rows, ladder_hermitian=herm)
     pv = 60 * 59 // 2
     for ncol in (5, 48):
         xd = torch.as_tensor(_xt(ncol, pv, 300 + ncol)).cuda()
