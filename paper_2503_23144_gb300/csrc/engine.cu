@@ -132,6 +132,14 @@ std::string cat(const std::vector<char>& a, const std::vector<char>& b, const st
     return s;
 }
 
+// contractions worth the tensor cores: K of at least 48, or a short K (an
+// occupied index, O = 10..28) over a large output -- those are bound by writing
+// the output, which the tensor-core epilogue does at HBM rate while a SIMT
+// FP32 GEMM computes them at a few TFLOP/s
+bool tc_shape(int64_t M, int64_t N, int64_t K, int64_t batch) {
+    return K >= 48 || (K >= 8 && double(M) * double(N) * double(batch) >= double(1 << 22));
+}
+
 }  // namespace
 
 void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA, const Tensor& B0, bool cB,
@@ -190,7 +198,7 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
         for (char c : gk) K *= dim_of(c);
         for (char c : gb) Bt *= dim_of(c);
         const double fl = 8.0 * double(M) * double(N) * double(K) * double(Bt);
-        const bool big = gemm_tc_available() && fl >= 5e7 && K >= 48;
+        const bool big = gemm_tc_available() && fl >= 5e7 && tc_shape(M, N, K, Bt);
         const bool emu_tc = prec == LRCC_FP64_EMULATED && big && std::min(M, N) >= 8;  // sliced path: flat only
         if (!emu_tc && std::max(M, N) < FAST_INDEX_LIMIT && K < FAST_INDEX_LIMIT && Bt <= 65535) {
             std::vector<char> ob = order_by(gb, C, sp.c), om = order_by(gm, C, sp.c), on = order_by(gn, C, sp.c);
@@ -287,7 +295,7 @@ void ein(Dev& D, const std::string& spec, cplx alpha, const Tensor& A0, bool cA,
     double flops = 8.0 * double(g.M) * double(g.N) * double(g.K) * double(g.batch);
     // mixed mode: every contraction with real work goes to the tensor cores
     // (the O-sized contractions too: FP64 on this part is 1.25 TFLOP/s)
-    const bool big = gemm_tc_available() && flops >= 5e7 && g.K >= 48;
+    const bool big = gemm_tc_available() && flops >= 5e7 && tc_shape(g.M, g.N, g.K, g.batch);
     if (mixed && big) gemm_tc(D, g, prec);
     else if (mixed) gemm_f32c(D, g);
     else if (prec == LRCC_FP64_EMULATED && big && std::min(g.M, g.N) >= 8) gemm_tc_f64(D, g);
