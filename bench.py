@@ -375,6 +375,11 @@ def main():
                     help="write every timed GEMM launch (kernel, M, N, K, batch, ms, flops) to this CSV file")
     ap.add_argument("--ladder-only", action="store_true",
                     help="time only the particle-particle ladder (no ground state); used for kernel profiling")
+    ap.add_argument("--solve", action="store_true",
+                    help="one full lrcc_solve on the workload (ground state, then X, F X, Y and alpha for the "
+                         "--solve-omegas and --solve-comps, --rhs right-hand sides per chunk), timed")
+    ap.add_argument("--solve-omegas", default="0.0")
+    ap.add_argument("--solve-comps", default="2")
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -399,6 +404,11 @@ def main():
     ctx = L.lrcc_setup(s["eps"], s["B"], s["mu"], O, V, opt)
     if args.ladder_only:
         return ladder_only(args, L, ctx, O, V, Lx, R, prec, world, rank, local, pg)
+    if args.solve:
+        del ctx
+        opt.rhs_chunk = args.rhs or 1
+        ctx = L.lrcc_setup(s["eps"], s["B"], s["mu"], O, V, opt)
+        return solve_run(args, L, ctx, cfg, rank)
     if args.fns:
         opt.solver = 1 if args.solver == "subspace" else 0
         ctx = L.lrcc_setup(s["eps"], s["B"], s["mu"], O, V, opt)
@@ -522,6 +532,34 @@ def main():
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def solve_run(args, L, ctx, cfg, rank):
+    """Ground state (T, Lambda) and the linear-response solves of Eq. 29-35 on the
+    workload's system through the C ABI, each phase timed."""
+    omegas = [float(x) for x in args.solve_omegas.split(",")]
+    comps = [int(x) for x in args.solve_comps.split(",")]
+    t0 = time.perf_counter()
+    E, itT, itL = L.lrcc_ccsd_ground(ctx)
+    t_gs = time.perf_counter() - t0
+    n64g, nmixg = L.lrcc_solve_counts(ctx)
+    t0 = time.perf_counter()
+    alpha, err = L.lrcc_solve(ctx, omegas, comps)
+    t_sol = time.perf_counter() - t0
+    n64, nmix = L.lrcc_solve_counts(ctx)
+    if rank == 0:
+        print(json.dumps({"metric": "LR-CCSD alpha(omega) through lrcc_solve", "workload": args.workload,
+                          "O": cfg["O"], "V": cfg["V"], "L": cfg["L"], "precision": args.prec,
+                          "omegas": omegas, "comps": comps, "rhs_chunk": args.rhs or 1,
+                          "seconds": {"ground": t_gs, "solve": t_sol},
+                          "alpha_solves_per_s": len(omegas) * len(comps) / t_sol,
+                          "E_corr": [E.real, E.imag], "iters_T": itT, "maps_L": itL,
+                          "fp64_class_maps": n64, "mixed_maps": nmix,
+                          "alpha": [[[[float(alpha[w, a, b].real), float(alpha[w, a, b].imag)]
+                                      for b in range(len(comps))] for a in range(len(comps))]
+                                    for w in range(len(omegas))],
+                          "max_residual": float(err.max()),
+                          "phase_ms": [round(x, 1) for x in L.lrcc_phase_times(ctx)]}), flush=True)
 
 
 def fns_run(args, L, ctx, cfg, rank):
