@@ -74,7 +74,10 @@ def recorded_traffic(kernel, workload):
             continue
         src = os.path.join(ROOT, kv["source"])
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return float(kv["bytes_per_launch"]) if sha == kv.get("sha256_16") else None
+        if sha != kv.get("sha256_16"):
+            return None
+        return {"per_step": float(kv["bytes_per_step"]), "per_launch": float(kv["bytes_per_launch"]),
+                "launches_per_step": int(kv["launches_per_step"])}
     return None
 
 
@@ -501,8 +504,11 @@ def main():
         else:
             peak, unit, bound = 1.25, "TFLOP/s", "alu"              # FP64 nominal (FMA pipes)
             note = "GB300 FP64 nominal 1.25 TFLOP/s"
+        tr = recorded_traffic(name, args.workload)
         roof = {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": recorded_traffic(name, args.workload),
+                "frac": achieved / peak, "traffic": tr["per_step"] if tr else None,
+                "traffic_unit": "DRAM bytes (read + write) per step of this kernel family, ncu capture in profiles/",
+                "traffic_per_launch": tr["per_launch"] if tr else None,
                 "launches": st["count"] // args.steps,
                 "achieved_basis": "nominal F_step (2 F_sigma) / this family's device time per step",
                 "executed_tflops": executed, "executed_frac": executed / peak,
