@@ -320,6 +320,13 @@ lrcc_status lrcc_phase_times(const lrcc_ctx* ctx, double* ms7);
 /* Number of kernels this library launched on ctx since creation. */
 int64_t lrcc_kernel_launches(const lrcc_ctx* ctx);
 
+/* Device memory of ctx's allocator since creation, in bytes: held now (live),
+ * the most held at once (peak), and the largest single buffer requested
+ * (largest; every integral block, amplitude array and workspace is one
+ * buffer).  Host-side counters only: no device work, no synchronisation.
+ * LRCC_EINVAL on a NULL argument. */
+lrcc_status lrcc_memory_stats(const lrcc_ctx* ctx, int64_t* live, int64_t* peak, int64_t* largest);
+
 /*
  * Measurement hooks.  lrcc_profile(ctx, 1) starts recording a CUDA-event pair
  * around every GEMM launch on the context's stream (and clears old records);

@@ -707,12 +707,13 @@ static void assemble_slab(Dev& D, LadderCtx& LC, const Slab& sl, int prec, bool 
     REQUIRE(sc.a_pitch == LC.b_pitch, "ladder: embedded K pitch mismatch");
     const int64_t es = prec == LRCC_MIXED_BF16X3 ? 2 : 4;
     const char* pb = (const char*)LC.bcache->p + (size_t)(2 * sl.gb0 * V) * (size_t)(LC.b_pitch * es);
-    // the B rows from (b, f) = (gb0, 0) to the end of the cached embedding
-    const int64_t rows_b = LC.b_rows - 2 * sl.gb0 * V;
+    // B starts at row (b, f) = (gb0, 0) of the cached embedding; the GEMM reads
+    // its 2N rows from there, and K panels (long L) keep the cache's panel
+    // stride of b_rows rows
     // GT in complex FP32: it is only split into the bf16x3 / TF32 embedding
     // (2^-17 / 2^-11 relative), so FP32 (2^-24) loses nothing and halves its traffic
     const double frac = double(V - emin) / double(V);
-    tc_gemm_embedded_ex(D, prec, sc.aemb->p, pb, M, N, L, 0, LC.b_pitch, M, rows_b, GT.p, 1, M, mkc(1.0), mkc(0.0),
+    tc_gemm_embedded_ex(D, prec, sc.aemb->p, pb, M, N, L, 0, LC.b_pitch, M, LC.b_rows, GT.p, 1, M, mkc(1.0), mkc(0.0),
                         false, 8.0 * M * N * L * frac * frac, emin > 0 ? (int)V : 0, (int)emin, true);
     tc_embed_antisym_slab(D, prec, GT.p, M, sl.a0, sl.gb0, sl.prow0, sl.nrows, V, pitch_w, rows_w, Wemb, emin, cmin,
                           true);
@@ -934,13 +935,14 @@ static void ladder_hermitian(Dev& D, LadderCtx& LC, const cplx* Xt, void* pb, in
     void* pw = D.pool.get(wb);
     std::shared_ptr<DevBuf> hw(new DevBuf{&D.pool, pw, wb});
     tc_zero_tail(D, prec, pw, wrows, PV, wrows);
-    // conjugate-transpose block: rows c (at most PV - p1 of the first group), K = group rows
-    int64_t t_re, t_pitch;
-    const size_t tb = tc_embed_bytes(prec, PV, wrows, 1, t_re, t_pitch, false);
+    // conjugate-transpose block: rows c (at most PV - p1 of the first group), K = group rows;
+    // the group's slice of X as its B operand (each sized for the longest group)
+    int64_t t_re, t_pitch_max;
+    const size_t tb = tc_embed_bytes(prec, PV, wrows, 1, t_re, t_pitch_max, false);
     void* pt = D.pool.get(tb);
     std::shared_ptr<DevBuf> ht(new DevBuf{&D.pool, pt, tb});
-    int64_t g_re, g_pitch;
-    const size_t gbytes = tc_embed_bytes(prec, ncol, wrows, 1, g_re, g_pitch, true);
+    int64_t g_re, g_pitch_max;
+    const size_t gbytes = tc_embed_bytes(prec, ncol, wrows, 1, g_re, g_pitch_max, true);
     void* pg = D.pool.get(gbytes);
     std::shared_ptr<DevBuf> hg(new DevBuf{&D.pool, pg, gbytes});
     CK(cudaMemsetAsync(Zt, 0, sizeof(cplx) * (size_t)ncol * (size_t)PV, D.st));
@@ -959,18 +961,14 @@ static void ladder_hermitian(Dev& D, LadderCtx& LC, const cplx* Xt, void* pb, in
         tc_gemm_embedded_ex(D, prec, pw, pb, gr.nrows, ncol, PV, kstart, pitch, wrows, rows_e, Zt + q0, 1, PV,
                             mkc(1.0), mkc(1.0), transpose, 8.0 * gr.nrows * double(PV - q0) * ncol, 0, 0);
         if (q1 < PV) {
-            // GEMM 2: rows c in [q1, PV), K = the group's rows
-            const int64_t nc = PV - q1;
+            // GEMM 2: rows c in [q1, PV), K = the group's rows (pitch of that K)
+            const int64_t nc = PV - q1, kp = t_pitch_for(prec, gr.nrows);
             tc_transpose_conj_a(D, prec, pw, PV, wrows, gr.nrows, q1, nc, pt, nc);
-            tc_embed_b(D, prec, Xt + q0, 0, 1, PV, transpose, 1, gr.nrows, ncol, t_pitch_for(prec, gr.nrows), g_re,
-                       pg);
-            tc_gemm_embedded(D, prec, pt, pg, 1, nc, ncol, gr.nrows, t_pitch_for(prec, gr.nrows), nc, g_re, Zt + q1,
-                             0, 1, PV, mkc(1.0), mkc(1.0), transpose, 8.0 * double(nc) * gr.nrows * ncol);
+            tc_embed_b(D, prec, Xt + q0, 0, 1, PV, transpose, 1, gr.nrows, ncol, kp, g_re, pg);
+            tc_gemm_embedded(D, prec, pt, pg, 1, nc, ncol, gr.nrows, kp, nc, g_re, Zt + q1, 0, 1, PV, mkc(1.0),
+                             mkc(1.0), transpose, 8.0 * double(nc) * gr.nrows * ncol);
         }
     }
-    (void)t_re;
-    (void)t_pitch;
-    (void)g_pitch;
 }
 
 void ladder(Dev& D, LadderCtx& LC, const Tensor& X, cplx alpha, cplx beta, Tensor& Z, bool transpose, int prec) {

@@ -16,6 +16,7 @@ static size_t round_size(size_t n) {
 
 void* Pool::get(size_t n) {
     n = round_size(n);
+    largest = std::max(largest, n);
     auto it = cache.find(n);
     if (it != cache.end()) {
         void* p = it->second;

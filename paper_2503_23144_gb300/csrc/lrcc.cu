@@ -1039,6 +1039,14 @@ lrcc_status lrcc_phase_times(const lrcc_ctx* c, double* ms7) {
 
 int64_t lrcc_kernel_launches(const lrcc_ctx* c) { return c ? c->D.launches : 0; }
 
+lrcc_status lrcc_memory_stats(const lrcc_ctx* c, int64_t* live, int64_t* peak, int64_t* largest) {
+    if (!c || !live || !peak || !largest) return LRCC_EINVAL;
+    *live = (int64_t)c->D.pool.live;
+    *peak = (int64_t)c->D.pool.peak;
+    *largest = (int64_t)c->D.pool.largest;
+    return LRCC_OK;
+}
+
 static void clear_recs(Dev& D) {
     for (auto& r : D.recs) {
         cudaEventDestroy(r.a);

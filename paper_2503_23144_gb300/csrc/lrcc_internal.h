@@ -47,7 +47,7 @@ struct LrccError : std::runtime_error {
 // ---------------------------------------------------------------------------
 struct Pool {
     std::multimap<size_t, void*> cache;
-    size_t live = 0, cached = 0, peak = 0;
+    size_t live = 0, cached = 0, peak = 0, largest = 0;  // bytes; largest single request
     void* get(size_t n);
     void put(void* p, size_t n);
     void trim();

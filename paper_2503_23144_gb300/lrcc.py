@@ -44,6 +44,7 @@ _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 _vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
 
 # (name, restype, argtypes) of every exported symbol
 SIGNATURES = [
@@ -62,6 +63,7 @@ SIGNATURES = [
     ("lrcc_ladder_packed_dev", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _vp]),
     ("lrcc_phase_times", ctypes.c_int, [_vp, _dp]),
     ("lrcc_kernel_launches", ctypes.c_int64, [_vp]),
+    ("lrcc_memory_stats", ctypes.c_int, [_vp, _i64p, _i64p, _i64p]),
     ("lrcc_profile", ctypes.c_int, [_vp, ctypes.c_int]),
     ("lrcc_profile_dump", ctypes.c_int, [_vp, ctypes.c_char_p]),
     ("lrcc_get_amplitudes", ctypes.c_int, [_vp, ctypes.c_int, _dp]),
@@ -323,6 +325,13 @@ def lrcc_phase_times(ctx: Context) -> np.ndarray:
 
 def lrcc_kernel_launches(ctx: Context) -> int:
     return int(library().lrcc_kernel_launches(ctx.h))
+
+
+def lrcc_memory_stats(ctx: Context) -> tuple:
+    """(live, peak, largest) bytes of ctx's device allocator."""
+    v = [ctypes.c_int64(0) for _ in range(3)]
+    ctx.check(library().lrcc_memory_stats(ctx.h, *[ctypes.byref(x) for x in v]))
+    return tuple(int(x.value) for x in v)
 
 
 def lrcc_get_amplitudes(ctx: Context, which: int = 0) -> np.ndarray:

@@ -143,3 +143,21 @@ def test_packed_long_rows_in_panels(L, prec, tol, slab_rows, herm):
             z64 = L.lrcc_ladder_packed_dev(ctx, xd, transpose=tr)
             z = L.lrcc_ladder_packed_dev(ctx, xd, transpose=tr, prec=prec)
             assert (z - z64).abs().max().item() < tol * z64.abs().max().item(), (ncol, tr)
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 3e-3), (2, 1e-4)])
+@pytest.mark.parametrize("slab_rows,herm", [(7, -1), (7, 1)])
+def test_long_factor_rank_in_panels(L, prec, tol, slab_rows, herm):
+    """L = 2100: the embedded factor rows of the <ab|ef> assembly products
+    (6 L bf16 = 25 KB, 2 L TF32 = 16.8 KB) are longer than one 16 KB panel, so
+    the cached B^L_bf operand is stored in K panels, and every slab after the
+    first reads it from a row offset inside each panel (slabs of 7 rows)."""
+    s = synth.make_system(2, 40, 2100, seed=16)
+    ctx = _ctx(L, s, slab_rows=slab_rows, ladder_hermitian=herm)
+    pv = 40 * 39 // 2
+    for ncol in (3, 40):
+        xd = torch.as_tensor(_xt(ncol, pv, 400 + ncol)).cuda()
+        for tr in (False, True):
+            z64 = L.lrcc_ladder_packed_dev(ctx, xd, transpose=tr)
+            z = L.lrcc_ladder_packed_dev(ctx, xd, transpose=tr, prec=prec)
+            assert (z - z64).abs().max().item() < tol * z64.abs().max().item(), (ncol, tr)

@@ -70,7 +70,7 @@ def setup(L):
     lamf = L.pack_amplitudes(l1.reshape(1, O, V), _expand(O, V, l2u.reshape(po, pv))[None])
     ctx = L.lrcc_setup(s["eps"], s["B"], s["mu"], O, V)
     del s
-    return g, t, x, lamf, ctx
+    return g, t, x, lamf, ctx, L.lrcc_memory_stats(ctx)
 
 
 def _unique(flat, idx, O, V):
@@ -89,7 +89,7 @@ def _unique(flat, idx, O, V):
 
 @pytest.mark.parametrize("prec,tol", [(3, 1e-10), (2, 1e-4), (1, 3e-3)])
 def test_c4_maps_against_oracle(L, setup, prec, tol):
-    g, t, x, lamf, ctx = setup
+    g, t, x, lamf, ctx, _ = setup
     O, V = g["O"], g["V"]
     sig = L.lrcc_residual(ctx, L.LRCC_RES_SIGMA, t, x, prec=prec)[0]
     got = _unique(sig, np.array(g["rows"]), O, V)
@@ -102,3 +102,17 @@ def test_c4_maps_against_oracle(L, setup, prec, tol):
     ref = np.array(g["vjp_re"]) + 1j * np.array(g["vjp_im"])
     err = np.abs(got - ref).max() / g["vjp_max"]
     assert err < tol, ("vjp", prec, err)
+
+
+def test_c4_no_buffer_of_ov3_size(L, setup):
+    """After lrcc_setup, and after the maps above in all three precisions, no
+    device buffer of the context was as large as a quarter of one complex
+    O V^3 block (16 O V^3 bytes = 97 GB here): the three-virtual integrals are
+    never stored, not even in their unique half (e<f)."""
+    g, t, x, lamf, ctx, at_setup = setup
+    O, V = g["O"], g["V"]
+    block = 16 * O * V ** 3
+    live, peak, largest = L.lrcc_memory_stats(ctx)
+    print(f"setup: peak {at_setup[1] / 1e9:.1f} GB; maps: peak {peak / 1e9:.1f} GB, largest buffer {largest / 1e9:.1f} GB")
+    assert at_setup[2] < block / 4, at_setup
+    assert largest < block / 4, (live, peak, largest)
