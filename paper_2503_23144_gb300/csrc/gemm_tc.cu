@@ -790,25 +790,35 @@ __device__ __forceinline__ void pair_of(int64_t k, int64_t n, int64_t& p, int64_
 // GT[(b,f)][(a,e)] = sum_L Bvv^L_ae Bvv^L_bf = <ab|ef>.  One task = one row
 // (a,b) and one 32x32 (e,f) tile pair with te <= tf; both GT blocks are read
 // along their contiguous (a,e) index and transposed through shared memory.
-// GT holds complex FP64 or complex FP32 (GTE = float2) values.  cmin > 0: only
-// the columns (pairs e<f) >= cmin are written, and the 32x32 (e, f) tiles whose
-// e are all below emin are skipped (their GT entries were not computed).
-__device__ __forceinline__ cplx gt_load(const cplx* p, int64_t i) { return p[i]; }
-__device__ __forceinline__ cplx gt_load(const float2* p, int64_t i) {
-    const float2 v = p[i];
-    return make_double2(f32_to_f64(v.x), f32_to_f64(v.y));
+// GT holds complex FP64 or complex FP32 (GTE = float2) values.  The FP64
+// difference is truncated to FP32; the FP32 difference is taken in FP32
+// (round to nearest): both within 2^-23 relative of the exact difference of
+// the stored values, and no FP64 instruction touches FP32 input.  cmin > 0:
+// only the columns (pairs e<f) >= cmin are written, and the 32x32 (e, f) tiles
+// whose e are all below emin are skipped (their GT entries were not computed).
+__device__ __forceinline__ float2 gt_diff(const cplx& u, const cplx& w) {
+    return make_float2(f64_to_f32_rz(u.x - w.x), f64_to_f32_rz(u.y - w.y));
 }
+__device__ __forceinline__ float2 gt_diff(const float2& u, const float2& w) {
+    return make_float2(u.x - w.x, u.y - w.y);
+}
+template <typename GTE>
+__device__ __forceinline__ GTE gt_zero();
+template <>
+__device__ __forceinline__ cplx gt_zero<cplx>() { return make_double2(0.0, 0.0); }
+template <>
+__device__ __forceinline__ float2 gt_zero<float2>() { return make_float2(0.f, 0.f); }
 
 template <int KIND, typename GTE>
 __global__ void __launch_bounds__(256) k_embed_antisym(const GTE* __restrict__ GT, int64_t ldt, int64_t a0,
                                                        int64_t gb0, int64_t prow0, int64_t nrows, int64_t V, EL L,
                                                        void* __restrict__ out, int64_t emin, int64_t cmin) {
-    __shared__ cplx t1[32][33];
-    __shared__ cplx t2[32][33];
+    __shared__ GTE t1[32][33];
+    __shared__ GTE t2[32][33];
     const int64_t T = (V + 31) / 32, npair = T * (T + 1) / 2;
     const int64_t tasks = nrows * npair;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const cplx zero = make_double2(0.0, 0.0);
+    const GTE zero = gt_zero<GTE>();
     for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
         const int64_t row = t / npair;
         int64_t rem = t - row * npair, te = 0;
@@ -824,18 +834,19 @@ __global__ void __launch_bounds__(256) k_embed_antisym(const GTE* __restrict__ G
         const int64_t e0 = te * 32, f0 = tf * 32;
         for (int j = ty; j < 32; j += 8) {
             const int64_t f = f0 + j, e = e0 + tx;
-            t1[j][tx] = (f < V && e < V) ? gt_load(GT, (cb + f) * ldt + ra + e) : zero;  // <ab|ef>, [f][e]
+            t1[j][tx] = (f < V && e < V) ? GT[(cb + f) * ldt + ra + e] : zero;  // <ab|ef>, [f][e]
             const int64_t e2 = e0 + j, f2 = f0 + tx;
-            t2[j][tx] = (e2 < V && f2 < V) ? gt_load(GT, (cb + e2) * ldt + ra + f2) : zero;  // <ab|fe>, [e][f]
+            t2[j][tx] = (e2 < V && f2 < V) ? GT[(cb + e2) * ldt + ra + f2] : zero;  // <ab|fe>, [e][f]
         }
         __syncthreads();
         for (int j = ty; j < 32; j += 8) {
             const int64_t e = e0 + j, f = f0 + tx;
             if (e < f && f < V) {
-                const cplx u = t1[tx][j], w = t2[j][tx];
                 const int64_t ef = e * (2 * V - e - 1) / 2 + (f - e - 1);
-                if (ef >= cmin)
-                    embed_store<KIND, false>(out, L, 0, row, ef, f64_to_f32_rz(u.x - w.x), f64_to_f32_rz(u.y - w.y));
+                if (ef >= cmin) {
+                    const float2 d = gt_diff(t1[tx][j], t2[j][tx]);
+                    embed_store<KIND, false>(out, L, 0, row, ef, d.x, d.y);
+                }
             }
         }
         __syncthreads();
