@@ -1144,7 +1144,9 @@ static void tc_launch(Dev& D, int kind, const void* pa, const void* pb, int64_t 
     sc.kps = kps;
     sc.num_kb = num_kb;
     sc.group = (int)std::min<int64_t>(tiles_m, 16);
-    sc.kchunk = kchunk;
+    // complex-FP32 output adds its chunks in FP32 anyway: one chain over the whole K
+    // (the same rounding as FP32 chunk sums) without a read-modify-write of C per chunk
+    sc.kchunk = ex.f32out ? std::max(kchunk, num_kb) : kchunk;
     sc.kpb = np > 1 ? (int)(pitch / kelem) : 0;
     sc.kbase = ex.kbase;
     sc.mv = ex.mask_v;

@@ -34,10 +34,11 @@ def _sample_rows(V):
     return [(0, 1), (0, V - 1), (0, 640), (1, 641), (597, 598), (V - 2, V - 1)]
 
 
-# Tolerances: FP32 tensor-core accumulation over at most 128 k-blocks (512
-# MMA steps; each step rounds at most 2^-24 relative, summed in FP64 across
-# chunks: <= 3.1e-5), plus the split representation (bf16x3: 2^-17 per operand,
-# 3 cross products; TF32: 2^-11 per operand).
+# Tolerances: the <ab|ef> products accumulate in FP32 over K = L = 1800 (one
+# chain of 169 bf16x3 k-blocks, 676 MMA steps, each rounding at most 2^-24
+# relative: <= 4.1e-5; TF32 113 k-blocks), the contraction in FP32 chains of
+# 128 k-blocks summed in FP64 (<= 3.1e-5), plus the split representation
+# (bf16x3: 2^-17 per operand, 3 cross products; TF32: 2^-11 per operand).
 @pytest.mark.parametrize("prec,tol", [(2, 1e-4), (1, 5e-3)])
 def test_ladder_c5_sampled(c5, prec, tol):
     L, s, ctx, xt = c5
