@@ -159,3 +159,13 @@ def test_header_is_plain_c99_and_links(lib, tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.split()[:2] == ["200", "0"]
+
+
+def test_query_hooks_reject_null(lib):
+    """Host-only measurement hooks validate their arguments without a context
+    or a device: a NULL context or output pointer gives LRCC_EINVAL."""
+    so = lib.library()
+    v = [ctypes.c_int64(7) for _ in range(3)]
+    assert so.lrcc_memory_stats(None, *[ctypes.byref(x) for x in v]) == lib.LRCC_EINVAL
+    assert [x.value for x in v] == [7, 7, 7]
+    assert so.lrcc_kernel_launches(None) == 0
